@@ -1,0 +1,363 @@
+"""Benchmark: checkerboard Metropolis sweeps of the 2D Ising model on GB300.
+
+One step = one sweep (black half-sweep, then white half-sweep with the fused
+{M, bond sum} reduction) of a multi-spin-coded 65536 x 65536 lattice (4.3e9
+spins, two 1.07 GB colour planes: larger than L2, so no flush is needed),
+random start from seed 1234, beta = 0.4406868.  The metric is spin flips/ns =
+L^2 x sweeps / ns (attempted updates).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one independent replica per GPU (weak scaling,
+seed 1234 + rank, no data-path collective); the value is all replicas' flips
+divided by the slowest rank's time.  ``--impl reference`` times the CPU oracle
+(the plain C implementation the kernels are checked against) on the host
+cores instead.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "spin flips/ns at 1 GB300 (% of roofline)"
+UNIT = "flips/ns"
+BETA_C_CONFIG = 0.4406868
+PAPER_CONTEXT = "417.53 flips/ns, multi-spin code, (123x2048)^2, 1x V100-SXM (Table 2); other hardware"
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--L", type=int, default=65536)
+    p.add_argument("--beta", type=float, default=BETA_C_CONFIG)
+    p.add_argument("--seed", type=int, default=1234)
+    p.add_argument("--init", choices=["random", "up"], default="random")
+    p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--cpu-L", type=int, default=8192, help="oracle sample lattice side")
+    p.add_argument("--cpu-sweeps", type=int, default=10, help="oracle sample sweeps")
+    p.add_argument("--no-extras", action="store_true", help="skip per-beta, rng probe, e2e and cpu legs")
+    return p.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (timing only; no data-path collective)
+# ---------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def replica_seed(base: int, rank: int) -> int:
+    return base + rank
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        ids = [x.strip() for x in vis.split(",")] if vis else []
+        self.gpu = ids[local_rank] if local_rank < len(ids) else str(local_rank)
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            import tempfile
+
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.path is None:
+            return None
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        loaded = [s for s in sm if s > 0.5 * mx] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def time_sweeps(ising, torch, lat, beta, seed, steps, warmup, trace, stream, per_kernel=True):
+    """Warm up, then time `steps` sweeps on `stream`.  Each step is two public
+    calls (black half-sweep; white half-sweep with the fused trace row), with
+    CUDA events around every launch.  Returns (total_ms, black_ms[], white_ms[])."""
+    for k in range(warmup):
+        ising.ising_half_sweep(lat, beta, 0, seed, k, None, stream)
+        ising.ising_half_sweep(lat, beta, 1, seed, k, trace[k % trace.shape[0]], stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps + 1)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(steps):
+            t = warmup + k
+            ising.ising_half_sweep(lat, beta, 0, seed, t, None, stream)
+            ev[2 * k + 1].record(stream)
+            ising.ising_half_sweep(lat, beta, 1, seed, t, trace[k], stream)
+            ev[2 * k + 2].record(stream)
+    torch.cuda.synchronize()
+    black = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(steps)]
+    white = [ev[2 * k + 1].elapsed_time(ev[2 * k + 2]) for k in range(steps)]
+    total = ev[0].elapsed_time(ev[2 * steps])
+    return total, black, white
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_1906_06297_gb300 as ising
+
+    ising.build()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=device)
+
+    L, beta = args.L, args.beta
+    seed = replica_seed(args.seed, rank)
+    n_sites = L * L
+    stream = torch.cuda.Stream(device=device)
+    lat = ising.Lattice(L, "msc4", device=device)
+    mode = ising.ISING_INIT_RANDOM if args.init == "random" else ising.ISING_INIT_UP
+    ising.ising_init_lattice(lat, mode, seed, stream)
+    trace = torch.zeros((max(args.steps, args.warmup, 1), 2), dtype=torch.int64, device=device)
+    torch.cuda.synchronize()
+
+    barrier(world)
+    with ClockSampler(local) as clk:
+        total_ms, black, white = time_sweeps(ising, torch, lat, beta, seed, args.steps, args.warmup, trace, stream)
+    clocks = clk.summary()
+    barrier(world)
+    max_ms = max_over_ranks(total_ms, world, device)
+    value = world * n_sites * args.steps / (max_ms * 1e6)
+
+    _, plane_bytes = ising.ising_lattice_bytes(L, ising.ISING_MSC4)
+    launch_ms = statistics.mean(black + white)
+    # algorithmic bytes of one half-sweep: read + write the target plane, read the source plane
+    alg_bytes = 3 * plane_bytes
+    peaks, peak_kind = measured_peaks()
+    hbm_gbs = alg_bytes / (launch_ms * 1e-3) / 1e9
+
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "impl": "ours",
+        "config": {"workload": f"msc4 L={L} {args.init} start seed {args.seed}+rank beta={beta}, 1 sweep per step",
+                   "L": L, "layout": "msc4", "beta": beta, "spins": n_sites,
+                   "plane_bytes": plane_bytes, "l2": "inputs larger than L2 (two planes of "
+                   f"{plane_bytes / 1e9:.2f} GB each), no flush", "parallelism": f"replicas{world}"},
+        "gpu_launches": 2 * args.steps,
+        "kernel_ms": {"black_mean": round(statistics.mean(black), 4), "white_mean": round(statistics.mean(white), 4),
+                      "min": round(min(black + white), 4)},
+        "roofline": {"bound": "hbm", "achieved": round(hbm_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": round(hbm_gbs / peaks["hbm_gbs"], 4), "traffic": None,
+                     "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes},
+        "clocks": clocks,
+        "context": PAPER_CONTEXT,
+    }
+
+    if rank == 0 and not args.no_extras:
+        # per-beta rates (config: beta in {0.30, 0.4406868, 0.60})
+        per_beta = {}
+        for b in (0.30, BETA_C_CONFIG, 0.60):
+            tot, _, _ = time_sweeps(ising, torch, lat, b, seed, 20, 2, trace, stream)
+            per_beta[str(b)] = round(n_sites * 20 / (tot * 1e6), 2)
+        result["per_beta"] = per_beta
+        result["rng_probe"] = rng_probe(ising, torch, L, seed, stream)
+        result["e2e"] = run_e2e(ising, torch, args, L, beta, seed, device, stream)
+        result["cpu_baseline"] = cpu_baseline(args)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return result
+
+
+def rng_probe(ising, torch, L, seed, stream):
+    """The generator alone: one Philox4x32-10 block per 4 sites of a
+    half-sweep, each word compared with the a = 3 threshold and counted."""
+    n_blocks = L * L // 8
+    T3 = ising.ising_thresholds(BETA_C_CONFIG)[3]
+    cnt = torch.zeros(1, dtype=torch.int64, device=stream.device)
+    for _ in range(3):
+        ising.ising_rng_probe(n_blocks, seed, 0, 0, T3, cnt, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for k in range(reps):
+            ising.ising_rng_probe(n_blocks, seed, k, 0, T3, cnt, stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"half_sweep_sites_per_ns": round(4 * n_blocks / (ms * 1e6), 1), "ms": round(ms, 4),
+            "flips_per_ns_ceiling": round(4 * n_blocks / (ms * 1e6), 1)}
+
+
+def run_e2e(ising, torch, args, L, beta, seed, device, stream):
+    """Through the host-buffer entry point: every step copies both planes in
+    from pinned host memory, sweeps once, and copies planes and trace back."""
+    steps = max(1, args.e2e_steps)
+    dev = ising.Lattice(L, "msc4", device=device)
+    ising.ising_init_lattice(dev, ising.ISING_INIT_RANDOM, seed, stream)
+    torch.cuda.synchronize()
+    hb = dev.black.cpu().pin_memory()
+    hw = dev.white.cpu().pin_memory()
+    tr_dev = torch.zeros((1, 2), dtype=torch.int64, device=device)
+    tr_host = torch.zeros((1, 2), dtype=torch.int64).pin_memory()
+    ising.ising_sweep_host(dev, hb.data_ptr(), hw.data_ptr(), beta, 1, seed, 0, tr_dev, tr_host.data_ptr(), stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for k in range(steps):
+            ising.ising_sweep_host(dev, hb.data_ptr(), hw.data_ptr(), beta, 1, seed, 1 + k, tr_dev,
+                                   tr_host.data_ptr(), stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    plane = dev.row_bytes * L
+    return {"value": round(L * L * steps / (ms * 1e6), 3), "unit": UNIT, "h2d_bytes_per_step": 2 * plane,
+            "d2h_bytes_per_step": 2 * plane + 16, "steps": steps, "ms_per_step": round(ms / steps, 3)}
+
+
+def cpu_baseline(args):
+    """The oracle as it stands, on the host cores: a bounded sample of the
+    same workload (a smaller lattice, same beta and start)."""
+    import oracle
+
+    L = args.cpu_L
+    s = oracle.init(L, oracle.MODE_RANDOM, args.seed)
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    oracle.run(s, args.beta, args.cpu_sweeps, args.seed, trace=True, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": round(L * L * args.cpu_sweeps / (dt * 1e9), 4), "unit": UNIT, "cores": threads,
+            "kind": "oracle", "sample": f"int8 L={L} random start seed {args.seed}, {args.cpu_sweeps} sweeps at "
+            f"beta={args.beta}, {threads} OpenMP threads ({dt:.1f} s)"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    import oracle
+
+    if rank != 0:
+        return None
+    L = args.cpu_L
+    s = oracle.init(L, oracle.MODE_RANDOM, args.seed)
+    threads = oracle.max_threads()
+    for k in range(args.warmup):
+        oracle.run(s, args.beta, 1, args.seed, off=k, trace=True, nthreads=threads)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.run(s, args.beta, 1, args.seed, off=args.warmup + k, trace=True, nthreads=threads)
+    dt = time.perf_counter() - t0
+    value = L * L * args.steps / (dt * 1e9)
+    sample = (f"oracle (plain C, int8 full lattice) L={L} random start seed {args.seed}, beta={args.beta}, "
+              f"1 sweep per step; bounded sample of the msc4 L={args.L} workload")
+    return {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic", "impl": "reference",
+        "config": {"workload": f"msc4 L={args.L} random start seed {args.seed}+rank beta={args.beta}, "
+                               "1 sweep per step", "L": args.L, "beta": args.beta, "sample_L": L},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        res = run_reference(args, world, rank)
+    else:
+        res = run_ours(args, world, rank, local)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,146 @@
+/*
+ * ising.h -- C ABI of libising: checkerboard Metropolis sweeps of the 2D
+ * ferromagnetic Ising model (J = 1, h = 0, periodic L x L) on one GPU.
+ *
+ * Method: Romero, Bisson, Fatica, Bernaschi, "A Performance study of the 2D
+ * Ising model on GPUs" (arXiv:1906.06297).  Sec. 2 defines the model (Eq. 1),
+ * the Metropolis rule and the checkerboard decomposition; Sec. 3.1 and Fig. 1
+ * the two colour planes of N x N/2 spins compacted along rows; Fig. 2 the
+ * per-site update (neighbour indexing by colour and row parity, acceptance
+ * exp(-2 beta nn s)); Sec. 3.3 and Fig. 3 the multi-spin-coded lattice with
+ * 4 bits per spin and one launch per colour per step.
+ *
+ * Conventions shared by every entry point
+ *   - Site (i, c) (row i, column c, 0 <= i, c < L) is BLACK iff (i + c) is
+ *     even, WHITE otherwise.  It lives in its colour's plane at row i,
+ *     compacted column j = c / 2.  L must be even.
+ *   - A sweep is a black half-sweep followed by a white half-sweep.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key
+ *     (seed_lo, seed_hi) and counter (q_lo, q_hi, t_lo,
+ *     colour | purpose << 1 | t_hi << 8), where site = i * (L/2) + j,
+ *     q = site >> 2, t = sweep index, and the site's draw is output word
+ *     (site & 3).  purpose 0 = Metropolis, 1 = random initial state.  The
+ *     result therefore depends only on (seed, t, colour, site), never on the
+ *     launch shape.
+ *   - Acceptance: a = number of the 4 neighbours equal to the spin,
+ *     dE = 4a - 8, p_a = min(1, exp(-beta dE)); T[a] = 2^32 if p_a >= 1 else
+ *     floor(p_a * 2^32) (built once per call on the host in FP64); the spin
+ *     flips iff (uint64) u < T[a].
+ *   - Layouts of one colour plane (rows of `row_stride_bytes` bytes):
+ *       ISING_INT8: L rows x L/2 int8 spins (+1 / -1), Sec. 3.1.
+ *       ISING_MSC4: L rows x L/32 uint64 words; column j is word j/16, bits
+ *         4*(j%16) .. 4*(j%16)+3, value 1 for +1 and 0 for -1 (Sec. 3.3).
+ *         Needs L % 64 == 0, 16-byte aligned planes and a row stride that is a
+ *         multiple of 16 bytes.
+ *   - Memory: every pointer argument named *_dev is device memory owned by
+ *     the caller; the library allocates nothing.  Calls are asynchronous on
+ *     the given stream (NULL = legacy default stream) unless stated.
+ *   - Errors: every call returns an ising_status; arguments are checked before
+ *     any work is queued, and nothing aborts the process.
+ */
+#ifndef ISING_H
+#define ISING_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define ISING_API __attribute__((visibility("default")))
+#else
+#define ISING_API
+#endif
+
+/* Same object as cudaStream_t; declared here so this header needs no CUDA. */
+typedef struct CUstream_st *ising_stream_t;
+
+typedef enum {
+    ISING_OK = 0,
+    ISING_EINVAL = 1,   /* bad argument: see ising_strerror / the entry point */
+    ISING_ECUDA = 2,    /* a CUDA runtime call or a launch failed */
+    ISING_ETIMEOUT = 3, /* a bounded device wait gave up */
+} ising_status;
+
+typedef enum { ISING_INT8 = 0, ISING_MSC4 = 1 } ising_layout;
+
+typedef enum { ISING_INIT_RANDOM = 0, ISING_INIT_UP = 1, ISING_INIT_DOWN = 2 } ising_init_mode;
+
+/* A lattice: two caller-owned device planes.  Plain data; copy freely. */
+typedef struct {
+    void *black;              /* device pointer, colour 0 */
+    void *white;              /* device pointer, colour 1 */
+    int64_t L;                /* side length (even; MSC4: multiple of 64) */
+    int32_t layout;           /* ising_layout */
+    int32_t reserved;         /* must be 0 */
+    int64_t row_stride_bytes; /* bytes between plane rows; >= the row size */
+} ising_lattice_t;
+
+/* Bytes of one colour plane row (`row_bytes`, the minimum row stride) and of
+ * one dense plane (`plane_bytes` = L * row_bytes).  Either output may be NULL.
+ * EINVAL: L <= 0, L odd, MSC4 with L % 64 != 0, unknown layout. */
+ISING_API int ising_lattice_bytes(int64_t L, int32_t layout, size_t *row_bytes, size_t *plane_bytes);
+
+/* Host, synchronous: the acceptance table for beta (Sec. 2, Metropolis rule)
+ * exactly as the kernels use it.  EINVAL: beta < 0 or not finite, T NULL. */
+ISING_API int ising_thresholds(double beta, uint64_t T[5]);
+
+/* Fill both planes: ISING_INIT_RANDOM gives spin +1 iff the purpose-1 draw at
+ * t = 0 is below 2^31; UP / DOWN give all +1 / all -1. */
+ISING_API int ising_init_lattice(const ising_lattice_t *lat, int32_t init, uint64_t seed,
+                                 ising_stream_t stream);
+
+/* One half-sweep of colour `colour` (0 black, 1 white) at sweep index t
+ * (Sec. 2 checkerboard; Fig. 2 per-site rule).  If obs_dev is not NULL the
+ * kernel ADDS {sum of spins, sum over bonds s_i s_j} of the whole lattice
+ * after the update to obs_dev[0..1] (int64, caller zeroes it); this is only
+ * supported for colour 1, where every bond has exactly one white end. */
+ISING_API int ising_half_sweep(const ising_lattice_t *lat, double beta, int32_t colour, uint64_t seed,
+                               uint64_t t, int64_t *obs_dev, ising_stream_t stream);
+
+/* n_sweeps sweeps with sweep indices sweep_offset .. sweep_offset+n_sweeps-1
+ * (Sec. 3.3: two launches per step, black then white).  trace_dev, if not
+ * NULL, receives n_sweeps x 2 int64 {sum of spins, sum over bonds} after each
+ * sweep (the call zeroes it first).  Running a sweeps and then b sweeps with
+ * offset a gives the same lattice as a + b sweeps in one call. */
+ISING_API int ising_sweep(const ising_lattice_t *lat, double beta, int64_t n_sweeps, uint64_t seed,
+                          uint64_t sweep_offset, int64_t *trace_dev, ising_stream_t stream);
+
+/* Same as ising_sweep, for a lattice held in host memory: copies the dense
+ * host planes (L rows of ising_lattice_bytes' row_bytes each) into the
+ * caller's device lattice `dev`, runs the sweeps, and copies the planes and
+ * the trace (if trace_host is not NULL; trace_dev is then required as device
+ * staging of n_sweeps x 2 int64) back.  Pinned host memory makes the copies
+ * asynchronous; the call does not synchronise the stream. */
+ISING_API int ising_sweep_host(const ising_lattice_t *dev, void *black_host, void *white_host, double beta,
+                               int64_t n_sweeps, uint64_t seed, uint64_t sweep_offset, int64_t *trace_dev,
+                               int64_t *trace_host, ising_stream_t stream);
+
+/* out_dev[0..1] = {sum of spins, sum over bonds s_i s_j}: magnetisation
+ * M = out[0], energy E = -out[1] (Eq. 1 with J = 1). */
+ISING_API int ising_observables(const ising_lattice_t *lat, int64_t *out_dev, ising_stream_t stream);
+
+/* Convert between layouts (same L): int8 planes -> MSC4 planes and back. */
+ISING_API int ising_pack(const ising_lattice_t *int8_src, const ising_lattice_t *msc4_dst, ising_stream_t stream);
+ISING_API int ising_unpack(const ising_lattice_t *msc4_src, const ising_lattice_t *int8_dst, ising_stream_t stream);
+
+/* The random stream alone, as the MSC4 sweep draws it: for q in [0, n_blocks)
+ * compute the Philox block with counter (q_lo, q_hi, t_lo, colour | t_hi << 8)
+ * and key (seed), compare each of its 4 words with threshold T3 and ADD the
+ * number of words below it to *count_dev (uint64, caller zeroes it).  Used to
+ * measure the generator's throughput ceiling and to check the stream. */
+ISING_API int ising_rng_probe(uint64_t n_blocks, uint64_t seed, uint64_t t, int32_t colour, uint32_t T3,
+                              uint64_t *count_dev, ising_stream_t stream);
+
+/* Static description of a status code. */
+ISING_API const char *ising_strerror(int status);
+
+/* Text of the last EINVAL / ECUDA reason seen by this thread ("" if none). */
+ISING_API const char *ising_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISING_H */

@@ -55,6 +55,8 @@ def _load():
         lib.oracle_draw.restype = u32
         lib.oracle_thresholds.argtypes = [ctypes.c_double, p]
         lib.oracle_thresholds.restype = i32
+        lib.oracle_init_row.argtypes = [i64, i64, p, i32, u64]
+        lib.oracle_init_row.restype = None
         lib.oracle_init.argtypes = [i64, p, i32, u64]
         lib.oracle_init.restype = i32
         lib.oracle_update_row.argtypes = [i64, p, p, p, i64, i32, p, u64, u64]
@@ -114,6 +116,13 @@ def init(L: int, mode: int = MODE_RANDOM, seed: int = 0) -> np.ndarray:
     if _load().oracle_init(L, _ptr(s), mode, seed) != 0:
         raise ValueError(f"invalid lattice size {L}")
     return s
+
+
+def init_row(L: int, i: int, mode: int = MODE_RANDOM, seed: int = 0) -> np.ndarray:
+    """Row i of the initial state of an L x L lattice (int8, length L)."""
+    row = np.zeros(L, dtype=np.int8)
+    _load().oracle_init_row(L, i, _ptr(row), mode, seed)
+    return row
 
 
 def half_sweep(s: np.ndarray, beta: float, colour: int, seed: int, t: int, nthreads: int = 0):

@@ -130,24 +130,27 @@ static inline uint64_t plane_site(int64_t L, int64_t i, int64_t c)
     return (uint64_t)i * (uint64_t)(L / 2) + (uint64_t)(c / 2);
 }
 
-/* Initial state: mode 0 = keyed random, 1 = all +1, 2 = all -1. */
+/* Initial state of row i: mode 0 = keyed random, 1 = all +1, 2 = all -1. */
+void oracle_init_row(int64_t L, int64_t i, int8_t *row, int mode, uint64_t seed)
+{
+    for (int64_t c = 0; c < L; c++) {
+        int8_t v;
+        if (mode == 1) {
+            v = 1;
+        } else if (mode == 2) {
+            v = -1;
+        } else {
+            uint32_t u = oracle_draw(seed, plane_site(L, i, c), 0, colour_of(i, c), 1);
+            v = (u < 0x80000000u) ? 1 : -1;
+        }
+        row[c] = v;
+    }
+}
+
 int oracle_init(int64_t L, int8_t *s, int mode, uint64_t seed)
 {
     if (L <= 0 || (L & 1)) return 1;
-    for (int64_t i = 0; i < L; i++) {
-        for (int64_t c = 0; c < L; c++) {
-            int8_t v;
-            if (mode == 1) {
-                v = 1;
-            } else if (mode == 2) {
-                v = -1;
-            } else {
-                uint32_t u = oracle_draw(seed, plane_site(L, i, c), 0, colour_of(i, c), 1);
-                v = (u < 0x80000000u) ? 1 : -1;
-            }
-            s[i * L + c] = v;
-        }
-    }
+    for (int64_t i = 0; i < L; i++) oracle_init_row(L, i, s + i * L, mode, seed);
     return 0;
 }
 

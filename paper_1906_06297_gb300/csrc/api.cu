@@ -1,0 +1,413 @@
+// api.cu -- the C ABI of libising (declared in include/ising.h): argument
+// checks, the FP64 acceptance table, and the launch sequence of a sweep.
+//
+// Every entry point validates its arguments before queueing work and returns
+// a status; device planes are checked to be device memory of the current
+// device that covers the whole plane (cuMemGetAddressRange through the
+// runtime's driver entry point), so a wrong size or a host pointer becomes
+// ISING_EINVAL instead of an out-of-bounds access on the GPU.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/ising.h"
+#include "common.cuh"
+#include "launch.h"
+
+namespace ising {
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+int fail(int status, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(ISING_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct DeviceCache {
+    std::mutex mu;
+    int sm_count[64] = {};
+};
+DeviceCache g_dev;
+
+typedef CUresult (*AddressRangeFn)(CUdeviceptr *base, size_t *size, CUdeviceptr ptr);
+
+AddressRangeFn address_range_fn()
+{
+    static AddressRangeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<AddressRangeFn>(p);
+    });
+    return fn;
+}
+
+// ptr must be device (or managed) memory usable by the current device, with
+// [ptr, ptr + bytes) inside one allocation.
+int check_device_range(const void *ptr, size_t bytes, const char *name)
+{
+    if (ptr == nullptr) return fail(ISING_EINVAL, "%s is NULL", name);
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ISING_EINVAL, "%s is not a CUDA pointer (%s)", name, cudaGetErrorString(e));
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(ISING_EINVAL, "%s is not device memory", name);
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (at.type == cudaMemoryTypeDevice && at.device != dev)
+        return fail(ISING_EINVAL, "%s lives on device %d, current device is %d", name, at.device, dev);
+    AddressRangeFn fn = address_range_fn();
+    if (fn != nullptr) {
+        CUdeviceptr base = 0;
+        size_t size = 0;
+        if (fn(&base, &size, (CUdeviceptr)ptr) == CUDA_SUCCESS) {
+            const size_t off = (size_t)((CUdeviceptr)ptr - base);
+            if (off > size || size - off < bytes)
+                return fail(ISING_EINVAL, "%s: %zu bytes needed, allocation has %zu past the pointer", name, bytes,
+                            size - off);
+        }
+    }
+    return ISING_OK;
+}
+
+int row_bytes_of(int64_t L, int32_t layout, size_t *row)
+{
+    if (L <= 0 || (L & 1)) return fail(ISING_EINVAL, "L = %lld must be positive and even", (long long)L);
+    if (L > (int64_t(1) << 31)) return fail(ISING_EINVAL, "L = %lld is too large", (long long)L);
+    if (layout == ISING_INT8) {
+        *row = (size_t)(L / 2);
+    } else if (layout == ISING_MSC4) {
+        if (L % 64 != 0) return fail(ISING_EINVAL, "MSC4 needs L %% 64 == 0 (L = %lld)", (long long)L);
+        *row = (size_t)(L / 32) * sizeof(uint64_t);
+    } else {
+        return fail(ISING_EINVAL, "unknown layout %d", (int)layout);
+    }
+    return ISING_OK;
+}
+
+int check_lattice(const ising_lattice_t *lat)
+{
+    if (lat == nullptr) return fail(ISING_EINVAL, "lattice is NULL");
+    size_t row = 0;
+    int rc = row_bytes_of(lat->L, lat->layout, &row);
+    if (rc) return rc;
+    if (lat->reserved != 0) return fail(ISING_EINVAL, "reserved field must be 0");
+    if (lat->row_stride_bytes < (int64_t)row)
+        return fail(ISING_EINVAL, "row stride %lld < row size %zu", (long long)lat->row_stride_bytes, row);
+    if (lat->black == lat->white) return fail(ISING_EINVAL, "black and white planes alias");
+    if (lat->layout == ISING_MSC4) {
+        if (lat->row_stride_bytes % 16 != 0) return fail(ISING_EINVAL, "MSC4 row stride must be a multiple of 16");
+        if (((uintptr_t)lat->black | (uintptr_t)lat->white) % 16 != 0)
+            return fail(ISING_EINVAL, "MSC4 planes must be 16-byte aligned");
+    }
+    const size_t plane = (size_t)(lat->L - 1) * (size_t)lat->row_stride_bytes + row;
+    const char *b = (const char *)lat->black, *w = (const char *)lat->white;
+    if ((b < w && b + plane > w) || (w < b && w + plane > b)) return fail(ISING_EINVAL, "planes overlap");
+    rc = check_device_range(lat->black, plane, "black plane");
+    if (rc) return rc;
+    return check_device_range(lat->white, plane, "white plane");
+}
+
+int build_accept(double beta, Accept *acc, uint64_t T[5])
+{
+    int rc = ising_thresholds(beta, T);
+    if (rc) return rc;
+    const uint64_t two32 = uint64_t(1) << 32;
+    if (T[0] != two32 || T[1] != two32 || T[2] != two32)
+        return fail(ISING_EINVAL, "beta = %g gives a non-trivial threshold for dE <= 0", beta);
+    acc->T3_64 = T[3];
+    acc->T4_64 = T[4];
+    acc->A3 = T[3] >= two32 ? kNibbleLsb : 0u;
+    acc->A4 = T[4] >= two32 ? kNibbleLsb : 0u;
+    acc->T3 = T[3] >= two32 ? 0xffffffffu : (uint32_t)T[3];
+    acc->T4 = T[4] >= two32 ? 0xffffffffu : (uint32_t)T[4];
+    return ISING_OK;
+}
+
+int half_sweep_impl(const ising_lattice_t *lat, const Accept &acc, const RoundKeys &rk, int colour, uint64_t t,
+                    int64_t *obs, cudaStream_t s)
+{
+    const uint32_t c2 = (uint32_t)t, c3 = counter_word3(colour, kPurposeMetropolis, t);
+    cudaError_t e;
+    if (lat->layout == ISING_MSC4) {
+        Msc4SweepParams p;
+        p.tgt = (uint64_t *)(colour == 0 ? lat->black : lat->white);
+        p.src = (const uint64_t *)(colour == 0 ? lat->white : lat->black);
+        p.L = lat->L;
+        p.wpr = lat->L / 32;
+        p.stride = lat->row_stride_bytes / 8;
+        p.qrow = lat->L / 8;
+        p.total = ((p.wpr + 63) / 64) * lat->L;
+        p.c2 = c2;
+        p.c3 = c3;
+        p.acc = acc;
+        p.rk = rk;
+        p.obs = (long long *)obs;
+        e = msc4_half_sweep(p, colour, s);
+    } else {
+        Int8SweepParams p;
+        p.tgt = (int8_t *)(colour == 0 ? lat->black : lat->white);
+        p.src = (const int8_t *)(colour == 0 ? lat->white : lat->black);
+        p.L = lat->L;
+        p.half = lat->L / 2;
+        p.stride = lat->row_stride_bytes;
+        p.nblk = (lat->L * (lat->L / 2) + 3) / 4;
+        p.c2 = c2;
+        p.c3 = c3;
+        p.acc = acc;
+        p.rk = rk;
+        p.obs = (long long *)obs;
+        e = int8_half_sweep(p, colour, s);
+    }
+    return e == cudaSuccess ? ISING_OK : cuda_fail(e, "half-sweep launch");
+}
+
+}  // namespace
+
+cudaError_t device_info(DeviceInfo *info)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_dev.mu);
+    if (g_dev.sm_count[dev] == 0) {
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        g_dev.sm_count[dev] = n;
+    }
+    info->sm_count = g_dev.sm_count[dev];
+    return cudaSuccess;
+}
+
+}  // namespace ising
+
+using namespace ising;
+
+extern "C" {
+
+ISING_API const char *ising_strerror(int status)
+{
+    switch (status) {
+    case ISING_OK: return "ok";
+    case ISING_EINVAL: return "invalid argument";
+    case ISING_ECUDA: return "CUDA error";
+    case ISING_ETIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+    }
+}
+
+ISING_API const char *ising_last_error(void) { return g_last_error; }
+
+ISING_API int ising_lattice_bytes(int64_t L, int32_t layout, size_t *row_bytes, size_t *plane_bytes)
+{
+    size_t row = 0;
+    int rc = row_bytes_of(L, layout, &row);
+    if (rc) return rc;
+    if (row_bytes) *row_bytes = row;
+    if (plane_bytes) *plane_bytes = row * (size_t)L;
+    return ISING_OK;
+}
+
+ISING_API int ising_thresholds(double beta, uint64_t T[5])
+{
+    if (T == nullptr) return fail(ISING_EINVAL, "T is NULL");
+    if (!std::isfinite(beta) || beta < 0.0) return fail(ISING_EINVAL, "beta = %g must be finite and >= 0", beta);
+    for (int a = 0; a <= 4; ++a) {
+        // a aligned neighbours: flipping changes the energy by 2 s sum(nn) = 4a - 8
+        const double p = std::exp(-beta * (4.0 * a - 8.0));
+        T[a] = p >= 1.0 ? (uint64_t(1) << 32) : (uint64_t)std::floor(std::ldexp(p, 32));
+    }
+    return ISING_OK;
+}
+
+ISING_API int ising_init_lattice(const ising_lattice_t *lat, int32_t init, uint64_t seed, ising_stream_t stream)
+{
+    int rc = check_lattice(lat);
+    if (rc) return rc;
+    if (init < ISING_INIT_RANDOM || init > ISING_INIT_DOWN) return fail(ISING_EINVAL, "unknown init mode %d", init);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int colour = 0; colour < 2; ++colour) {
+        void *plane = colour == 0 ? lat->black : lat->white;
+        cudaError_t e = lat->layout == ISING_MSC4
+                            ? msc4_init((uint64_t *)plane, colour, lat->L, lat->row_stride_bytes / 8, init, seed, s)
+                            : int8_init((int8_t *)plane, colour, lat->L, lat->row_stride_bytes, init, seed, s);
+        if (e != cudaSuccess) return cuda_fail(e, "init launch");
+    }
+    return ISING_OK;
+}
+
+ISING_API int ising_half_sweep(const ising_lattice_t *lat, double beta, int32_t colour, uint64_t seed, uint64_t t,
+                               int64_t *obs_dev, ising_stream_t stream)
+{
+    int rc = check_lattice(lat);
+    if (rc) return rc;
+    if (colour != 0 && colour != 1) return fail(ISING_EINVAL, "colour must be 0 or 1");
+    if (obs_dev != nullptr) {
+        if (colour != 1) return fail(ISING_EINVAL, "observables are fused into the white half-sweep only");
+        rc = check_device_range(obs_dev, 2 * sizeof(int64_t), "obs");
+        if (rc) return rc;
+    }
+    Accept acc;
+    uint64_t T[5];
+    rc = build_accept(beta, &acc, T);
+    if (rc) return rc;
+    return half_sweep_impl(lat, acc, make_round_keys(seed), colour, t, obs_dev, (cudaStream_t)stream);
+}
+
+ISING_API int ising_sweep(const ising_lattice_t *lat, double beta, int64_t n_sweeps, uint64_t seed,
+                          uint64_t sweep_offset, int64_t *trace_dev, ising_stream_t stream)
+{
+    int rc = check_lattice(lat);
+    if (rc) return rc;
+    if (n_sweeps < 0) return fail(ISING_EINVAL, "n_sweeps = %lld < 0", (long long)n_sweeps);
+    Accept acc;
+    uint64_t T[5];
+    rc = build_accept(beta, &acc, T);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (trace_dev != nullptr && n_sweeps > 0) {
+        rc = check_device_range(trace_dev, (size_t)n_sweeps * 2 * sizeof(int64_t), "trace");
+        if (rc) return rc;
+        cudaError_t e = cudaMemsetAsync(trace_dev, 0, (size_t)n_sweeps * 2 * sizeof(int64_t), s);
+        if (e != cudaSuccess) return cuda_fail(e, "trace memset");
+    }
+    const RoundKeys rk = make_round_keys(seed);
+    for (int64_t k = 0; k < n_sweeps; ++k) {
+        const uint64_t t = sweep_offset + (uint64_t)k;
+        rc = half_sweep_impl(lat, acc, rk, 0, t, nullptr, s);
+        if (rc) return rc;
+        rc = half_sweep_impl(lat, acc, rk, 1, t, trace_dev ? trace_dev + 2 * k : nullptr, s);
+        if (rc) return rc;
+    }
+    return ISING_OK;
+}
+
+ISING_API int ising_sweep_host(const ising_lattice_t *dev, void *black_host, void *white_host, double beta,
+                               int64_t n_sweeps, uint64_t seed, uint64_t sweep_offset, int64_t *trace_dev,
+                               int64_t *trace_host, ising_stream_t stream)
+{
+    int rc = check_lattice(dev);
+    if (rc) return rc;
+    if (black_host == nullptr || white_host == nullptr) return fail(ISING_EINVAL, "host planes are NULL");
+    if (trace_host != nullptr && trace_dev == nullptr)
+        return fail(ISING_EINVAL, "trace_host needs trace_dev as device staging");
+    size_t row = 0;
+    row_bytes_of(dev->L, dev->layout, &row);
+    cudaStream_t s = (cudaStream_t)stream;
+    void *host[2] = {black_host, white_host};
+    void *devp[2] = {dev->black, dev->white};
+    for (int c = 0; c < 2; ++c) {
+        cudaError_t e = cudaMemcpy2DAsync(devp[c], (size_t)dev->row_stride_bytes, host[c], row, row, (size_t)dev->L,
+                                          cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    }
+    rc = ising_sweep(dev, beta, n_sweeps, seed, sweep_offset, trace_dev, stream);
+    if (rc) return rc;
+    for (int c = 0; c < 2; ++c) {
+        cudaError_t e = cudaMemcpy2DAsync(host[c], row, devp[c], (size_t)dev->row_stride_bytes, row, (size_t)dev->L,
+                                          cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    }
+    if (trace_host != nullptr && n_sweeps > 0) {
+        cudaError_t e = cudaMemcpyAsync(trace_host, trace_dev, (size_t)n_sweeps * 2 * sizeof(int64_t),
+                                        cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "trace copy");
+    }
+    return ISING_OK;
+}
+
+ISING_API int ising_observables(const ising_lattice_t *lat, int64_t *out_dev, ising_stream_t stream)
+{
+    int rc = check_lattice(lat);
+    if (rc) return rc;
+    rc = check_device_range(out_dev, 2 * sizeof(int64_t), "out");
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(out_dev, 0, 2 * sizeof(int64_t), s);
+    if (e != cudaSuccess) return cuda_fail(e, "observables memset");
+    e = lat->layout == ISING_MSC4
+            ? msc4_observables((const uint64_t *)lat->black, (const uint64_t *)lat->white, lat->L,
+                               lat->row_stride_bytes / 8, (long long *)out_dev, s)
+            : int8_observables((const int8_t *)lat->black, (const int8_t *)lat->white, lat->L, lat->row_stride_bytes,
+                               (long long *)out_dev, s);
+    return e == cudaSuccess ? ISING_OK : cuda_fail(e, "observables launch");
+}
+
+static int check_pair(const ising_lattice_t *a, int32_t la, const ising_lattice_t *b, int32_t lb)
+{
+    int rc = check_lattice(a);
+    if (rc) return rc;
+    rc = check_lattice(b);
+    if (rc) return rc;
+    if (a->layout != la || b->layout != lb) return fail(ISING_EINVAL, "wrong layouts for conversion");
+    if (a->L != b->L) return fail(ISING_EINVAL, "lattice sizes differ");
+    return ISING_OK;
+}
+
+ISING_API int ising_pack(const ising_lattice_t *int8_src, const ising_lattice_t *msc4_dst, ising_stream_t stream)
+{
+    int rc = check_pair(int8_src, ISING_INT8, msc4_dst, ISING_MSC4);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int c = 0; c < 2; ++c) {
+        cudaError_t e = msc4_pack((const int8_t *)(c ? int8_src->white : int8_src->black), int8_src->row_stride_bytes,
+                                  (uint64_t *)(c ? msc4_dst->white : msc4_dst->black), msc4_dst->row_stride_bytes / 8,
+                                  int8_src->L, s);
+        if (e != cudaSuccess) return cuda_fail(e, "pack launch");
+    }
+    return ISING_OK;
+}
+
+ISING_API int ising_unpack(const ising_lattice_t *msc4_src, const ising_lattice_t *int8_dst, ising_stream_t stream)
+{
+    int rc = check_pair(msc4_src, ISING_MSC4, int8_dst, ISING_INT8);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int c = 0; c < 2; ++c) {
+        cudaError_t e = msc4_unpack((const uint64_t *)(c ? msc4_src->white : msc4_src->black),
+                                    msc4_src->row_stride_bytes / 8, (int8_t *)(c ? int8_dst->white : int8_dst->black),
+                                    int8_dst->row_stride_bytes, msc4_src->L, s);
+        if (e != cudaSuccess) return cuda_fail(e, "unpack launch");
+    }
+    return ISING_OK;
+}
+
+ISING_API int ising_rng_probe(uint64_t n_blocks, uint64_t seed, uint64_t t, int32_t colour, uint32_t T3,
+                              uint64_t *count_dev, ising_stream_t stream)
+{
+    if (colour != 0 && colour != 1) return fail(ISING_EINVAL, "colour must be 0 or 1");
+    int rc = check_device_range(count_dev, sizeof(uint64_t), "count");
+    if (rc) return rc;
+    if (n_blocks == 0) return ISING_OK;
+    cudaError_t e = rng_probe(n_blocks, make_round_keys(seed), (uint32_t)t,
+                              counter_word3(colour, kPurposeMetropolis, t), T3, (unsigned long long *)count_dev,
+                              (cudaStream_t)stream);
+    return e == cudaSuccess ? ISING_OK : cuda_fail(e, "rng probe launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,42 @@
+// launch.h -- host-side launchers implemented by the kernel translation units
+// and called by the C ABI in api.cu.  Every launcher returns the cudaError_t of
+// its launch (cudaGetLastError right after it).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace ising {
+
+struct DeviceInfo {
+    int sm_count;
+};
+
+// Multi-spin-coded (4 bits per spin) lattice.
+cudaError_t msc4_init(uint64_t *plane, int colour, int64_t L, int64_t stride_words, int mode,
+                      uint64_t seed, cudaStream_t s);
+cudaError_t msc4_half_sweep(const Msc4SweepParams &p, int colour, cudaStream_t s);
+cudaError_t msc4_observables(const uint64_t *black, const uint64_t *white, int64_t L,
+                             int64_t stride_words, long long *out, cudaStream_t s);
+cudaError_t msc4_pack(const int8_t *src, int64_t src_stride, uint64_t *dst, int64_t dst_stride_words,
+                      int64_t L, cudaStream_t s);
+cudaError_t msc4_unpack(const uint64_t *src, int64_t src_stride_words, int8_t *dst, int64_t dst_stride,
+                        int64_t L, cudaStream_t s);
+
+// One int8 per spin.
+cudaError_t int8_init(int8_t *plane, int colour, int64_t L, int64_t stride, int mode, uint64_t seed,
+                      cudaStream_t s);
+cudaError_t int8_half_sweep(const Int8SweepParams &p, int colour, cudaStream_t s);
+cudaError_t int8_observables(const int8_t *black, const int8_t *white, int64_t L, int64_t stride,
+                             long long *out, cudaStream_t s);
+
+// Generator alone.
+cudaError_t rng_probe(uint64_t n_blocks, const RoundKeys &rk, uint32_t c2, uint32_t c3, uint32_t T3,
+                      unsigned long long *count, cudaStream_t s);
+
+// Cached per-device facts (SM count), for the device current on this thread.
+cudaError_t device_info(DeviceInfo *info);
+
+}  // namespace ising

@@ -1,0 +1,255 @@
+"""Parity of the CUDA path with the oracle: bit-exact lattices and traces.
+
+Every GPU result is decoded into a full L x L lattice by the oracle's own
+decoder of the documented plane layouts and compared element by element with
+the oracle's lattice for the same seed, beta, sweep offset and start state.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1906_06297_gb300 as ising
+from oracle import exact
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+BETAS = [0.0, 0.30, 0.4406868, 0.60, 50.0]
+MODES = {"random": ising.ISING_INIT_RANDOM, "up": ising.ISING_INIT_UP, "down": ising.ISING_INIT_DOWN}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    ising.build()
+    oracle.build()
+    torch.cuda.init()
+
+
+def full_from_gpu(lat: ising.Lattice) -> np.ndarray:
+    b, w = lat.planes_numpy()
+    if lat.layout == ising.ISING_MSC4:
+        return oracle.from_planes_msc4(lat.L, b, w)
+    return oracle.from_planes_int8(lat.L, b, w)
+
+
+def load_full(lat: ising.Lattice, s: np.ndarray):
+    if lat.layout == ising.ISING_MSC4:
+        b, w = oracle.to_planes_msc4(s)
+    else:
+        b, w = oracle.to_planes_int8(s)
+    lat.load_numpy(b, w)
+
+
+def gpu_run(lat, beta, n, seed, off=0, trace=True):
+    tr = torch.zeros((max(n, 1), 2), dtype=torch.int64, device="cuda") if trace else None
+    ising.ising_sweep(lat, beta, n, seed, off, tr)
+    torch.cuda.synchronize()
+    return tr[:n].cpu().numpy() if trace else None
+
+
+# ---------------------------------------------------------------------------
+# initial state
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("layout,L", [("int8", 2), ("int8", 6), ("int8", 10), ("int8", 130), ("int8", 256),
+                                      ("msc4", 64), ("msc4", 192), ("msc4", 256), ("msc4", 4224)])
+@pytest.mark.parametrize("mode", ["random", "up", "down"])
+def test_init_matches_oracle(layout, L, mode):
+    lat = ising.Lattice(L, layout)
+    ising.ising_init_lattice(lat, MODES[mode], 1234)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(full_from_gpu(lat), oracle.init(L, MODES[mode], 1234))
+
+
+# ---------------------------------------------------------------------------
+# sweeps from the library's own initial state
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("layout,L", [("int8", 2), ("int8", 6), ("int8", 18), ("int8", 130), ("int8", 256),
+                                      ("msc4", 64), ("msc4", 128), ("msc4", 192), ("msc4", 640),
+                                      ("msc4", 2112)])
+@pytest.mark.parametrize("beta", BETAS)
+def test_sweeps_bit_exact(layout, L, beta):
+    n, seed = 12, 77
+    lat = ising.Lattice(L, layout)
+    ising.ising_init_lattice(lat, ising.ISING_INIT_RANDOM, seed)
+    tr = gpu_run(lat, beta, n, seed)
+    s = oracle.init(L, oracle.MODE_RANDOM, seed)
+    tr_o = oracle.run(s, beta, n, seed)
+    np.testing.assert_array_equal(full_from_gpu(lat), s)
+    np.testing.assert_array_equal(tr, tr_o)
+
+
+@pytest.mark.parametrize("layout", ["int8", "msc4"])
+def test_reference_workload_1000_sweeps(layout):
+    """L = 256, beta = 0.4406868, random start from seed 1234, 1000 sweeps:
+    final lattice and the per-sweep {M, bond sum} trace bit-exact."""
+    L, beta, seed, n = 256, 0.4406868, 1234, 1000
+    lat = ising.Lattice(L, layout)
+    ising.ising_init_lattice(lat, ising.ISING_INIT_RANDOM, seed)
+    tr = gpu_run(lat, beta, n, seed)
+    s = oracle.init(L, oracle.MODE_RANDOM, seed)
+    tr_o = oracle.run(s, beta, n, seed)
+    np.testing.assert_array_equal(full_from_gpu(lat), s)
+    np.testing.assert_array_equal(tr, tr_o)
+
+
+@pytest.mark.parametrize("beta", [exact.BETA_C, 0.6])
+def test_several_tiles_with_ragged_tail(beta):
+    """L = 4224: 132 words per plane row = two full 64-word chunks and a
+    4-word tail; 4224 rows split over many warps."""
+    L, n, seed = 4224, 3, 5
+    lat = ising.Lattice(L, "msc4")
+    ising.ising_init_lattice(lat, ising.ISING_INIT_RANDOM, seed)
+    tr = gpu_run(lat, beta, n, seed, off=40)
+    s = oracle.init(L, oracle.MODE_RANDOM, seed)
+    tr_o = oracle.run(s, beta, n, seed, off=40)
+    np.testing.assert_array_equal(full_from_gpu(lat), s)
+    np.testing.assert_array_equal(tr, tr_o)
+
+
+# ---------------------------------------------------------------------------
+# arbitrary start states, padded strides, half-sweeps
+# ---------------------------------------------------------------------------
+STARTS = {
+    "neel": lambda L: inputs.neel(L),
+    "random": lambda L: inputs.random_lattice(L, 3),
+    "biased": lambda L: inputs.random_lattice(L, 4, p_up=0.9),
+    "domains": lambda L: inputs.domains(L, 5),
+}
+
+
+@pytest.mark.parametrize("layout,L,stride", [("int8", 64, None), ("int8", 66, 40), ("msc4", 128, None),
+                                             ("msc4", 192, 64), ("msc4", 256, 96)])
+@pytest.mark.parametrize("start", sorted(STARTS))
+@pytest.mark.parametrize("beta", [0.3, 0.4406868, 50.0])
+def test_half_sweeps_from_arbitrary_states(layout, L, stride, start, beta):
+    s = STARTS[start](L)
+    lat = ising.Lattice(L, layout, row_stride_bytes=stride)
+    load_full(lat, s)
+    seed, t = 99, 7
+    obs = torch.zeros(2, dtype=torch.int64, device="cuda")
+    ising.ising_half_sweep(lat, beta, 0, seed, t)
+    ising.ising_half_sweep(lat, beta, 1, seed, t, obs)
+    torch.cuda.synchronize()
+    oracle.half_sweep(s, beta, 0, seed, t)
+    oracle.half_sweep(s, beta, 1, seed, t)
+    np.testing.assert_array_equal(full_from_gpu(lat), s)
+    np.testing.assert_array_equal(obs.cpu().numpy(), oracle.observables(s))
+
+
+def test_padding_is_not_touched():
+    L, stride = 128, 64  # 16 bytes of data per row, 48 of padding
+    lat = ising.Lattice(L, "msc4", row_stride_bytes=stride)
+    lat.black.fill_(0xAB)
+    lat.white.fill_(0xCD)
+    ising.ising_init_lattice(lat, ising.ISING_INIT_RANDOM, 1)
+    ising.ising_sweep(lat, 0.44, 5, 1, 0, None)
+    torch.cuda.synchronize()
+    assert bool((lat.black[:, lat.row_bytes:] == 0xAB).all())
+    assert bool((lat.white[:, lat.row_bytes:] == 0xCD).all())
+
+
+# ---------------------------------------------------------------------------
+# invariants of the API
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("layout", ["int8", "msc4"])
+def test_resume_equals_single_call(layout):
+    L, beta, seed, a, b = 128, 0.4406868, 11, 9, 14
+    one = ising.Lattice(L, layout)
+    two = ising.Lattice(L, layout)
+    for lat in (one, two):
+        ising.ising_init_lattice(lat, ising.ISING_INIT_RANDOM, seed)
+    t1 = gpu_run(one, beta, a + b, seed)
+    ta = gpu_run(two, beta, a, seed)
+    tb = gpu_run(two, beta, b, seed, off=a)
+    np.testing.assert_array_equal(full_from_gpu(one), full_from_gpu(two))
+    np.testing.assert_array_equal(t1, np.vstack([ta, tb]))
+
+
+def test_int8_and_msc4_give_the_same_lattice():
+    L, beta, seed, n = 256, 0.35, 21, 30
+    a = ising.Lattice(L, "int8")
+    b = ising.Lattice(L, "msc4")
+    for lat in (a, b):
+        ising.ising_init_lattice(lat, ising.ISING_INIT_RANDOM, seed)
+    ta = gpu_run(a, beta, n, seed)
+    tb = gpu_run(b, beta, n, seed)
+    np.testing.assert_array_equal(full_from_gpu(a), full_from_gpu(b))
+    np.testing.assert_array_equal(ta, tb)
+    # and through the library's own conversion
+    c = ising.Lattice(L, "int8")
+    ising.ising_unpack(b, c)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(full_from_gpu(c), full_from_gpu(a))
+
+
+@pytest.mark.parametrize("layout,L", [("int8", 6), ("int8", 130), ("msc4", 64), ("msc4", 2112)])
+@pytest.mark.parametrize("start", sorted(STARTS))
+def test_observables_kernel(layout, L, start):
+    s = STARTS[start](L)
+    lat = ising.Lattice(L, layout)
+    load_full(lat, s)
+    out = torch.full((2,), 7, dtype=torch.int64, device="cuda")
+    ising.ising_observables(lat, out)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), oracle.observables(s))
+
+
+@pytest.mark.parametrize("L", [64, 192, 2112])
+def test_pack_unpack_against_oracle_encoding(L):
+    s = inputs.random_lattice(L, 8)
+    src = ising.Lattice(L, "int8")
+    load_full(src, s)
+    dst = ising.Lattice(L, "msc4")
+    ising.ising_pack(src, dst)
+    back = ising.Lattice(L, "int8", row_stride_bytes=L // 2 + 3)
+    ising.ising_unpack(dst, back)
+    torch.cuda.synchronize()
+    ob, ow = oracle.to_planes_msc4(s)
+    gb, gw = dst.planes_numpy()
+    np.testing.assert_array_equal(gb, ob)
+    np.testing.assert_array_equal(gw, ow)
+    np.testing.assert_array_equal(full_from_gpu(back), s)
+
+
+def test_rng_probe_counts_match_oracle():
+    n_blocks, seed, t, colour = 5000, 321, 3, 1
+    T3 = int(oracle.thresholds(0.4406868)[3])
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ising.ising_rng_probe(n_blocks, seed, t, colour, T3, cnt)
+    torch.cuda.synchronize()
+    expect = sum(int(oracle.draw(seed, site, t, colour) < T3) for site in range(4 * n_blocks))
+    assert int(cnt.item()) == expect
+
+
+def test_host_buffer_entry_point():
+    L, beta, seed, n = 256, 0.4406868, 4, 7
+    init = ising.Lattice(L, "msc4")
+    ising.ising_init_lattice(init, ising.ISING_INIT_RANDOM, seed)
+    torch.cuda.synchronize()
+    hb = init.black.cpu().pin_memory()
+    hw = init.white.cpu().pin_memory()
+    dev = ising.Lattice(L, "msc4")
+    tr_dev = torch.zeros((n, 2), dtype=torch.int64, device="cuda")
+    tr_host = torch.zeros((n, 2), dtype=torch.int64).pin_memory()
+    ising.ising_sweep_host(dev, hb.data_ptr(), hw.data_ptr(), beta, n, seed, 0, tr_dev, tr_host.data_ptr())
+    torch.cuda.synchronize()
+    s = oracle.init(L, oracle.MODE_RANDOM, seed)
+    tr_o = oracle.run(s, beta, n, seed)
+    got = oracle.from_planes_msc4(L, hb.numpy().view(np.uint64), hw.numpy().view(np.uint64))
+    np.testing.assert_array_equal(got, s)
+    np.testing.assert_array_equal(tr_host.numpy(), tr_o)
+
+
+def test_undersized_buffers_are_rejected():
+    """The library checks each plane against the extent of its CUDA allocation
+    (the caching allocator's segment, so only overruns past the segment can be
+    seen: the claims below are far larger than any segment)."""
+    lat = ising.Lattice(64, "msc4")
+    big = ising.ising_lattice_t(lat.black.data_ptr(), lat.white.data_ptr(), 1 << 16, ising.ISING_MSC4, 0, 1 << 14)
+    with pytest.raises(ising.IsingError) as e:
+        ising.ising_sweep(big, 0.4, 1, 1, 0, None)
+    assert e.value.status == ising.ISING_EINVAL
+    tr = torch.zeros(2, dtype=torch.int64, device="cuda")
+    with pytest.raises(ising.IsingError):
+        ising.ising_sweep(lat, 0.4, 1 << 24, 1, 0, tr)  # trace for 2^24 sweeps
