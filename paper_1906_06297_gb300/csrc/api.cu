@@ -140,8 +140,12 @@ int build_accept(double beta, Accept *acc, uint64_t T[5])
         return fail(ISING_EINVAL, "beta = %g gives a non-trivial threshold for dE <= 0", beta);
     acc->T3_64 = T[3];
     acc->T4_64 = T[4];
-    acc->A3 = T[3] >= two32 ? kNibbleLsb : 0u;
-    acc->A4 = T[4] >= two32 ? kNibbleLsb : 0u;
+    // T4 <= T3 for beta >= 0, and T3 reaches 2^32 only at beta = 0, where T4
+    // does too; the kernels then mask out the threshold test entirely
+    if (T[4] > T[3] || (T[3] >= two32) != (T[4] >= two32))
+        return fail(ISING_EINVAL, "beta = %g gives an unordered threshold table", beta);
+    acc->always = T[3] >= two32 ? 1u : 0u;
+    acc->zero = 0u;
     acc->T3 = T[3] >= two32 ? 0xffffffffu : (uint32_t)T[3];
     acc->T4 = T[4] >= two32 ? 0xffffffffu : (uint32_t)T[4];
     return ISING_OK;

@@ -66,12 +66,13 @@ enum Purpose { kPurposeMetropolis = 0, kPurposeInit = 1 };
 
 // ---------------------------------------------------------------------------
 // Acceptance, in the form the kernels consume.  For beta >= 0, T[0..2] = 2^32
-// (always flip); T3 / T4 are the 32-bit thresholds for a = 3 / a = 4 and the
-// "always" masks stand in for a threshold of 2^32 (beta = 0).
+// (always flip); T3 / T4 are the 32-bit thresholds for a = 3 / a = 4, and
+// `always` stands in for a threshold of 2^32 (beta = 0, where T3 = T4 = 2^32).
 // ---------------------------------------------------------------------------
 struct Accept {
-    uint32_t T3, T4;  // flip iff u < T (when not always)
-    uint32_t A3, A4;  // 0x11111111 if T64 >= 2^32 else 0 (nibble masks)
+    uint32_t T3, T4;  // 32-bit thresholds (meaningful when below 2^32)
+    uint32_t always;  // 1 when T3 = T4 = 2^32 (beta = 0): every spin flips
+    uint32_t zero;    // 0 (a value the compiler cannot see)
     uint64_t T3_64, T4_64;
 };
 

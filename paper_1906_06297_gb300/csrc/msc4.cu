@@ -41,169 +41,292 @@ namespace ising {
 
 namespace {
 
-constexpr int kThreads = 256;
+// Launch shape of the sweep kernel (compile-time; the defaults are the tuned
+// values for GB300).
+#ifndef ISING_MSC4_THREADS
+#define ISING_MSC4_THREADS 512
+#endif
+#ifndef ISING_MSC4_MIN_BLOCKS
+#define ISING_MSC4_MIN_BLOCKS 1
+#endif
+constexpr int kThreads = ISING_MSC4_THREADS;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMinRowsPerWarp = 16;
 
-__device__ __forceinline__ ulonglong2 ld128(const uint64_t *p)
+// 128-bit load that only the lanes holding words execute; the registers of
+// the other lanes are left undefined (their values never reach a valid lane).
+__device__ __forceinline__ uint4 ld128_if(const uint64_t *p, bool pred)
 {
-    return *reinterpret_cast<const ulonglong2 *>(p);
+    uint4 v;
+    asm volatile("{\n\t"
+                 ".reg .pred q;\n\t"
+                 "setp.ne.b32 q, %5, 0;\n\t"
+                 "@q ld.global.v4.u32 {%0, %1, %2, %3}, [%4];\n\t"
+                 "}"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "r"((int)pred));
+    return v;
 }
 
-__device__ __forceinline__ void st128(uint64_t *p, uint64_t x, uint64_t y)
+__device__ __forceinline__ uint32_t ld32_if(const uint32_t *p, bool pred)
 {
-    *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(x, y);
+    uint32_t v;
+    asm volatile("{\n\t"
+                 ".reg .pred q;\n\t"
+                 "setp.ne.b32 q, %2, 0;\n\t"
+                 "@q ld.global.u32 %0, [%1];\n\t"
+                 "}"
+                 : "=r"(v)
+                 : "l"(p), "r"((int)pred));
+    return v;
 }
 
-// New values of 8 spins (one 32-bit half word).  s: spins, k: neighbour sums
-// (nibble-wise 0..4); blocks c0 and c0+1 give the 8 draws (spin n uses word
-// n%4 of block c0 + n/4).  With OBS, adds the anti-aligned counts after the
-// update into the byte lanes of dbytes.
-template <bool OBS>
-__device__ __forceinline__ uint32_t update_half(uint32_t s, uint32_t k, uint32_t c0, uint32_t c1,
-                                                const Msc4SweepParams &p, uint32_t &dbytes)
+__device__ __forceinline__ void st128(uint64_t *p, uint4 v)
 {
-    uint32_t r3 = 0, r4 = 0;
+    *reinterpret_cast<uint4 *>(p) = v;
+}
+
+// Counts, at the nibble given by `bit`, how many of the two thresholds the
+// draw u fails: [u >= T3] + [u >= T4] (0..2).  Two compares and two predicated
+// updates per draw.  Where the updates run is a compile-time choice, because
+// the logic pipe and the multiply-add pipe share the load of this kernel:
+//   ISING_MSC4_MARK 0: two predicated adds into one counter (the compiler puts
+//                      them on the multiply-add pipe, next to Philox),
+//   ISING_MSC4_MARK 1: g3 by a predicated OR (logic pipe), g4 by an add,
+//   ISING_MSC4_MARK 2: both by predicated ORs (logic pipe).
+// The OR forms start from a runtime zero (Accept::zero), which keeps the
+// compiler from rewriting them as adds.  ncu on GB300: form 0 is fastest.
+#ifndef ISING_MSC4_MARK
+#define ISING_MSC4_MARK 0
+#endif
+__device__ __forceinline__ void mark_ge(uint32_t &g3, uint32_t &g4, uint32_t u, uint32_t T3, uint32_t T4,
+                                        uint32_t bit)
+{
+#if ISING_MSC4_MARK == 0
+    asm("{\n\t"
+        ".reg .pred p3, p4;\n\t"
+        "setp.ge.u32 p3, %1, %3;\n\t"
+        "setp.ge.u32 p4, %1, %4;\n\t"
+        "@p3 add.u32 %0, %0, %2;\n\t"
+        "@p4 add.u32 %0, %0, %2;\n\t"
+        "}"
+        : "+r"(g3)
+        : "r"(u), "r"(bit), "r"(T3), "r"(T4));
+    (void)g4;
+#elif ISING_MSC4_MARK == 1
+    asm("{\n\t"
+        ".reg .pred p3, p4;\n\t"
+        "setp.ge.u32 p3, %2, %4;\n\t"
+        "setp.ge.u32 p4, %2, %5;\n\t"
+        "@p3 or.b32 %0, %0, %3;\n\t"
+        "@p4 add.u32 %1, %1, %3;\n\t"
+        "}"
+        : "+r"(g3), "+r"(g4)
+        : "r"(u), "r"(bit), "r"(T3), "r"(T4));
+#else
+    asm("{\n\t"
+        ".reg .pred p3, p4;\n\t"
+        "setp.ge.u32 p3, %2, %4;\n\t"
+        "setp.ge.u32 p4, %2, %5;\n\t"
+        "@p3 or.b32 %0, %0, %3;\n\t"
+        "@p4 or.b32 %1, %1, %3;\n\t"
+        "}"
+        : "+r"(g3), "+r"(g4)
+        : "r"(u), "r"(bit), "r"(T3), "r"(T4));
+#endif
+}
+
+// New values of 8 spins (one 32-bit half word).
+//   s     spins (0/1 per nibble)
+//   t, e  neighbour words: t = up + down + centre (nibble-wise), e = side word
+//   c0,c1 Philox blocks c0 and c0+1 give the 8 draws (spin n uses word n%4 of
+//         block c0 + n/4); c0 is even
+//
+// With d = number of anti-aligned neighbours (0..4) and G = [u >= T3] +
+// [u >= T4] (T4 <= T3), the Metropolis decision "flip iff u < T[4 - d]"
+// (always for d >= 2) is exactly "flip iff d >= G": for d = 1 it reads
+// u < T3, for d = 0 it reads u < T4.  Per nibble d + 8 - G lies in 6..12, so
+// bit 3 of the nibble is the flip bit and no carry crosses nibbles.  d + 8 is
+// selected from k + 8 (down spin) and 12 - k (up spin), k = t + e.
+//
+// ALWAYS (beta = 0: every threshold is 2^32) flips every spin; the draws are
+// then irrelevant and not computed.
+//
+// With OBS, the anti-aligned counts after the update are added to the byte
+// lanes of dacc.
+template <bool OBS, bool ALWAYS>
+__device__ __forceinline__ uint32_t update_half(uint32_t s, uint32_t t, uint32_t e, uint32_t c0, uint32_t c1,
+                                                const Msc4SweepParams &p, uint32_t &dacc)
+{
+    const uint32_t a8 = t + e + 0x88888888u;  // 8 + k
+    const uint32_t b8 = 0xCCCCCCCCu - t - e;  // 12 - k
+    uint32_t ns;
+    if (ALWAYS) {
+        ns = s ^ kNibbleLsb;
+    } else {
+#if ISING_MSC4_MARK == 0
+        uint32_t g3 = 0, g4 = 0;  // g3 holds G, g4 stays 0
+#else
+        uint32_t g3 = p.acc.zero, g4 = p.acc.zero;
+#endif
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-        const uint4 u = philox(c0 + b, c1, p.c2, p.c3, p.rk);
-        const int sh = 16 * b;
-        r3 |= ((uint32_t)(u.x < p.acc.T3) << sh) | ((uint32_t)(u.y < p.acc.T3) << (sh + 4)) |
-              ((uint32_t)(u.z < p.acc.T3) << (sh + 8)) | ((uint32_t)(u.w < p.acc.T3) << (sh + 12));
-        r4 |= ((uint32_t)(u.x < p.acc.T4) << sh) | ((uint32_t)(u.y < p.acc.T4) << (sh + 4)) |
-              ((uint32_t)(u.z < p.acc.T4) << (sh + 8)) | ((uint32_t)(u.w < p.acc.T4) << (sh + 12));
+        for (int b = 0; b < 2; ++b) {
+            const uint4 u = philox(c0 | b, c1, p.c2, p.c3, p.rk);
+            mark_ge(g3, g4, u.x, p.acc.T3, p.acc.T4, 1u << (16 * b));
+            mark_ge(g3, g4, u.y, p.acc.T3, p.acc.T4, 1u << (16 * b + 4));
+            mark_ge(g3, g4, u.z, p.acc.T3, p.acc.T4, 1u << (16 * b + 8));
+            mark_ge(g3, g4, u.w, p.acc.T3, p.acc.T4, 1u << (16 * b + 12));
+        }
+        const uint32_t m = s * 15u;               // nibble mask of the up spins
+        const uint32_t d8 = (a8 & ~m) | (b8 & m);  // 8 + d
+        const uint32_t x = d8 - g3 - g4;
+        ns = s ^ ((x >> 3) & kNibbleLsb);
     }
-    // d = number of anti-aligned neighbours (4 - a): k for a down spin,
-    // 4 - k for an up spin.
-    const uint32_t m = s * 15u;
-    const uint32_t k4 = 0x44444444u - k;
-    const uint32_t d = (k & ~m) | (k4 & m);
-    const uint32_t t1 = d >> 1;
-    const uint32_t ge2 = (t1 | (t1 >> 1)) & kNibbleLsb;  // d >= 2: dE <= 0, always flip
-    const uint32_t eq1 = d & ~ge2 & kNibbleLsb;          // d == 1: a = 3
-    const uint32_t eq0 = ~(d | ge2) & kNibbleLsb;        // d == 0: a = 4
-    const uint32_t flip = ge2 | (eq1 & (r3 | p.acc.A3)) | (eq0 & (r4 | p.acc.A4));
-    const uint32_t ns = s ^ flip;
     if (OBS) {
+        // both selections have bit 3 set (k <= 4), so masking with 7 leaves d
         const uint32_t m2 = ns * 15u;
-        const uint32_t d2 = (k & ~m2) | (k4 & m2);
-        dbytes += (d2 & 0x0F0F0F0Fu) + ((d2 >> 4) & 0x0F0F0F0Fu);
+        const uint32_t d2 = (a8 & ~m2) | (b8 & m2);
+        dacc += (d2 & 0x07070707u) + ((d2 >> 4) & 0x07070707u);
     }
     return ns;
 }
 
-template <bool OBS>
-__device__ __forceinline__ uint64_t update_word(uint64_t s, uint64_t k, uint64_t q0, const Msc4SweepParams &p,
-                                                uint32_t &dbytes)
-{
-    // q0 is a multiple of 4, so the low counter word of its 4 blocks never carries.
-    const uint32_t c0 = (uint32_t)q0, c1 = (uint32_t)(q0 >> 32);
-    const uint32_t lo = update_half<OBS>((uint32_t)s, (uint32_t)k, c0, c1, p, dbytes);
-    const uint32_t hi = update_half<OBS>((uint32_t)(s >> 32), (uint32_t)(k >> 32), c0 + 2, c1, p, dbytes);
-    return ((uint64_t)hi << 32) | lo;
-}
-
-template <int COLOR, bool OBS>
-__global__ void __launch_bounds__(kThreads) msc4_sweep_kernel(const __grid_constant__ Msc4SweepParams p)
+template <int COLOR, bool OBS, bool ALWAYS>
+__global__ void __launch_bounds__(kThreads, ISING_MSC4_MIN_BLOCKS)
+    msc4_sweep_kernel(const __grid_constant__ Msc4SweepParams p)
 {
     const int lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t nw = (int64_t)gridDim.x * kWarps;
     const int64_t begin = gw * p.total / nw;
     const int64_t end = (gw + 1) * p.total / nw;
+    const int64_t L = p.L, stride = p.stride;
 
-    long long ones = 0, dsum = 0, nrows = 0;
+    uint32_t ones = 0, dsum = 0, nrows = 0;
 
     for (int64_t lin = begin; lin < end;) {
-        const int64_t chunk = lin / p.L;
-        const int64_t r0 = lin - chunk * p.L;
-        const int64_t r1 = min(p.L, r0 + (end - lin));
+        const int64_t chunk = lin / L;
+        const int64_t r0 = lin - chunk * L;
+        const int64_t r1 = min(L, r0 + (end - lin));
         lin += r1 - r0;
 
         const int64_t w0 = chunk * 64 + 2 * lane;
         const bool valid = w0 < p.wpr;
-        // chunk-edge lanes read the one side word that no lane of this warp holds
+        // chunk-edge lanes read the one side word that no lane of this warp
+        // holds: lane 0 the high half of the word on the left, the last valid
+        // lane the low half of the word on the right (periodic in the row);
+        // offsets in 32-bit units from this lane's first word
         const bool edge_right = valid && (lane == 31 || w0 + 2 >= p.wpr);
-        const int64_t w_left = (w0 == 0 ? p.wpr : w0) - 1;
-        const int64_t w_right = (w0 + 2 >= p.wpr) ? 0 : w0 + 2;
+        const int64_t off_left = 2 * ((w0 == 0 ? p.wpr : w0) - 1 - w0) + 1;
+        const int64_t off_right = 2 * ((w0 + 2 >= p.wpr ? 0 : w0 + 2) - w0);
+        const bool edge_left = lane == 0;
 
-        auto load_row = [&](int64_t r) {
-            return valid ? ld128(p.src + r * p.stride + w0) : make_ulonglong2(0, 0);
-        };
-        auto load_edge = [&](int64_t r) -> uint64_t {
+        const uint64_t *col = p.src + w0;  // this lane's column of the source plane
+        auto edge_of = [&](const uint64_t *row, int64_t r) -> uint32_t {
             const bool left = ((r + COLOR) & 1) == 0;
-            if (left) return lane == 0 ? p.src[r * p.stride + w_left] : 0;
-            return edge_right ? p.src[r * p.stride + w_right] : 0;
+            const uint32_t *h = reinterpret_cast<const uint32_t *>(row) + (left ? off_left : off_right);
+            return ld32_if(h, left ? edge_left : edge_right);
         };
 
-        ulonglong2 up = load_row(r0 == 0 ? p.L - 1 : r0 - 1);
-        ulonglong2 cur = load_row(r0);
-        uint64_t edge = load_edge(r0);
+        // rows r-1, r, r+1 of the source and row r of the target are in
+        // registers at the top of each iteration; rows r+2 / r+1 are fetched
+        // before the arithmetic of row r
+        int64_t rn = r0 + 2 >= L ? r0 + 2 - L : r0 + 2;  // row of the next source fetch
+        const uint64_t *pn = col + rn * stride;
+        const uint64_t *p_up = col + (r0 == 0 ? L - 1 : r0 - 1) * stride;
+        const uint64_t *p_cur = col + r0 * stride;
+        const uint64_t *p_dn = col + (r0 + 1 == L ? 0 : r0 + 1) * stride;
+        uint4 up = ld128_if(p_up, valid);
+        uint4 cur = ld128_if(p_cur, valid);
+        uint4 dn = ld128_if(p_dn, valid);
+        uint32_t edge = edge_of(p_cur, r0);
+        uint32_t edge_dn = edge_of(p_dn, r0 + 1);
+        uint64_t *tp = p.tgt + w0 + r0 * stride;  // target row r
+        uint4 tg = ld128_if(tp, valid);
+        uint64_t q0 = (uint64_t)r0 * (uint64_t)p.qrow + 4 * (uint64_t)w0;
 
         for (int64_t r = r0; r < r1; ++r) {
-            const int64_t rdn = (r + 1 == p.L) ? 0 : r + 1;
-            const ulonglong2 dn = load_row(rdn);
-            const uint64_t edge_dn = load_edge(rdn);
-            uint64_t *trow = p.tgt + r * p.stride;
-            const ulonglong2 tg = valid ? ld128(trow + w0) : make_ulonglong2(0, 0);
+            const uint4 nxt = ld128_if(pn, valid);
+            const uint32_t edge_nxt = edge_of(pn, rn);
+            const uint4 tg_nxt = ld128_if(tp + stride, valid && r + 1 < r1);
 
-            // side word: the source spin on the far side of each target spin
-            uint64_t sx, sy;
-            if (((r + COLOR) & 1) == 0) {  // left neighbour word
-                const uint64_t prev = __shfl_up_sync(0xffffffffu, cur.y, 1);
-                const uint64_t W = lane == 0 ? edge : prev;
-                sx = (cur.x << 4) | (W >> 60);
-                sy = (cur.y << 4) | (cur.x >> 60);
-            } else {  // right neighbour word
-                const uint64_t next = __shfl_down_sync(0xffffffffu, cur.x, 1);
-                const uint64_t E = edge_right ? edge : next;
-                sx = (cur.x >> 4) | (cur.y << 60);
-                sy = (cur.y >> 4) | (E << 60);
+            // side words, as 32-bit halves: .x/.y = lo/hi of word w0, .z/.w of w0+1
+            uint4 sd;
+            if (((r + COLOR) & 1) == 0) {  // left neighbour word: shift up one spin
+                const uint32_t prev = __shfl_up_sync(0xffffffffu, cur.w, 1);
+                const uint32_t W = edge_left ? edge : prev;
+                sd.x = __funnelshift_l(W, cur.x, 4);
+                sd.y = __funnelshift_l(cur.x, cur.y, 4);
+                sd.z = __funnelshift_l(cur.y, cur.z, 4);
+                sd.w = __funnelshift_l(cur.z, cur.w, 4);
+            } else {  // right neighbour word: shift down one spin
+                const uint32_t next = __shfl_down_sync(0xffffffffu, cur.x, 1);
+                const uint32_t E = edge_right ? edge : next;
+                sd.x = __funnelshift_r(cur.x, cur.y, 4);
+                sd.y = __funnelshift_r(cur.y, cur.z, 4);
+                sd.z = __funnelshift_r(cur.z, cur.w, 4);
+                sd.w = __funnelshift_r(cur.w, E, 4);
             }
-            // nibble-wise neighbour sums, 0..4: no carry ever leaves a nibble
-            const uint64_t kx = up.x + dn.x + cur.x + sx;
-            const uint64_t ky = up.y + dn.y + cur.y + sy;
-
-            const uint64_t q0 = (uint64_t)r * (uint64_t)p.qrow + 4 * (uint64_t)w0;
-            uint32_t dbytes = 0;
-            const uint64_t nx = update_word<OBS>(tg.x, kx, q0, p, dbytes);
-            const uint64_t ny = update_word<OBS>(tg.y, ky, q0 + 4, p, dbytes);
-            if (valid) st128(trow + w0, nx, ny);
+            // Philox blocks q0 .. q0+7 cover the lane's 32 sites; q0 % 8 == 0,
+            // so the low counter word never carries within them
+            const uint32_t c0 = (uint32_t)q0, c1 = (uint32_t)(q0 >> 32);
+            uint32_t dacc = 0;
+            uint4 ns;
+            // nibble-wise neighbour sums stay in 0..4: no carry leaves a nibble
+            ns.x = update_half<OBS, ALWAYS>(tg.x, up.x + dn.x + cur.x, sd.x, c0, c1, p, dacc);
+            ns.y = update_half<OBS, ALWAYS>(tg.y, up.y + dn.y + cur.y, sd.y, c0 | 2, c1, p, dacc);
+            ns.z = update_half<OBS, ALWAYS>(tg.z, up.z + dn.z + cur.z, sd.z, c0 | 4, c1, p, dacc);
+            ns.w = update_half<OBS, ALWAYS>(tg.w, up.w + dn.w + cur.w, sd.w, c0 | 6, c1, p, dacc);
+            if (valid) st128(tp, ns);
 
             if (OBS && valid) {
-                dsum += (dbytes * 0x01010101u) >> 24;
-                ones += __popcll(nx) + __popcll(ny) + __popcll(cur.x) + __popcll(cur.y);
+                // up-spin counts of the 32 white and 32 black sites, nibble-wise
+                // (at most 8 per nibble), then folded to bytes
+                const uint32_t n8 = ns.x + ns.y + ns.z + ns.w + cur.x + cur.y + cur.z + cur.w;
+                const uint32_t sb = (n8 & 0x0F0F0F0Fu) + ((n8 >> 4) & 0x0F0F0F0Fu);
+                ones += (sb * 0x01010101u) >> 24;    // 4 byte lanes of at most 16
+                dsum += (dacc * 0x01010101u) >> 24;  // 4 byte lanes of at most 32
                 nrows += 1;
             }
             up = cur;
             cur = dn;
+            dn = nxt;
+            tg = tg_nxt;
             edge = edge_dn;
+            edge_dn = edge_nxt;
+            tp += stride;
+            q0 += (uint64_t)p.qrow;
+            pn += stride;
+            if (++rn == L) {
+                rn = 0;
+                pn = col;
+            }
         }
     }
     if (OBS) {
         // per lane and row: 32 white + 32 black spins; 32 white sites x 4 bonds
-        const long long sum_s = 2 * ones - 64 * nrows;
-        const long long sum_b = 128 * nrows - 2 * dsum;
+        const long long sum_s = 2 * (long long)ones - 64 * (long long)nrows;
+        const long long sum_b = 128 * (long long)nrows - 2 * (long long)dsum;
         block_reduce_add2<kThreads>(sum_s, sum_b, p.obs);
     }
 }
 
 struct Occupancy {
     std::mutex mu;
-    int blocks[64][4] = {};  // per device: colour x obs
+    int blocks[64][8] = {};  // per device: colour x obs x always
 };
 Occupancy g_occ;
 
-template <int COLOR, bool OBS>
+template <int COLOR, bool OBS, bool ALWAYS>
 int sweep_blocks_per_sm()
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
     std::lock_guard<std::mutex> lock(g_occ.mu);
-    int &b = g_occ.blocks[dev][COLOR * 2 + (OBS ? 1 : 0)];
+    int &b = g_occ.blocks[dev][COLOR * 4 + (OBS ? 2 : 0) + (ALWAYS ? 1 : 0)];
     if (b == 0) {
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, msc4_sweep_kernel<COLOR, OBS>, kThreads, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, msc4_sweep_kernel<COLOR, OBS, ALWAYS>, kThreads, 0) !=
                 cudaSuccess ||
             n < 1)
             n = 1;
@@ -212,18 +335,26 @@ int sweep_blocks_per_sm()
     return b;
 }
 
-template <int COLOR, bool OBS>
+template <int COLOR, bool OBS, bool ALWAYS>
 cudaError_t launch_sweep(const Msc4SweepParams &p, cudaStream_t s)
 {
     DeviceInfo info;
     cudaError_t e = device_info(&info);
     if (e != cudaSuccess) return e;
-    const int64_t max_warps = (int64_t)info.sm_count * sweep_blocks_per_sm<COLOR, OBS>() * kWarps;
+    const int64_t max_warps = (int64_t)info.sm_count * sweep_blocks_per_sm<COLOR, OBS, ALWAYS>() * kWarps;
     const int64_t want = std::max<int64_t>(1, (p.total + kMinRowsPerWarp - 1) / kMinRowsPerWarp);
     const int64_t warps = std::min(max_warps, want);
     const int64_t blocks = (warps + kWarps - 1) / kWarps;
-    msc4_sweep_kernel<COLOR, OBS><<<(unsigned)blocks, kThreads, 0, s>>>(p);
+    msc4_sweep_kernel<COLOR, OBS, ALWAYS><<<(unsigned)blocks, kThreads, 0, s>>>(p);
     return cudaGetLastError();
+}
+
+template <int COLOR>
+cudaError_t launch_sweep_colour(const Msc4SweepParams &p, cudaStream_t s)
+{
+    const bool obs = p.obs != nullptr, always = p.acc.always != 0;
+    if (always) return obs ? launch_sweep<COLOR, true, true>(p, s) : launch_sweep<COLOR, false, true>(p, s);
+    return obs ? launch_sweep<COLOR, true, false>(p, s) : launch_sweep<COLOR, false, false>(p, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -336,9 +467,7 @@ unsigned grid_for(int64_t n, int threads)
 
 cudaError_t msc4_half_sweep(const Msc4SweepParams &p, int colour, cudaStream_t s)
 {
-    const bool obs = p.obs != nullptr;
-    if (colour == 0) return obs ? launch_sweep<0, true>(p, s) : launch_sweep<0, false>(p, s);
-    return obs ? launch_sweep<1, true>(p, s) : launch_sweep<1, false>(p, s);
+    return colour == 0 ? launch_sweep_colour<0>(p, s) : launch_sweep_colour<1>(p, s);
 }
 
 cudaError_t msc4_init(uint64_t *plane, int colour, int64_t L, int64_t stride_words, int mode, uint64_t seed,
