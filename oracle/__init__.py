@@ -77,6 +77,14 @@ def _load():
         for name in ("oracle_from_planes_int8", "oracle_from_planes_msc4"):
             getattr(lib, name).argtypes = [i64, p, p, i64, p]
             getattr(lib, name).restype = None
+        lib.oracle_draw_stream.argtypes = [u64, u32, u64, u64, i32, i32]
+        lib.oracle_draw_stream.restype = u32
+        lib.oracle_init_row_stream.argtypes = [i64, i64, p, i32, u64, u32]
+        lib.oracle_init_row_stream.restype = None
+        lib.oracle_swap_threshold.argtypes = [ctypes.c_double, ctypes.c_double, i64]
+        lib.oracle_swap_threshold.restype = u64
+        lib.oracle_batch_run.argtypes = [i64, p, p, i64, p, p, p, i64, u64, u64, i64, i32, p, i32]
+        lib.oracle_batch_run.restype = i32
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = i32
         _lib = lib
@@ -219,3 +227,57 @@ def row_from_planes_int8(L: int, i: int, black_row: np.ndarray, white_row: np.nd
 
 def max_threads() -> int:
     return int(_load().oracle_max_threads())
+
+
+# ---------------------------------------------------------------------------
+# batches with replica exchange
+# ---------------------------------------------------------------------------
+def draw_stream(seed: int, stream: int, site: int, t: int, colour: int, purpose: int = PURPOSE_METROPOLIS) -> int:
+    return int(_load().oracle_draw_stream(seed, stream, site, t, colour, purpose))
+
+
+def swap_threshold(beta_lo: float, beta_hi: float, D: int) -> int:
+    return int(_load().oracle_swap_threshold(float(beta_lo), float(beta_hi), int(D)))
+
+
+class Batch:
+    """n full int8 lattices with sides L[i]; ladders of S consecutive lattices
+    over the inverse temperatures `beta` (S ascending values)."""
+
+    def __init__(self, L, S: int, beta, mode: int = MODE_RANDOM, seed: int = 0):
+        self.L = np.ascontiguousarray(L, dtype=np.int64)
+        self.n = int(self.L.size)
+        self.S = int(S)
+        self.beta = np.ascontiguousarray(beta, dtype=np.float64)
+        assert self.beta.size == self.S and self.n % self.S == 0
+        self.start = np.concatenate([[0], np.cumsum(self.L * self.L)])
+        self.spins = np.zeros(int(self.start[-1]), dtype=np.int8)
+        for i in range(self.n):
+            Li = int(self.L[i])
+            view = self.spins[self.start[i]:self.start[i + 1]].reshape(Li, Li)
+            for r in range(Li):
+                row = np.zeros(Li, dtype=np.int8)
+                _load().oracle_init_row_stream(Li, r, _ptr(row), mode, seed, i)
+                view[r] = row
+        self.slot_of = (np.arange(self.n) % self.S).astype(np.int32)
+        self.lattice_at = np.arange(self.n, dtype=np.int32)
+
+    def lattice(self, i: int) -> np.ndarray:
+        Li = int(self.L[i])
+        return self.spins[self.start[i]:self.start[i + 1]].reshape(Li, Li)
+
+    def run(self, n_sweeps: int, seed: int, off: int = 0, record_every: int = 0, swaps: bool = True,
+            nthreads: int = 0):
+        """Sweeps in place; returns the trace (events x n x 2, slot-ordered
+        within each ladder) when record_every > 0."""
+        n_events = 0
+        if record_every > 0:
+            n_events = (off + n_sweeps) // record_every - off // record_every
+        tr = np.zeros((max(n_events, 0), self.n, 2), dtype=np.int64) if record_every > 0 else None
+        rc = _load().oracle_batch_run(self.n, _ptr(self.L), _ptr(self.spins), self.S, _ptr(self.beta),
+                                      _ptr(self.slot_of), _ptr(self.lattice_at), n_sweeps, seed, off,
+                                      record_every, int(bool(swaps)), _ptr(tr) if tr is not None else None,
+                                      nthreads)
+        if rc != 0:
+            raise ValueError("invalid batch arguments")
+        return tr

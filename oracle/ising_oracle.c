@@ -84,19 +84,28 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
     out[0] = x[0]; out[1] = x[1]; out[2] = x[2]; out[3] = x[3];
 }
 
-/* The 32-bit draw for one site of one colour plane at sweep t. */
-uint32_t oracle_draw(uint64_t seed, uint64_t site, uint64_t t, int colour, int purpose)
+/*
+ * The 32-bit draw for one site of one colour plane at sweep t.  `stream`
+ * separates the lattices of a batch (and the ladders of its replica swaps):
+ * it is added to counter word 1, which is q_hi for a single lattice.
+ */
+uint32_t oracle_draw_stream(uint64_t seed, uint32_t stream, uint64_t site, uint64_t t, int colour, int purpose)
 {
     uint64_t q = site >> 2;
     uint32_t ctr[4], key[2], out[4];
     ctr[0] = (uint32_t)(q & 0xffffffffu);
-    ctr[1] = (uint32_t)(q >> 32);
+    ctr[1] = (uint32_t)(q >> 32) + stream;
     ctr[2] = (uint32_t)(t & 0xffffffffu);
     ctr[3] = (uint32_t)colour | ((uint32_t)purpose << 1) | ((uint32_t)(t >> 32) << 8);
     key[0] = (uint32_t)(seed & 0xffffffffu);
     key[1] = (uint32_t)(seed >> 32);
     oracle_philox4x32_10(ctr, key, out);
     return out[site & 3];
+}
+
+uint32_t oracle_draw(uint64_t seed, uint64_t site, uint64_t t, int colour, int purpose)
+{
+    return oracle_draw_stream(seed, 0, site, t, colour, purpose);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -131,7 +140,7 @@ static inline uint64_t plane_site(int64_t L, int64_t i, int64_t c)
 }
 
 /* Initial state of row i: mode 0 = keyed random, 1 = all +1, 2 = all -1. */
-void oracle_init_row(int64_t L, int64_t i, int8_t *row, int mode, uint64_t seed)
+void oracle_init_row_stream(int64_t L, int64_t i, int8_t *row, int mode, uint64_t seed, uint32_t stream)
 {
     for (int64_t c = 0; c < L; c++) {
         int8_t v;
@@ -140,11 +149,16 @@ void oracle_init_row(int64_t L, int64_t i, int8_t *row, int mode, uint64_t seed)
         } else if (mode == 2) {
             v = -1;
         } else {
-            uint32_t u = oracle_draw(seed, plane_site(L, i, c), 0, colour_of(i, c), 1);
+            uint32_t u = oracle_draw_stream(seed, stream, plane_site(L, i, c), 0, colour_of(i, c), 1);
             v = (u < 0x80000000u) ? 1 : -1;
         }
         row[c] = v;
     }
+}
+
+void oracle_init_row(int64_t L, int64_t i, int8_t *row, int mode, uint64_t seed)
+{
+    oracle_init_row_stream(L, i, row, mode, seed, 0);
 }
 
 int oracle_init(int64_t L, int8_t *s, int mode, uint64_t seed)
@@ -159,33 +173,46 @@ int oracle_init(int64_t L, int8_t *s, int mode, uint64_t seed)
  * ("below") of the full lattice.  The row is updated in place; sites of the
  * other colour in it are only read (they are the horizontal neighbours).
  */
-void oracle_update_row(int64_t L, const int8_t *above, int8_t *row, const int8_t *below,
-                       int64_t i, int colour, const uint64_t T[5], uint64_t seed, uint64_t t)
+void oracle_update_row_stream(int64_t L, const int8_t *above, int8_t *row, const int8_t *below, int64_t i,
+                              int colour, const uint64_t T[5], uint64_t seed, uint64_t t, uint32_t stream)
 {
     for (int64_t c = 0; c < L; c++) {
         if (colour_of(i, c) != colour) continue;
         int nb = above[c] + below[c] + row[wrap(c - 1, L)] + row[wrap(c + 1, L)];
         int s = row[c];
         int a = (4 + s * nb) / 2; /* aligned neighbours: s*nb = a - (4 - a) */
-        uint32_t u = oracle_draw(seed, plane_site(L, i, c), t, colour, 0);
+        uint32_t u = oracle_draw_stream(seed, stream, plane_site(L, i, c), t, colour, 0);
         if ((uint64_t)u < T[a]) row[c] = (int8_t)(-s);
     }
 }
 
+void oracle_update_row(int64_t L, const int8_t *above, int8_t *row, const int8_t *below, int64_t i, int colour,
+                       const uint64_t T[5], uint64_t seed, uint64_t t)
+{
+    oracle_update_row_stream(L, above, row, below, i, colour, T, seed, t, 0);
+}
+
 /* One half-sweep: every site of one colour, rows in parallel. */
-void oracle_half_sweep(int64_t L, int8_t *s, int colour, const uint64_t T[5], uint64_t seed,
-                       uint64_t t, int nthreads)
+void oracle_half_sweep_stream(int64_t L, int8_t *s, int colour, const uint64_t T[5], uint64_t seed, uint64_t t,
+                              uint32_t stream, int nthreads)
 {
 #ifdef _OPENMP
     if (nthreads <= 0) nthreads = omp_get_max_threads();
-#pragma omp parallel for schedule(static) num_threads(nthreads)
+    /* threads only pay off on large lattices; small ones run serially */
+#pragma omp parallel for schedule(static) num_threads(nthreads) if (L >= 256)
 #endif
     for (int64_t i = 0; i < L; i++) {
         const int8_t *above = s + wrap(i - 1, L) * L;
         const int8_t *below = s + wrap(i + 1, L) * L;
-        oracle_update_row(L, above, s + i * L, below, i, colour, T, seed, t);
+        oracle_update_row_stream(L, above, s + i * L, below, i, colour, T, seed, t, stream);
     }
     (void)nthreads;
+}
+
+void oracle_half_sweep(int64_t L, int8_t *s, int colour, const uint64_t T[5], uint64_t seed, uint64_t t,
+                       int nthreads)
+{
+    oracle_half_sweep_stream(L, s, colour, T, seed, t, 0, nthreads);
 }
 
 /*
@@ -315,4 +342,94 @@ int oracle_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------- */
+/* Batches of lattices with replica exchange (parallel tempering).            */
+/*                                                                            */
+/* Not in the paper: a batch of n independent lattices (sides L[i]) swept     */
+/* together.  Lattice i draws with stream i.  Lattices [l*S, (l+1)*S) form    */
+/* ladder l over S inverse temperatures beta[0] < ... < beta[S-1]; lattice i  */
+/* sits at slot slot_of[i] and is swept at beta[slot_of[i]]; lattice_at[l*S+k] */
+/* is the lattice at slot k of ladder l.                                       */
+/*                                                                            */
+/* After sweep t, when record_every > 0 and (t + 1) % record_every == 0, event */
+/* e = (t + 1) / record_every - 1 happens: each lattice's {sum s, sum bonds}   */
+/* is recorded at trace[e - e_first][l*S + k] for the lattice at (l, k), and,  */
+/* with swaps on, adjacent slots (k, k+1), k = (e mod 2), (e mod 2) + 2, ...   */
+/* exchange their lattices with the replica-exchange probability              */
+/*   P = min(1, exp((beta[k+1] - beta[k]) (E_b - E_a))),  E = -sum bonds,      */
+/* a at slot k, b at slot k+1: the ratio of the joint Boltzmann weights after  */
+/* and before the exchange.  E_b - E_a = bonds_a - bonds_b = D is a multiple  */
+/* of 4 on a periodic lattice with even sides; for D < 0 the threshold is      */
+/*   TS = floor(2^32 exp(-x)),  x = (beta[k+1] - beta[k]) * (double)(-D)       */
+/* (2^32 when exp(-x) >= 1) and the pair swaps iff its draw u < TS, u the      */
+/* purpose-2 draw of site k in stream l at sweep t (colour 0).                 */
+/* ------------------------------------------------------------------------- */
+uint64_t oracle_swap_threshold(double beta_lo, double beta_hi, int64_t D)
+{
+    if (D >= 0) return (uint64_t)1 << 32;
+    double x = (beta_hi - beta_lo) * (double)(-D);
+    double p = exp(-x);
+    if (p >= 1.0) return (uint64_t)1 << 32;
+    return (uint64_t)floor(ldexp(p, 32));
+}
+
+int oracle_batch_run(int64_t n, const int64_t *L, int8_t *spins, int64_t S, const double *beta,
+                     int32_t *slot_of, int32_t *lattice_at, int64_t n_sweeps, uint64_t seed, uint64_t off,
+                     int64_t record_every, int swaps, int64_t *trace, int nthreads)
+{
+    if (n <= 0 || S <= 0 || n % S != 0 || n_sweeps < 0) return 1;
+    int64_t n_ladders = n / S;
+    int64_t *start = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int64_t *obs = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * n));
+    uint64_t (*T)[5] = malloc(sizeof(uint64_t[5]) * (size_t)S);
+    if (!start || !obs || !T) return 2;
+    start[0] = 0;
+    for (int64_t i = 0; i < n; i++) {
+        if (L[i] <= 0 || (L[i] & 1)) return 1;
+        start[i + 1] = start[i] + L[i] * L[i];
+    }
+    for (int64_t k = 0; k < S; k++)
+        if (oracle_thresholds(beta[k], T[k])) return 1;
+    int64_t e_first = -1;
+    for (int64_t s = 0; s < n_sweeps; s++) {
+        uint64_t t = off + (uint64_t)s;
+        for (int64_t i = 0; i < n; i++) {
+            const uint64_t *Ti = T[slot_of[i]];
+            oracle_half_sweep_stream(L[i], spins + start[i], 0, Ti, seed, t, (uint32_t)i, nthreads);
+            oracle_half_sweep_stream(L[i], spins + start[i], 1, Ti, seed, t, (uint32_t)i, nthreads);
+        }
+        if (record_every <= 0 || (t + 1) % (uint64_t)record_every != 0) continue;
+        int64_t e = (int64_t)((t + 1) / (uint64_t)record_every) - 1;
+        if (e_first < 0) e_first = e;
+        for (int64_t i = 0; i < n; i++) oracle_observables(L[i], spins + start[i], obs + 2 * i);
+        for (int64_t l = 0; l < n_ladders; l++) {
+            if (trace) {
+                for (int64_t k = 0; k < S; k++) {
+                    int64_t x = lattice_at[l * S + k];
+                    int64_t *dst = trace + 2 * ((e - e_first) * n + l * S + k);
+                    dst[0] = obs[2 * x];
+                    dst[1] = obs[2 * x + 1];
+                }
+            }
+            if (!swaps) continue;
+            for (int64_t k = e & 1; k + 1 < S; k += 2) {
+                int32_t a = lattice_at[l * S + k], b = lattice_at[l * S + k + 1];
+                int64_t D = obs[2 * a + 1] - obs[2 * b + 1];
+                uint64_t TS = oracle_swap_threshold(beta[k], beta[k + 1], D);
+                uint32_t u = oracle_draw_stream(seed, (uint32_t)l, (uint64_t)k, t, 0, 2);
+                if ((uint64_t)u < TS) {
+                    lattice_at[l * S + k] = b;
+                    lattice_at[l * S + k + 1] = a;
+                    slot_of[a] = (int32_t)(k + 1);
+                    slot_of[b] = (int32_t)k;
+                }
+            }
+        }
+    }
+    free(start);
+    free(obs);
+    free(T);
+    return 0;
 }

@@ -26,9 +26,13 @@ MUTANTS = {
     "right_bonds_only": ("        b += v * s[wrap(i + 1, L) * L + c];\n", ""),
     "wrong_plane_site": ("return (uint64_t)i * (uint64_t)(L / 2) + (uint64_t)(c / 2);",
                          "return (uint64_t)i * (uint64_t)(L / 2) + (uint64_t)(c % (L / 2));"),
+    "swap_exponent_sign": ("double p = exp(-x);", "double p = exp(x);"),
+    "swap_keeps_slot": ("                    slot_of[a] = (int32_t)(k + 1);\n", ""),
+    "stream_ignored": ("ctr[1] = (uint32_t)(q >> 32) + stream;", "ctr[1] = (uint32_t)(q >> 32);"),
 }
 
-PIN_FILES = ["tests/test_oracle_philox.py", "tests/test_oracle_rules.py", "tests/test_oracle_statistics.py"]
+PIN_FILES = ["tests/test_oracle_philox.py", "tests/test_oracle_rules.py", "tests/test_oracle_batch.py",
+             "tests/test_oracle_statistics.py"]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
