@@ -134,6 +134,84 @@ ISING_API int ising_unpack(const ising_lattice_t *msc4_src, const ising_lattice_
 ISING_API int ising_rng_probe(uint64_t n_blocks, uint64_t seed, uint64_t t, int32_t colour, uint32_t T3,
                               uint64_t *count_dev, ising_stream_t stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batches of lattices with replica exchange.  Not in the paper: the batched */
+/* form of its sweep.  n lattices (sides L[i], multiples of 32 up to 65536,  */
+/* MSC4 planes) are swept together in ONE persistent cooperative launch with */
+/* grid-wide barriers (each wait bounded: a timeout sets ISING_ETIMEOUT,     */
+/* read back by ising_batch_check).  Lattices [l*S, (l+1)*S) form ladder l   */
+/* over S increasing inverse temperatures beta[0..S-1]; lattice i starts at  */
+/* slot i mod S and is swept at the beta of its current slot.  Lattice i     */
+/* draws in stream i (i added to Philox counter word 1), so lattice 0 follows */
+/* the single-lattice trajectory for the same seed.                          */
+/*                                                                           */
+/* After sweep t with (t + 1) % record_every == 0 (event e = (t+1)/record_every */
+/* - 1): every lattice's {sum s, sum bonds} goes to trace[e - e_first][l*S+k] */
+/* for the lattice at slot k of ladder l (e_first = first event of the call) */
+/* and, with swaps on, slot pairs (k, k+1), k = e mod 2, e mod 2 + 2, ...     */
+/* exchange lattices iff u < floor(2^32 exp(-(beta[k+1]-beta[k]) m)), where  */
+/* m = bonds_b - bonds_a if that is positive (else always), a at slot k, b at */
+/* k+1, and u the purpose-2 draw of site k in stream l at sweep t: the       */
+/* replica-exchange probability min(1, exp((beta[k+1]-beta[k])(E_b - E_a))). */
+/*                                                                           */
+/* All device memory is one caller-owned workspace (ising_batch_bytes); the  */
+/* handle itself is host memory owned by the library until destroy.          */
+/* ------------------------------------------------------------------------ */
+typedef struct ising_batch ising_batch_t;
+
+/* Workspace bytes for a batch.  EINVAL: n not a multiple of S, a side not a
+ * multiple of 32 in [32, 65536], unequal sides within a ladder, betas not
+ * increasing by >= 1e-4 or not > 0. */
+ISING_API int ising_batch_bytes(int64_t n, const int64_t *L, int32_t ladder_size, const double *beta,
+                                size_t *bytes);
+
+/* Lay a batch out in `workspace_dev` (device, 256-byte aligned, at least
+ * ising_batch_bytes) and upload its tables (synchronous).  *out receives the
+ * host handle. */
+ISING_API int ising_batch_create(int64_t n, const int64_t *L, int32_t ladder_size, const double *beta,
+                                 void *workspace_dev, size_t workspace_bytes, ising_batch_t **out);
+ISING_API int ising_batch_destroy(ising_batch_t *batch);
+
+/* Initial planes (ISING_INIT_*; random: lattice i draws in stream i), identity
+ * slots, cleared accumulators and barrier. */
+ISING_API int ising_batch_init(ising_batch_t *batch, int32_t init, uint64_t seed, ising_stream_t stream);
+
+/* n_sweeps sweeps with indices sweep_offset.. in one persistent launch
+ * (replayed from a captured CUDA graph when use_graph != 0).  trace_dev
+ * (nullable) receives events x n x 2 int64 as described above.  swaps needs
+ * record_every > 0.  Asynchronous: ising_batch_check reports barrier
+ * timeouts. */
+ISING_API int ising_batch_run(ising_batch_t *batch, int64_t n_sweeps, uint64_t seed, uint64_t sweep_offset,
+                              int32_t record_every, int32_t swaps, int64_t *trace_dev, int32_t use_graph,
+                              ising_stream_t stream);
+
+/* Synchronises `stream` and returns ISING_ETIMEOUT (or EINVAL for a device-side
+ * consistency failure) if a launch of this batch reported one, clearing it. */
+ISING_API int ising_batch_check(ising_batch_t *batch, ising_stream_t stream);
+
+/* Device pointers of the concatenated planes and the word offset of each
+ * lattice's plane (host array of n + 1), and of the slot state arrays. */
+ISING_API int ising_batch_planes(const ising_batch_t *batch, void **black_dev, void **white_dev,
+                                 int64_t *word_offsets);
+ISING_API int ising_batch_state(const ising_batch_t *batch, int32_t **slot_of_dev, int32_t **lattice_at_dev);
+
+/* Launch shape: 256 or 512 threads per block, 1, 2 or 4 words per thread (per
+ * lattice the largest that divides its words per row).  Results do not depend
+ * on it.  ising_batch_autotune times every shape for n_sweeps sweeps on a copy
+ * of the planes (in the workspace) and keeps the fastest. */
+ISING_API int ising_batch_config(ising_batch_t *batch, int32_t threads, int32_t words_per_thread);
+ISING_API int ising_batch_get_config(const ising_batch_t *batch, int32_t *threads, int32_t *words_per_thread);
+ISING_API int ising_batch_autotune(ising_batch_t *batch, int64_t n_sweeps, ising_stream_t stream);
+
+/* Self-test of the bounded grid barrier: a launch on the workspace's tuning
+ * copy whose barrier waits for one block more than the grid holds, so every
+ * wait runs out after timeout_cycles SM clocks.  Returns ISING_ETIMEOUT when
+ * the kernel gave up and returned as designed. */
+ISING_API int ising_batch_barrier_selftest(ising_batch_t *batch, int64_t timeout_cycles, ising_stream_t stream);
+
+/* Text of the last batch-API failure seen by this thread. */
+ISING_API const char *ising_batch_last_error(void);
+
 /* Static description of a status code. */
 ISING_API const char *ising_strerror(int status);
 

@@ -83,7 +83,7 @@ def _load():
         lib.oracle_init_row_stream.restype = None
         lib.oracle_swap_threshold.argtypes = [ctypes.c_double, ctypes.c_double, i64]
         lib.oracle_swap_threshold.restype = u64
-        lib.oracle_batch_run.argtypes = [i64, p, p, i64, p, p, p, i64, u64, u64, i64, i32, p, i32]
+        lib.oracle_batch_run.argtypes = [i64, p, p, i64, p, p, p, i64, u64, u64, i64, i32, p, i32, i64]
         lib.oracle_batch_run.restype = i32
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = i32
@@ -244,12 +244,13 @@ class Batch:
     """n full int8 lattices with sides L[i]; ladders of S consecutive lattices
     over the inverse temperatures `beta` (S ascending values)."""
 
-    def __init__(self, L, S: int, beta, mode: int = MODE_RANDOM, seed: int = 0):
+    def __init__(self, L, S: int, beta, mode: int = MODE_RANDOM, seed: int = 0, lattice_base: int = 0):
         self.L = np.ascontiguousarray(L, dtype=np.int64)
         self.n = int(self.L.size)
         self.S = int(S)
         self.beta = np.ascontiguousarray(beta, dtype=np.float64)
-        assert self.beta.size == self.S and self.n % self.S == 0
+        self.lattice_base = int(lattice_base)
+        assert self.beta.size == self.S and self.n % self.S == 0 and self.lattice_base % self.S == 0
         self.start = np.concatenate([[0], np.cumsum(self.L * self.L)])
         self.spins = np.zeros(int(self.start[-1]), dtype=np.int8)
         for i in range(self.n):
@@ -257,7 +258,7 @@ class Batch:
             view = self.spins[self.start[i]:self.start[i + 1]].reshape(Li, Li)
             for r in range(Li):
                 row = np.zeros(Li, dtype=np.int8)
-                _load().oracle_init_row_stream(Li, r, _ptr(row), mode, seed, i)
+                _load().oracle_init_row_stream(Li, r, _ptr(row), mode, seed, self.lattice_base + i)
                 view[r] = row
         self.slot_of = (np.arange(self.n) % self.S).astype(np.int32)
         self.lattice_at = np.arange(self.n, dtype=np.int32)
@@ -277,7 +278,7 @@ class Batch:
         rc = _load().oracle_batch_run(self.n, _ptr(self.L), _ptr(self.spins), self.S, _ptr(self.beta),
                                       _ptr(self.slot_of), _ptr(self.lattice_at), n_sweeps, seed, off,
                                       record_every, int(bool(swaps)), _ptr(tr) if tr is not None else None,
-                                      nthreads)
+                                      nthreads, self.lattice_base)
         if rc != 0:
             raise ValueError("invalid batch arguments")
         return tr

@@ -375,11 +375,16 @@ uint64_t oracle_swap_threshold(double beta_lo, double beta_hi, int64_t D)
     return (uint64_t)floor(ldexp(p, 32));
 }
 
+/*
+ * lattice_base lets the oracle run a piece of a larger batch: its lattices
+ * are lattices lattice_base .. lattice_base + n - 1 of that batch (streams
+ * lattice_base + i; ladder streams lattice_base / S + l).
+ */
 int oracle_batch_run(int64_t n, const int64_t *L, int8_t *spins, int64_t S, const double *beta,
                      int32_t *slot_of, int32_t *lattice_at, int64_t n_sweeps, uint64_t seed, uint64_t off,
-                     int64_t record_every, int swaps, int64_t *trace, int nthreads)
+                     int64_t record_every, int swaps, int64_t *trace, int nthreads, int64_t lattice_base)
 {
-    if (n <= 0 || S <= 0 || n % S != 0 || n_sweeps < 0) return 1;
+    if (n <= 0 || S <= 0 || n % S != 0 || n_sweeps < 0 || lattice_base < 0 || lattice_base % S != 0) return 1;
     int64_t n_ladders = n / S;
     int64_t *start = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
     int64_t *obs = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * n));
@@ -397,8 +402,9 @@ int oracle_batch_run(int64_t n, const int64_t *L, int8_t *spins, int64_t S, cons
         uint64_t t = off + (uint64_t)s;
         for (int64_t i = 0; i < n; i++) {
             const uint64_t *Ti = T[slot_of[i]];
-            oracle_half_sweep_stream(L[i], spins + start[i], 0, Ti, seed, t, (uint32_t)i, nthreads);
-            oracle_half_sweep_stream(L[i], spins + start[i], 1, Ti, seed, t, (uint32_t)i, nthreads);
+            uint32_t stream = (uint32_t)(lattice_base + i);
+            oracle_half_sweep_stream(L[i], spins + start[i], 0, Ti, seed, t, stream, nthreads);
+            oracle_half_sweep_stream(L[i], spins + start[i], 1, Ti, seed, t, stream, nthreads);
         }
         if (record_every <= 0 || (t + 1) % (uint64_t)record_every != 0) continue;
         int64_t e = (int64_t)((t + 1) / (uint64_t)record_every) - 1;
@@ -418,7 +424,7 @@ int oracle_batch_run(int64_t n, const int64_t *L, int8_t *spins, int64_t S, cons
                 int32_t a = lattice_at[l * S + k], b = lattice_at[l * S + k + 1];
                 int64_t D = obs[2 * a + 1] - obs[2 * b + 1];
                 uint64_t TS = oracle_swap_threshold(beta[k], beta[k + 1], D);
-                uint32_t u = oracle_draw_stream(seed, (uint32_t)l, (uint64_t)k, t, 0, 2);
+                uint32_t u = oracle_draw_stream(seed, (uint32_t)(lattice_base / S + l), (uint64_t)k, t, 0, 2);
                 if ((uint64_t)u < TS) {
                     lattice_at[l * S + k] = b;
                     lattice_at[l * S + k + 1] = a;

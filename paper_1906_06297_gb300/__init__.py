@@ -78,6 +78,27 @@ def _load():
             f = getattr(lib, name)
             f.argtypes = args
             f.restype = ctypes.c_int
+        BP = ctypes.c_void_p  # opaque ising_batch_t *
+        bsig = {
+            "ising_batch_bytes": [i64, P, i32, P, P],
+            "ising_batch_create": [i64, P, i32, P, P, ctypes.c_size_t, P],
+            "ising_batch_destroy": [BP],
+            "ising_batch_init": [BP, i32, u64, P],
+            "ising_batch_run": [BP, i64, u64, u64, i32, i32, P, i32, P],
+            "ising_batch_check": [BP, P],
+            "ising_batch_planes": [BP, P, P, P],
+            "ising_batch_state": [BP, P, P],
+            "ising_batch_config": [BP, i32, i32],
+            "ising_batch_get_config": [BP, P, P],
+            "ising_batch_autotune": [BP, i64, P],
+            "ising_batch_barrier_selftest": [BP, i64, P],
+        }
+        for name, args in bsig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        lib.ising_batch_last_error.argtypes = []
+        lib.ising_batch_last_error.restype = ctypes.c_char_p
         lib.ising_strerror.argtypes = [ctypes.c_int]
         lib.ising_strerror.restype = ctypes.c_char_p
         lib.ising_last_error.argtypes = []
@@ -89,7 +110,8 @@ def _load():
 def _check(rc: int, where: str):
     if rc != ISING_OK:
         lib = _load()
-        raise IsingError(rc, where, lib.ising_last_error().decode() or lib.ising_strerror(rc).decode())
+        msg = lib.ising_batch_last_error().decode() if where.startswith("ising_batch") else ""
+        raise IsingError(rc, where, msg or lib.ising_last_error().decode() or lib.ising_strerror(rc).decode())
 
 
 def _stream(stream):
@@ -225,3 +247,109 @@ def _struct(lat) -> ising_lattice_t:
     if isinstance(lat, ising_lattice_t):
         return lat
     return lat.struct()
+
+
+# ---------------------------------------------------------------------------
+# Batches with replica exchange
+# ---------------------------------------------------------------------------
+def ising_batch_bytes(L, ladder_size: int, beta) -> int:
+    import numpy as np
+
+    Ls = np.ascontiguousarray(L, dtype=np.int64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    out = ctypes.c_size_t()
+    _check(_load().ising_batch_bytes(Ls.size, Ls.ctypes.data, ladder_size, b.ctypes.data, ctypes.byref(out)),
+           "ising_batch_bytes")
+    return out.value
+
+
+class Batch:
+    """n lattices (sides L[i]) in one device workspace owned by PyTorch; the
+    ladders are S consecutive lattices over the S inverse temperatures `beta`."""
+
+    def __init__(self, L, ladder_size: int, beta, device="cuda"):
+        import numpy as np
+        import torch
+
+        self.L = np.ascontiguousarray(L, dtype=np.int64)
+        self.n = int(self.L.size)
+        self.S = int(ladder_size)
+        self.beta = np.ascontiguousarray(beta, dtype=np.float64)
+        nbytes = ising_batch_bytes(self.L, self.S, self.beta)
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        h = ctypes.c_void_p()
+        _check(_load().ising_batch_create(self.n, self.L.ctypes.data, self.S, self.beta.ctypes.data,
+                                          self.ws.data_ptr(), nbytes, ctypes.byref(h)), "ising_batch_create")
+        self.handle = h
+        black, white = ctypes.c_void_p(), ctypes.c_void_p()
+        self.word_off = np.zeros(self.n + 1, dtype=np.int64)
+        _check(_load().ising_batch_planes(h, ctypes.byref(black), ctypes.byref(white), self.word_off.ctypes.data),
+               "ising_batch_planes")
+        self._black_off = black.value - self.ws.data_ptr()
+        self._white_off = white.value - self.ws.data_ptr()
+        slot, at = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(_load().ising_batch_state(h, ctypes.byref(slot), ctypes.byref(at)), "ising_batch_state")
+        self._slot_off = slot.value - self.ws.data_ptr()
+        self._at_off = at.value - self.ws.data_ptr()
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.ising_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, init: int = ISING_INIT_RANDOM, seed: int = 0, stream=None):
+        _check(_load().ising_batch_init(self.handle, init, seed, _stream(stream)), "ising_batch_init")
+
+    def run(self, n_sweeps: int, seed: int, offset: int = 0, record_every: int = 0, swaps: bool = False,
+            trace=None, use_graph: bool = True, stream=None):
+        _check(_load().ising_batch_run(self.handle, n_sweeps, seed, offset, record_every, int(bool(swaps)),
+                                       _addr(trace), int(bool(use_graph)), _stream(stream)), "ising_batch_run")
+
+    def check(self, stream=None):
+        _check(_load().ising_batch_check(self.handle, _stream(stream)), "ising_batch_check")
+
+    def config(self, threads: int, words_per_thread: int):
+        _check(_load().ising_batch_config(self.handle, threads, words_per_thread), "ising_batch_config")
+
+    def get_config(self):
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(_load().ising_batch_get_config(self.handle, ctypes.byref(a), ctypes.byref(b)), "ising_batch_get_config")
+        return a.value, b.value
+
+    def autotune(self, n_sweeps: int = 3, stream=None):
+        _check(_load().ising_batch_autotune(self.handle, n_sweeps, _stream(stream)), "ising_batch_autotune")
+        return self.get_config()
+
+    def barrier_selftest(self, timeout_cycles: int, stream=None) -> int:
+        """Runs the bounded-barrier self-test; returns its status code."""
+        return int(_load().ising_batch_barrier_selftest(self.handle, timeout_cycles, _stream(stream)))
+
+    def n_events(self, n_sweeps: int, offset: int, record_every: int) -> int:
+        if record_every <= 0:
+            return 0
+        return (offset + n_sweeps) // record_every - offset // record_every
+
+    def planes_numpy(self, i: int):
+        """Host copies of lattice i's black and white planes (uint64 words)."""
+        import numpy as np
+
+        words = int(self.word_off[i + 1] - self.word_off[i])
+        out = []
+        for off in (self._black_off, self._white_off):
+            a = off + 8 * int(self.word_off[i])
+            out.append(np.ascontiguousarray(self.ws[a:a + 8 * words].cpu().numpy()).view(np.uint64)
+                       .reshape(int(self.L[i]), int(self.L[i]) // 32))
+        return out
+
+    def state_numpy(self):
+        import numpy as np
+
+        slot = np.ascontiguousarray(self.ws[self._slot_off:self._slot_off + 4 * self.n].cpu().numpy()).view(np.int32)
+        at = np.ascontiguousarray(self.ws[self._at_off:self._at_off + 4 * self.n].cpu().numpy()).view(np.int32)
+        return slot.copy(), at.copy()

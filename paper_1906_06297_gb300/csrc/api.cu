@@ -25,6 +25,7 @@ namespace {
 
 thread_local char g_last_error[256] = "";
 
+
 int fail(int status, const char *fmt, ...)
 {
     va_list ap;
@@ -44,54 +45,6 @@ struct DeviceCache {
     int sm_count[64] = {};
 };
 DeviceCache g_dev;
-
-typedef CUresult (*AddressRangeFn)(CUdeviceptr *base, size_t *size, CUdeviceptr ptr);
-
-AddressRangeFn address_range_fn()
-{
-    static AddressRangeFn fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<AddressRangeFn>(p);
-    });
-    return fn;
-}
-
-// ptr must be device (or managed) memory usable by the current device, with
-// [ptr, ptr + bytes) inside one allocation.
-int check_device_range(const void *ptr, size_t bytes, const char *name)
-{
-    if (ptr == nullptr) return fail(ISING_EINVAL, "%s is NULL", name);
-    cudaPointerAttributes at;
-    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(ISING_EINVAL, "%s is not a CUDA pointer (%s)", name, cudaGetErrorString(e));
-    }
-    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
-        return fail(ISING_EINVAL, "%s is not device memory", name);
-    int dev = -1;
-    cudaGetDevice(&dev);
-    if (at.type == cudaMemoryTypeDevice && at.device != dev)
-        return fail(ISING_EINVAL, "%s lives on device %d, current device is %d", name, at.device, dev);
-    AddressRangeFn fn = address_range_fn();
-    if (fn != nullptr) {
-        CUdeviceptr base = 0;
-        size_t size = 0;
-        if (fn(&base, &size, (CUdeviceptr)ptr) == CUDA_SUCCESS) {
-            const size_t off = (size_t)((CUdeviceptr)ptr - base);
-            if (off > size || size - off < bytes)
-                return fail(ISING_EINVAL, "%s: %zu bytes needed, allocation has %zu past the pointer", name, bytes,
-                            size - off);
-        }
-    }
-    return ISING_OK;
-}
 
 int row_bytes_of(int64_t L, int32_t layout, size_t *row)
 {
@@ -190,6 +143,55 @@ int half_sweep_impl(const ising_lattice_t *lat, const Accept &acc, const RoundKe
 }
 
 }  // namespace
+
+typedef CUresult (*AddressRangeFn)(CUdeviceptr *base, size_t *size, CUdeviceptr ptr);
+
+AddressRangeFn address_range_fn()
+{
+    static AddressRangeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<AddressRangeFn>(p);
+    });
+    return fn;
+}
+
+// ptr must be device (or managed) memory usable by the current device, with
+// [ptr, ptr + bytes) inside one allocation.
+int check_device_range(const void *ptr, size_t bytes, const char *name)
+{
+    if (ptr == nullptr) return fail(ISING_EINVAL, "%s is NULL", name);
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ISING_EINVAL, "%s is not a CUDA pointer (%s)", name, cudaGetErrorString(e));
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(ISING_EINVAL, "%s is not device memory", name);
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (at.type == cudaMemoryTypeDevice && at.device != dev)
+        return fail(ISING_EINVAL, "%s lives on device %d, current device is %d", name, at.device, dev);
+    AddressRangeFn fn = address_range_fn();
+    if (fn != nullptr) {
+        CUdeviceptr base = 0;
+        size_t size = 0;
+        if (fn(&base, &size, (CUdeviceptr)ptr) == CUDA_SUCCESS) {
+            const size_t off = (size_t)((CUdeviceptr)ptr - base);
+            if (off > size || size - off < bytes)
+                return fail(ISING_EINVAL, "%s: %zu bytes needed, allocation has %zu past the pointer", name, bytes,
+                            size - off);
+        }
+    }
+    return ISING_OK;
+}
+
 
 cudaError_t device_info(DeviceInfo *info)
 {

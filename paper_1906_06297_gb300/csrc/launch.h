@@ -36,6 +36,10 @@ cudaError_t int8_observables(const int8_t *black, const int8_t *white, int64_t L
 cudaError_t rng_probe(uint64_t n_blocks, const RoundKeys &rk, uint32_t c2, uint32_t c3, uint32_t T3,
                       unsigned long long *count, cudaStream_t s);
 
+// ISING_OK if [ptr, ptr + bytes) is device memory of the current device inside
+// one allocation; else ISING_EINVAL with the reason in ising_last_error().
+int check_device_range(const void *ptr, size_t bytes, const char *name);
+
 // Cached per-device facts (SM count), for the device current on this thread.
 cudaError_t device_info(DeviceInfo *info);
 
