@@ -209,6 +209,31 @@ ISING_API int ising_batch_autotune(ising_batch_t *batch, int64_t n_sweeps, ising
  * the kernel gave up and returned as designed. */
 ISING_API int ising_batch_barrier_selftest(ising_batch_t *batch, int64_t timeout_cycles, ising_stream_t stream);
 
+/* Allocation-free form of ising_batch_run.  The paper has no counterpart.
+ * For callers that may not allocate device memory themselves (code running
+ * under another framework's memory manager, which owns the device budget and
+ * does not let plug-ins call cudaMalloc; latency-bound loops where an
+ * allocation could synchronise the device): the batch is described by its
+ * arrays as in ising_batch_bytes, the caller passes the planes (black_dev,
+ * white_dev: the concatenated MSC4 planes laid out as ising_batch_planes
+ * reports, lattice i at word offset sum_{j<i} L_j^2/32), the slot state
+ * (slot_of_dev, lattice_at_dev: n int32 each, e.g. the identity slot i mod S
+ * and lattice i), and an optional trace; all other scratch (tables,
+ * accumulators, barrier words) lives in a fixed 4 MiB array inside the
+ * library, which every GPU that loads the library holds until exit.  Batches
+ * whose scratch exceeds it are rejected with ISING_EINVAL and a message
+ * giving the size.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Calls share the array: calls that overlap on
+ * the GPU race.  Each call clears what must start at zero.  Synchronous:
+ * returns after the sweeps, with ISING_ETIMEOUT if a barrier wait ran out.
+ * Results equal ising_batch_run's for the same arguments. */
+ISING_API int ising_batch_run_noalloc(int64_t n, const int64_t *L, int32_t ladder_size, const double *beta,
+                                      void *black_dev, void *white_dev, int32_t *slot_of_dev,
+                                      int32_t *lattice_at_dev, int64_t n_sweeps, uint64_t seed,
+                                      uint64_t sweep_offset, int32_t record_every, int32_t swaps,
+                                      int64_t *trace_dev, ising_stream_t stream);
+
 /* Text of the last batch-API failure seen by this thread. */
 ISING_API const char *ising_batch_last_error(void);
 

@@ -92,6 +92,7 @@ def _load():
             "ising_batch_get_config": [BP, P, P],
             "ising_batch_autotune": [BP, i64, P],
             "ising_batch_barrier_selftest": [BP, i64, P],
+            "ising_batch_run_noalloc": [i64, P, i32, P, P, P, P, P, i64, u64, u64, i32, i32, P, P],
         }
         for name, args in bsig.items():
             f = getattr(lib, name)
@@ -353,3 +354,19 @@ class Batch:
         slot = np.ascontiguousarray(self.ws[self._slot_off:self._slot_off + 4 * self.n].cpu().numpy()).view(np.int32)
         at = np.ascontiguousarray(self.ws[self._at_off:self._at_off + 4 * self.n].cpu().numpy()).view(np.int32)
         return slot.copy(), at.copy()
+
+
+def ising_batch_run_noalloc(L, ladder_size: int, beta, black, white, slot_of, lattice_at, n_sweeps: int, seed: int,
+                            sweep_offset: int = 0, record_every: int = 0, swaps: bool = False, trace=None,
+                            stream=None):
+    """Allocation-free batched run (see include/ising.h): the caller passes the
+    planes, the slot state and the trace; the library's fixed scratch array
+    holds everything else.  Synchronous."""
+    import numpy as np
+
+    Ls = np.ascontiguousarray(L, dtype=np.int64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    _check(_load().ising_batch_run_noalloc(Ls.size, Ls.ctypes.data, ladder_size, b.ctypes.data, _addr(black),
+                                           _addr(white), _addr(slot_of), _addr(lattice_at), n_sweeps, seed,
+                                           sweep_offset, record_every, int(bool(swaps)), _addr(trace),
+                                           _stream(stream)), "ising_batch_run_noalloc")

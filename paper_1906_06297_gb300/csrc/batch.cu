@@ -38,6 +38,9 @@
 #include "launch.h"
 #include "sweep_core.cuh"
 
+// Size of the fixed scratch array of ising_batch_run_noalloc (4 MiB).
+#define ISING_NOALLOC_SCRATCH_BYTES (4u << 20)
+
 namespace ising {
 
 namespace {
@@ -856,3 +859,169 @@ ISING_API int ising_batch_barrier_selftest(ising_batch_t *b, int64_t timeout_cyc
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free batched run.
+//
+// For callers that must not allocate device memory themselves -- for example
+// code running under another framework's memory manager, which owns the
+// device budget and does not let plug-ins call cudaMalloc, or a latency-bound
+// loop where an allocation could synchronise the device -- this entry point
+// keeps the batch kernel's scratch (threshold tables, exchange tables,
+// per-lattice accumulators, barrier words) in the fixed array below instead
+// of a caller-provided workspace.  Every GPU that loads the library holds the
+// array until the process exits.  Its address is looked up once per device
+// (cudaGetSymbolAddress, with that device current) by the first call on the
+// device.  All calls share the array, so calls that overlap on the GPU race;
+// each call clears what must start at zero (accumulators, barrier words).
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[ISING_NOALLOC_SCRATCH_BYTES];
+
+namespace ising {
+namespace {
+
+struct NoallocScratch {
+    std::mutex mu;
+    void *addr[64] = {};
+};
+NoallocScratch g_noalloc;
+
+int noalloc_scratch(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return bfail(ISING_ECUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64) return bfail(ISING_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc.mu);
+    if (g_noalloc.addr[dev] == nullptr) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) return bfail(ISING_ECUDA, "cudaGetSymbolAddress of the scratch failed");
+        g_noalloc.addr[dev] = p;
+    }
+    *out = g_noalloc.addr[dev];
+    return ISING_OK;
+}
+
+}  // namespace
+}  // namespace ising
+
+extern "C" ISING_API int ising_batch_run_noalloc(int64_t n, const int64_t *L, int32_t ladder_size, const double *beta,
+                                                 void *black_dev, void *white_dev, int32_t *slot_of_dev,
+                                                 int32_t *lattice_at_dev, int64_t n_sweeps, uint64_t seed,
+                                                 uint64_t sweep_offset, int32_t record_every, int32_t swaps,
+                                                 int64_t *trace_dev, ising_stream_t stream)
+{
+    int rc = check_batch_args(n, L, ladder_size, beta);
+    if (rc) return rc;
+    if (n_sweeps < 0 || record_every < 0) return bfail(ISING_EINVAL, "bad batch run arguments");
+    if (swaps && record_every == 0) return bfail(ISING_EINVAL, "exchanges happen on record sweeps: set record_every");
+    // host-side layout of the planes (the same as ising_batch_create's)
+    ising_batch_t lay;
+    lay.n = n;
+    lay.S = ladder_size;
+    lay.L.assign(L, L + n);
+    lay.beta.assign(beta, beta + ladder_size);
+    layout(&lay);
+    // scratch layout inside the fixed array
+    std::vector<uint32_t> thr(2 * (size_t)ladder_size);
+    for (int k = 0; k < ladder_size; ++k) {
+        uint64_t T[5];
+        ising_thresholds(beta[k], T);
+        thr[2 * k] = (uint32_t)T[3];
+        thr[2 * k + 1] = (uint32_t)T[4];
+    }
+    std::vector<uint64_t> tab;
+    std::vector<int64_t> len;
+    swap_tables(lay.beta, len, &tab);
+    std::vector<int64_t> off(len.size());
+    int64_t o_acc_tab = 0;
+    for (size_t k = 0; k < len.size(); ++k) {
+        off[k] = o_acc_tab;
+        o_acc_tab += len[k];
+    }
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align256(o + bytes);
+        return at;
+    };
+    const size_t s_thr = take(thr.size() * 4), s_off = take(std::max<size_t>(1, off.size()) * 8),
+                 s_len = take(std::max<size_t>(1, len.size()) * 8), s_tab = take(std::max<size_t>(1, tab.size()) * 8),
+                 s_acc = take((size_t)n * 16), s_bar = take(64);
+    if (o > (size_t)ISING_NOALLOC_SCRATCH_BYTES) {
+        char msg[160];
+        snprintf(msg, sizeof(msg), "needs %zu bytes of scratch; the allocation-free entry point holds %zu",
+                 o, (size_t)ISING_NOALLOC_SCRATCH_BYTES);
+        return bfail(ISING_EINVAL, msg);
+    }
+    // the caller's buffers must cover what the kernel touches
+    const size_t plane = lay.plane_words * 8;
+    if (check_device_range(black_dev, plane, "black") || check_device_range(white_dev, plane, "white") ||
+        check_device_range(slot_of_dev, (size_t)n * 4, "slot_of") ||
+        check_device_range(lattice_at_dev, (size_t)n * 4, "lattice_at"))
+        return bfail(ISING_EINVAL, "planes and slot arrays must be device memory of the batch's sizes");
+    if (trace_dev != nullptr && record_every > 0) {
+        const int64_t events = (int64_t)((sweep_offset + (uint64_t)n_sweeps) / (uint64_t)record_every) -
+                               (int64_t)(sweep_offset / (uint64_t)record_every);
+        if (events > 0 && check_device_range(trace_dev, (size_t)events * (size_t)n * 16, "trace") != ISING_OK)
+            return bfail(ISING_EINVAL, "trace must be device memory of events x n x 2 int64");
+    }
+    void *scr = nullptr;
+    rc = noalloc_scratch(&scr);
+    if (rc) return rc;
+    char *sc = (char *)scr;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(sc + s_thr, thr.data(), thr.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !len.empty())
+        e = cudaMemcpyAsync(sc + s_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !len.empty())
+        e = cudaMemcpyAsync(sc + s_len, len.data(), len.size() * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !tab.empty())
+        e = cudaMemcpyAsync(sc + s_tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc + s_acc, 0, (s_bar + 64) - s_acc, s);
+    if (e != cudaSuccess) return bfail(ISING_ECUDA, cudaGetErrorString(e));
+
+    BatchParams p;
+    memset(&p, 0, sizeof(p));
+    p.black = (uint64_t *)black_dev;
+    p.white = (uint64_t *)white_dev;
+    rc = build_groups(&lay, 4, p);
+    if (rc) return rc;
+    p.S = ladder_size;
+    p.n = n;
+    p.n_ladders = n / ladder_size;
+    p.slot_of = slot_of_dev;
+    p.lattice_at = lattice_at_dev;
+    p.thr = (const uint32_t *)(sc + s_thr);
+    p.swap_off = (const int64_t *)(sc + s_off);
+    p.swap_len = (const int64_t *)(sc + s_len);
+    p.swap_tab = (const uint64_t *)(sc + s_tab);
+    p.acc = (long long *)(sc + s_acc);
+    p.bar = (unsigned *)(sc + s_bar);
+    p.err = (int *)(sc + s_bar + 16);
+    p.n_sweeps = n_sweeps;
+    p.t0 = sweep_offset;
+    p.record_every = record_every;
+    p.swaps = swaps;
+    p.trace = (long long *)trace_dev;
+    p.event_first = record_every > 0 ? (int64_t)(sweep_offset / (uint64_t)record_every) : 0;
+    p.rk = make_round_keys(seed);
+    p.timeout_cycles = (long long)4e9;
+    int blocks = 0;
+    rc = blocks_for(512, &blocks);
+    if (rc) return rc;
+    p.expect_blocks = blocks;
+    if (n_sweeps > 0) {
+        e = launch_coop(p, blocks, 512, s);
+        if (e != cudaSuccess) return bfail(ISING_ECUDA, cudaGetErrorString(e));
+    }
+    // synchronous: report a timed-out barrier wait before returning
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bfail(ISING_ECUDA, cudaGetErrorString(e));
+    int err = 0;
+    e = cudaMemcpy(&err, sc + s_bar + 16, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bfail(ISING_ECUDA, cudaGetErrorString(e));
+    if (err != 0) return bfail(err, err == ISING_ETIMEOUT ? "a grid barrier wait timed out" : "device-side check failed");
+    return ISING_OK;
+}
