@@ -48,6 +48,10 @@ def parse_args(argv=None):
     p.add_argument("--cpu-L", type=int, default=8192, help="oracle sample lattice side")
     p.add_argument("--cpu-sweeps", type=int, default=10, help="oracle sample sweeps")
     p.add_argument("--no-extras", action="store_true", help="skip per-beta, rng probe, e2e and cpu legs")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched parallel-tempering leg")
+    p.add_argument("--pt-sweeps", type=int, default=10000)
+    p.add_argument("--workload", choices=["sweep", "pt"], default="sweep",
+                   help="sweep: the 65536^2 lattice (default); pt: only the batched parallel-tempering leg")
     return p.parse_args(argv)
 
 
@@ -298,6 +302,8 @@ def run_ours(args, world, rank, local):
         result["rng_probe"] = rng_probe(ising, torch, L, seed, stream)
         result["e2e"] = run_e2e(ising, torch, args, L, beta, seed, device, stream)
         result["cpu_baseline"] = cpu_baseline(args)
+        if not args.no_batch:
+            result["pt_batch"] = run_pt_batch(ising, torch, args, device, stream)
     if world > 1:
         import torch.distributed as dist
 
@@ -351,6 +357,126 @@ def run_e2e(ising, torch, args, L, beta, seed, device, stream):
     plane = dev.row_bytes * L
     return {"value": round(L * L * steps / (ms * 1e6), 3), "unit": UNIT, "h2d_bytes_per_step": 2 * plane,
             "d2h_bytes_per_step": 2 * plane + 16, "steps": steps, "ms_per_step": round(ms / steps, 3)}
+
+
+def run_pt_batch(ising, torch, args, device, stream):
+    """The batched form: 4096 lattices (sides 32..1024, 8:8:4:2:1:1) in 64
+    ladders of 64 temperatures in [0.30, 0.60], exchanges every 10 sweeps,
+    all sweeps in one persistent launch replayed from a captured graph.
+    Compared with looping the one-byte-per-spin single-lattice kernel over the
+    same lattices, and, at the temperature nearest beta_c, effective samples
+    per second of the side-32 ladders against the same lattices swept without
+    exchanges."""
+    import numpy as np
+
+    from paper_1906_06297_gb300 import analysis, workloads
+
+    L, S, beta = workloads.pt_batch()
+    spins = int(sum(x * x for x in L))
+    seed, every, warm = args.seed, 10, 20
+    b = ising.Batch(L, S, beta, device=device)
+    b.init(ising.ISING_INIT_RANDOM, seed, stream)
+    threads, wpt = b.autotune(2, stream)
+    b.run(warm, seed, 0, every, True, None, True, stream)
+    b.check(stream)
+    sweeps = args.pt_sweeps
+    n_ev = b.n_events(sweeps, warm, every)
+    tr = torch.zeros((n_ev, len(L), 2), dtype=torch.int64, device=device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        b.run(sweeps, seed, warm, every, True, tr, True, stream)
+        e1.record(stream)
+    b.check(stream)
+    ms = e0.elapsed_time(e1)
+    out = {"workload": f"{len(L)} lattices, sides {sorted(set(L))}, ladders of {S} betas in [0.30, 0.60], "
+                       f"exchange every {every} sweeps, {sweeps} sweeps in one persistent launch (graph)",
+           "spins": spins, "sweeps": sweeps, "ms": round(ms, 2), "flips_per_ns": round(spins * sweeps / (ms * 1e6), 1),
+           "autotuned": {"threads": threads, "words_per_thread": wpt}, "gpu_launches": 1}
+    del tr, b
+    # looping the single-lattice one-byte-per-spin kernel over the same lattices
+    lats = [ising.Lattice(x, "int8", device=device) for x in L]
+    for i, lat in enumerate(lats):
+        ising.ising_init_lattice(lat, ising.ISING_INIT_RANDOM, seed + i, stream)
+    loop_sweeps = 2
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for i, lat in enumerate(lats):
+            ising.ising_sweep(lat, float(beta[i % S]), loop_sweeps, seed + i, 0, None, stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = e0.elapsed_time(e1)
+    out["loop_int8_per_lattice"] = {"flips_per_ns": round(spins * loop_sweeps / (loop_ms * 1e6), 2),
+                                    "gpu_launches": 2 * loop_sweeps * len(L)}
+    out["speedup_vs_loop"] = round(out["flips_per_ns"] / out["loop_int8_per_lattice"]["flips_per_ns"], 1)
+    del lats
+    # effective samples at the temperature nearest beta_c, side-32 ladders
+    k = int(np.argmin(np.abs(beta - 0.5 * np.log(1 + np.sqrt(2)))))
+    n32 = sum(1 for x in L if x == 32)
+    L32 = [32] * n32
+    ess = {}
+    for name, ladder_S, betas, swaps in (("exchange", S, beta, True), ("plain", 1, [float(beta[k])], False)):
+        bb = ising.Batch(L32, ladder_S, betas, device=device)
+        bb.init(ising.ISING_INIT_RANDOM, seed, stream)
+        bb.run(2000, seed, 0, every, swaps, None, True, stream)  # equilibration
+        nev = bb.n_events(sweeps, 2000, every)
+        tr = torch.zeros((nev, n32, 2), dtype=torch.int64, device=device)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            bb.run(sweeps, seed, 2000, every, swaps, tr, True, stream)
+            e1.record(stream)
+        bb.check(stream)
+        t_ms = e0.elapsed_time(e1)
+        h = tr.cpu().numpy()
+        cols = range(k, n32, S) if name == "exchange" else range(n32)
+        m = [np.abs(h[:, c, 0]) / 1024.0 for c in cols]
+        e = [-h[:, c, 1] / 1024.0 for c in cols]
+        em, ee = analysis.effective_samples(m), analysis.effective_samples(e)
+        ess[name] = {"beta": round(float(beta[k]), 5), "chains_at_beta": len(m), "ms": round(t_ms, 2),
+                     "tau_abs_m_sweeps": round(em["tau_int"] * every, 1), "tau_e_sweeps": round(ee["tau_int"] * every, 1),
+                     "ess_per_s_abs_m": round(em["effective"] / (t_ms * 1e-3), 1),
+                     "ess_per_s_e": round(ee["effective"] / (t_ms * 1e-3), 1),
+                     "mean_abs_m": round(float(np.mean(np.concatenate(m))), 5)}
+        del bb, tr
+    out["ess_side32_near_beta_c"] = ess
+    return out
+
+
+def run_pt_only(args, world, rank, local):
+    """Only the batched leg (one timed persistent launch of --pt-sweeps sweeps;
+    with --no-extras no loop or effective-sample runs): used for profiling."""
+    import torch
+
+    import paper_1906_06297_gb300 as ising
+    from paper_1906_06297_gb300 import workloads
+
+    ising.build()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=device)
+    if args.no_extras:
+        L, S, beta = workloads.pt_batch()
+        b = ising.Batch(L, S, beta, device=device)
+        b.init(ising.ISING_INIT_RANDOM, args.seed, stream)
+        tuned = b.autotune(2, stream)
+        b.run(10, args.seed, 0, 10, True, None, True, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            b.run(args.pt_sweeps, args.seed, 10, 10, True, None, True, stream)
+            e1.record(stream)
+        b.check(stream)
+        ms = e0.elapsed_time(e1)
+        spins = int(sum(x * x for x in L))
+        pt = {"spins": spins, "sweeps": args.pt_sweeps, "ms": round(ms, 3),
+              "flips_per_ns": round(spins * args.pt_sweeps / (ms * 1e6), 1),
+              "autotuned": {"threads": tuned[0], "words_per_thread": tuned[1]}}
+    else:
+        pt = run_pt_batch(ising, torch, args, device, stream)
+    return {"metric": METRIC, "value": pt["flips_per_ns"], "unit": UNIT, "n_gpus": world, "impl": "ours",
+            "config": {"workload": "parallel-tempering batch (4096 lattices, 64 ladders x 64 betas)"},
+            "pt_batch": pt}
 
 
 def cpu_baseline(args):
@@ -407,6 +533,8 @@ def main(argv=None):
     world, rank, local = dist_env()
     if args.impl == "reference":
         res = run_reference(args, world, rank)
+    elif args.workload == "pt":
+        res = run_pt_only(args, world, rank, local)
     else:
         res = run_ours(args, world, rank, local)
     if rank == 0 and res is not None:

@@ -53,7 +53,9 @@ struct BatchGroup {
     int64_t word_base;    // word offset of the first lattice's plane
     int64_t chunk_begin;  // first chunk (32 items) of the group
     int64_t items;        // items per lattice = L * wpr / wpt
+    int64_t weight_begin; // cumulative work weight of the groups before this one
     int32_t L, wpr, wpt, gpr;  // side, words per row, words per item, items per row
+    int32_t weight;       // work weight of one chunk: wpt + kappa
 };
 
 struct BatchParams {
@@ -64,6 +66,8 @@ struct BatchParams {
     int64_t n;            // lattices
     int64_t n_ladders;
     int64_t n_chunks;
+    int64_t plane_words;  // words of one colour plane over all lattices
+    int64_t total_weight; // sum of the chunk weights
     int32_t *slot_of;     // [n] slot of each lattice
     int32_t *lattice_at;  // [n_ladders * S] lattice at each (ladder, slot)
     const uint32_t *thr;  // [S][2] (T3, T4) of each slot's beta
@@ -164,16 +168,25 @@ __device__ __forceinline__ void sweep_item(const uint64_t *__restrict__ src, uin
     if (OBS) dsum += (dacc & 0xFFu) + ((dacc >> 8) & 0xFFu) + ((dacc >> 16) & 0xFFu) + (dacc >> 24);
 }
 
-// One half-sweep of every lattice.  Warp gw owns the contiguous chunk range
-// [gw * n_chunks / nw, (gw + 1) * n_chunks / nw); observables are flushed with
-// one pair of atomics whenever the warp moves to another lattice.
+// One half-sweep of every lattice.  Each chunk carries a work weight wpt +
+// kappa (its words plus a fixed per-chunk cost, kappa chosen by the
+// autotuner); warp gw owns the contiguous chunks whose starting weight lies in
+// [gw * W / nw, (gw + 1) * W / nw) of the total W.  Observables are flushed
+// with one pair of atomics whenever the warp moves to another lattice.
 template <bool OBS>
 __device__ void batch_half(const BatchParams &p, int colour, uint64_t t)
 {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t cb = gw * p.n_chunks / nw, ce = (gw + 1) * p.n_chunks / nw;
+    auto chunk_at = [&](int64_t w) -> int64_t {
+        if (w >= p.total_weight) return p.n_chunks;
+        int g = 0;
+        while (g + 1 < p.n_groups && p.g[g + 1].weight_begin <= w) ++g;
+        const int64_t per = p.g[g].weight;
+        return p.g[g].chunk_begin + (w - p.g[g].weight_begin + per - 1) / per;
+    };
+    const int64_t cb = chunk_at(gw * p.total_weight / nw), ce = chunk_at((gw + 1) * p.total_weight / nw);
     const uint64_t *src = colour == 0 ? p.white : p.black;
     uint64_t *tgt = colour == 0 ? p.black : p.white;
     DrawCtx dc{(uint32_t)t, counter_word3(colour, kPurposeMetropolis, t), 0u, 0u, 0u};
@@ -372,6 +385,7 @@ struct ising_batch {
     std::vector<int64_t> swap_len;
     int32_t threads = 512;
     int32_t wpt_max = 4;
+    int32_t kappa = 4;
     int device = 0;
     // captured graph of the persistent launch
     cudaGraph_t graph = nullptr;
@@ -442,10 +456,10 @@ int layout(ising_batch_t *b)
     return ISING_OK;
 }
 
-int build_groups(const ising_batch_t *b, int wpt_max, BatchParams &p)
+int build_groups(const ising_batch_t *b, int wpt_max, int kappa, BatchParams &p)
 {
     int ng = 0;
-    int64_t chunk = 0;
+    int64_t chunk = 0, weight = 0;
     for (int64_t i = 0; i < b->n;) {
         int64_t j = i;
         while (j < b->n && b->L[j] == b->L[i]) ++j;
@@ -466,11 +480,16 @@ int build_groups(const ising_batch_t *b, int wpt_max, BatchParams &p)
         G.gpr = G.wpr / G.wpt;
         G.items = (int64_t)G.L * G.gpr;
         G.chunk_begin = chunk;
+        G.weight = G.wpt + kappa;
+        G.weight_begin = weight;
         chunk += G.count * G.items / 32;
+        weight += G.count * G.items / 32 * G.weight;
         i = j;
     }
     p.n_groups = ng;
     p.n_chunks = chunk;
+    p.plane_words = b->word_off[b->n];
+    p.total_weight = weight;
     return ISING_OK;
 }
 
@@ -657,7 +676,7 @@ ISING_API int ising_batch_init(ising_batch_t *b, int32_t init, uint64_t seed, is
     if (b == nullptr) return bfail(ISING_EINVAL, "NULL batch");
     if (init < ISING_INIT_RANDOM || init > ISING_INIT_DOWN) return bfail(ISING_EINVAL, "unknown init mode");
     BatchParams p = base_params(b);
-    int rc = build_groups(b, b->wpt_max, p);
+    int rc = build_groups(b, b->wpt_max, b->kappa, p);
     if (rc) return rc;
     p.rk = make_round_keys(seed);
     cudaStream_t s = (cudaStream_t)stream;
@@ -679,7 +698,7 @@ static int run_impl(ising_batch_t *b, uint64_t *black, uint64_t *white, int64_t 
         p.black = black;
         p.white = white;
     }
-    int rc = build_groups(b, b->wpt_max, p);
+    int rc = build_groups(b, b->wpt_max, b->kappa, p);
     if (rc) return rc;
     p.n_sweeps = n_sweeps;
     p.t0 = off;
@@ -802,6 +821,7 @@ ISING_API int ising_batch_autotune(ising_batch_t *b, int64_t n_sweeps, ising_str
     cudaEventCreate(&e1);
     float best = 1e30f;
     int32_t bt = b->threads, bw = b->wpt_max;
+    b->kappa = 1 << 20;  // chunk-count split while tuning the shape
     const int32_t threads_c[2] = {256, 512}, wpt_c[3] = {1, 2, 4};
     for (int32_t th : threads_c) {
         for (int32_t w : wpt_c) {
@@ -825,10 +845,30 @@ ISING_API int ising_batch_autotune(ising_batch_t *b, int64_t n_sweeps, ising_str
             }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     b->threads = bt;
     b->wpt_max = bw;
+    // then the per-chunk weight of the work split
+    int32_t bk = b->kappa;
+    for (int32_t kap : {0, 1, 2, 4, 8, 1 << 20}) {
+        b->kappa = kap;
+        int rc = run_impl(b, tb, tw, 1, 0x5eed, 0, 0, 0, nullptr, 0, s);
+        if (rc == ISING_OK) {
+            cudaEventRecord(e0, s);
+            rc = run_impl(b, tb, tw, n_sweeps, 0x5eed, 1, 0, 0, nullptr, 0, s);
+            cudaEventRecord(e1, s);
+        }
+        if (rc != ISING_OK) continue;
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            bk = kap;
+        }
+    }
+    b->kappa = bk;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     return best < 1e30f ? ISING_OK : bfail(ISING_ECUDA, "no autotune candidate ran");
 }
 
@@ -839,7 +879,7 @@ ISING_API int ising_batch_barrier_selftest(ising_batch_t *b, int64_t timeout_cyc
 {
     if (b == nullptr || timeout_cycles <= 0) return bfail(ISING_EINVAL, "bad self-test arguments");
     BatchParams p = base_params(b);
-    int rc = build_groups(b, b->wpt_max, p);
+    int rc = build_groups(b, b->wpt_max, b->kappa, p);
     if (rc) return rc;
     int blocks = 0;
     rc = blocks_for(b->threads, &blocks);
@@ -986,7 +1026,7 @@ extern "C" ISING_API int ising_batch_run_noalloc(int64_t n, const int64_t *L, in
     memset(&p, 0, sizeof(p));
     p.black = (uint64_t *)black_dev;
     p.white = (uint64_t *)white_dev;
-    rc = build_groups(&lay, 4, p);
+    rc = build_groups(&lay, 4, 4, p);
     if (rc) return rc;
     p.S = ladder_size;
     p.n = n;

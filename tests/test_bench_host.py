@@ -49,3 +49,23 @@ def test_reference_arm_runs_on_rank_zero_only():
     res = bench.run_reference(args, 1, 0)
     assert res["impl"] == "reference" and res["unit"] == "flips/ns" and res["value"] > 0
     assert res["e2e"]["h2d_bytes_per_step"] == 0 and res["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_integrated_time_of_an_ar1_series():
+    """The package's effective-sample estimator: tau_int of AR(1) with
+    coefficient phi is (1 + phi) / (2 (1 - phi))."""
+    import numpy as np
+
+    from paper_1906_06297_gb300 import analysis
+
+    rng = np.random.default_rng(1)
+    phi, n = 0.7, 300_000
+    eps = rng.standard_normal(n)
+    x = np.empty(n)
+    x[0] = 0.0
+    for i in range(1, n):
+        x[i] = phi * x[i - 1] + eps[i]
+    tau = analysis.integrated_time(x)
+    assert abs(tau - (1 + phi) / (2 * (1 - phi))) < 0.2
+    e = analysis.effective_samples([x[: n // 2], x[n // 2:]])
+    assert abs(e["effective"] - n / (2 * e["tau_int"])) < 1e-6
