@@ -234,6 +234,71 @@ ISING_API int ising_batch_run_noalloc(int64_t n, const int64_t *L, int32_t ladde
                                       uint64_t sweep_offset, int32_t record_every, int32_t swaps,
                                       int64_t *trace_dev, ising_stream_t stream);
 
+/* ------------------------------------------------------------------------ */
+/* Learned block proposals.  Not in the paper: a Metropolis-Hastings move    */
+/* that flips one 8 x 8 block, proposed by a small convolutional network,    */
+/* layered on the checkerboard sweep.  Chains are C lattices of side L       */
+/* (multiple of 32, at most 4096) laid out as a batch of equal sides:        */
+/* lattice c's planes at word c * L * L/32 of the black and white buffers.    */
+/* Network: three 3x3 periodic conv layers of 32 channels with GELU (the    */
+/* first reads the spins), a 3x3 conv to one channel, and the mean over each  */
+/* 8 x 8 block gives that block's logit (b = by * L/8 + bx).  Weights are    */
+/* rounded to bfloat16 for every use; products accumulate in FP32; every    */
+/* reduction has a fixed order, so logits are a deterministic function of    */
+/* the state.  Parameters: one FP32 vector of ising_net_param_count() values, */
+/* W1[32][9], b1[32], W2[32][32][9], b2[32], W3[32][32][9], b3[32], W4[32][9], */
+/* b4[1] (tap k = 3 (dy + 1) + (dx + 1)).                                     */
+/* ------------------------------------------------------------------------ */
+ISING_API int ising_net_param_count(void);
+
+/* Device work-buffer bytes of a forward (train = 0) or a forward + backward
+ * (train = 1) over C chains of side L. */
+ISING_API int ising_net_workspace_bytes(int64_t L, int64_t C, int32_t train, size_t *bytes);
+
+/* logits_dev[c][b] for every chain; flip_block_dev (nullable, int32[C], -1 for
+ * none) evaluates each chain with that block flipped.  train != 0 keeps the
+ * activations in work_dev for ising_net_backward. */
+ISING_API int ising_net_forward(int64_t L, int64_t C, const void *black_dev, const void *white_dev,
+                                const int32_t *flip_block_dev, const float *params_dev, float *logits_dev,
+                                void *work_dev, size_t work_bytes, int32_t train, ising_stream_t stream);
+
+/* grad_dev = d(sum dlogits * logits)/d(params) for the last training forward
+ * on the same chains and parameters (straight-through the bfloat16 rounding). */
+ISING_API int ising_net_backward(int64_t L, int64_t C, const void *black_dev, const void *white_dev,
+                                 const float *params_dev, const float *dlogits_dev, float *grad_dev, void *work_dev,
+                                 size_t work_bytes, ising_stream_t stream);
+
+/* Regression of the block acceptance: t_b = min(0, -beta dE_b) from the exact
+ * block energy changes; dlogits = 2 (logits - t) / (C nb) (the gradient of the
+ * mean squared residual), chain_sq_dev[c] = that chain's squared residual sum,
+ * *loss_dev = the mean squared residual. */
+ISING_API int ising_net_targets_loss(int64_t L, int64_t C, const void *black_dev, const void *white_dev, double beta,
+                                     const float *logits_dev, float *dlogits_dev, float *chain_sq_dev,
+                                     float *loss_dev, ising_stream_t stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected at `step`). */
+ISING_API int ising_net_adam(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev, int64_t step,
+                             float lr, ising_stream_t stream);
+
+/* Draw one block per chain: inverse CDF of softmax(logits) (FP64, block order)
+ * with the purpose-3 draw of site 0 in stream c at step t, or uniformly
+ * ((u * nb) >> 32) when logits_dev is NULL. */
+ISING_API int ising_block_propose(int64_t L, int64_t C, const float *logits_dev, uint64_t seed, uint64_t t,
+                                  int32_t *block_dev, ising_stream_t stream);
+
+/* Accept or reject flipping block_dev[c] of each chain: dE = twice the sum of
+ * the boundary bonds s_in s_out (exact); x = -beta dE + log q_x'(b) -
+ * log q_x(b) (logits of the state and of the flipped state; both NULL for
+ * uniform proposals); flip iff the purpose-3 draw of site 1 is below
+ * floor(2^32 min(1, exp(x))).  accepted_dev[c] = 0/1, dE_dev (nullable) = dE. */
+ISING_API int ising_block_accept(int64_t L, int64_t C, void *black_dev, void *white_dev, double beta,
+                                 const float *logits_x_dev, const float *logits_xp_dev, const int32_t *block_dev,
+                                 uint64_t seed, uint64_t t, int32_t *accepted_dev, int64_t *dE_dev,
+                                 ising_stream_t stream);
+
+/* Text of the last learned-proposal API failure seen by this thread. */
+ISING_API const char *ising_net_last_error(void);
+
 /* Text of the last batch-API failure seen by this thread. */
 ISING_API const char *ising_batch_last_error(void);
 

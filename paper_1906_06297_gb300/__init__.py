@@ -93,11 +93,22 @@ def _load():
             "ising_batch_autotune": [BP, i64, P],
             "ising_batch_barrier_selftest": [BP, i64, P],
             "ising_batch_run_noalloc": [i64, P, i32, P, P, P, P, P, i64, u64, u64, i32, i32, P, P],
+            "ising_net_workspace_bytes": [i64, i64, i32, P],
+            "ising_net_forward": [i64, i64, P, P, P, P, P, P, ctypes.c_size_t, i32, P],
+            "ising_net_backward": [i64, i64, P, P, P, P, P, P, ctypes.c_size_t, P],
+            "ising_net_targets_loss": [i64, i64, P, P, dbl, P, P, P, P, P],
+            "ising_net_adam": [P, P, P, P, i64, ctypes.c_float, P],
+            "ising_block_propose": [i64, i64, P, u64, u64, P, P],
+            "ising_block_accept": [i64, i64, P, P, dbl, P, P, P, u64, u64, P, P, P],
         }
         for name, args in bsig.items():
             f = getattr(lib, name)
             f.argtypes = args
             f.restype = ctypes.c_int
+        lib.ising_net_param_count.argtypes = []
+        lib.ising_net_param_count.restype = ctypes.c_int
+        lib.ising_net_last_error.argtypes = []
+        lib.ising_net_last_error.restype = ctypes.c_char_p
         lib.ising_batch_last_error.argtypes = []
         lib.ising_batch_last_error.restype = ctypes.c_char_p
         lib.ising_strerror.argtypes = [ctypes.c_int]
@@ -112,6 +123,8 @@ def _check(rc: int, where: str):
     if rc != ISING_OK:
         lib = _load()
         msg = lib.ising_batch_last_error().decode() if where.startswith("ising_batch") else ""
+        if where.startswith("ising_net") or where.startswith("ising_block"):
+            msg = lib.ising_net_last_error().decode()
         raise IsingError(rc, where, msg or lib.ising_last_error().decode() or lib.ising_strerror(rc).decode())
 
 
@@ -370,3 +383,153 @@ def ising_batch_run_noalloc(L, ladder_size: int, beta, black, white, slot_of, la
                                            _addr(white), _addr(slot_of), _addr(lattice_at), n_sweeps, seed,
                                            sweep_offset, record_every, int(bool(swaps)), _addr(trace),
                                            _stream(stream)), "ising_batch_run_noalloc")
+
+
+# ---------------------------------------------------------------------------
+# Learned block proposals
+# ---------------------------------------------------------------------------
+def ising_net_param_count() -> int:
+    return int(_load().ising_net_param_count())
+
+
+def ising_net_workspace_bytes(L: int, C: int, train: bool) -> int:
+    out = ctypes.c_size_t()
+    _check(_load().ising_net_workspace_bytes(L, C, int(bool(train)), ctypes.byref(out)), "ising_net_workspace_bytes")
+    return out.value
+
+
+def ising_net_forward(L, C, black, white, flip_block, params, logits, work, train=False, stream=None):
+    _check(_load().ising_net_forward(L, C, _addr(black), _addr(white), _addr(flip_block), _addr(params),
+                                     _addr(logits), _addr(work), work.numel() * work.element_size(),
+                                     int(bool(train)), _stream(stream)), "ising_net_forward")
+
+
+def ising_net_backward(L, C, black, white, params, dlogits, grad, work, stream=None):
+    _check(_load().ising_net_backward(L, C, _addr(black), _addr(white), _addr(params), _addr(dlogits), _addr(grad),
+                                      _addr(work), work.numel() * work.element_size(), _stream(stream)),
+           "ising_net_backward")
+
+
+def ising_net_targets_loss(L, C, black, white, beta, logits, dlogits, chain_sq, loss, stream=None):
+    _check(_load().ising_net_targets_loss(L, C, _addr(black), _addr(white), float(beta), _addr(logits),
+                                          _addr(dlogits), _addr(chain_sq), _addr(loss), _stream(stream)),
+           "ising_net_targets_loss")
+
+
+def ising_net_adam(params, grad, m, v, step: int, lr: float, stream=None):
+    _check(_load().ising_net_adam(_addr(params), _addr(grad), _addr(m), _addr(v), step, float(lr), _stream(stream)),
+           "ising_net_adam")
+
+
+def ising_block_propose(L, C, logits, seed: int, t: int, block, stream=None):
+    _check(_load().ising_block_propose(L, C, _addr(logits), seed, t, _addr(block), _stream(stream)),
+           "ising_block_propose")
+
+
+def ising_block_accept(L, C, black, white, beta, logits_x, logits_xp, block, seed: int, t: int, accepted, dE=None,
+                       stream=None):
+    _check(_load().ising_block_accept(L, C, _addr(black), _addr(white), float(beta), _addr(logits_x),
+                                      _addr(logits_xp), _addr(block), seed, t, _addr(accepted), _addr(dE),
+                                      _stream(stream)), "ising_block_accept")
+
+
+class BlockMove:
+    """C chains of side L, kept in a Batch of equal sides at one beta (plain
+    sweeps through the batch kernel), with a network-proposed (or uniform)
+    Metropolis-Hastings block move after each sweep."""
+
+    def __init__(self, L: int, C: int, beta: float, device="cuda"):
+        import torch
+
+        self.L, self.C, self.beta = int(L), int(C), float(beta)
+        self.nb = (self.L // 8) ** 2
+        self.batch = Batch([self.L] * self.C, 1, [self.beta], device=device)
+        words = int(self.batch.word_off[-1])
+        ws = self.batch.ws
+        self.black = ws[self.batch._black_off:self.batch._black_off + 8 * words]
+        self.white = ws[self.batch._white_off:self.batch._white_off + 8 * words]
+        self.work = torch.empty(ising_net_workspace_bytes(self.L, self.C, False), dtype=torch.uint8, device=device)
+        self.lx = torch.zeros((self.C, self.nb), dtype=torch.float32, device=device)
+        self.lxp = torch.zeros_like(self.lx)
+        self.block = torch.zeros(self.C, dtype=torch.int32, device=device)
+        self.accepted = torch.zeros(self.C, dtype=torch.int32, device=device)
+        self.dE = torch.zeros(self.C, dtype=torch.int64, device=device)
+
+    def move(self, params, seed: int, t: int, stream=None):
+        """One block move of every chain; params None proposes uniformly."""
+        if params is None:
+            ising_block_propose(self.L, self.C, None, seed, t, self.block, stream)
+            ising_block_accept(self.L, self.C, self.black, self.white, self.beta, None, None, self.block, seed, t,
+                               self.accepted, self.dE, stream)
+            return
+        ising_net_forward(self.L, self.C, self.black, self.white, None, params, self.lx, self.work, False, stream)
+        ising_block_propose(self.L, self.C, self.lx, seed, t, self.block, stream)
+        ising_net_forward(self.L, self.C, self.black, self.white, self.block, params, self.lxp, self.work, False,
+                          stream)
+        ising_block_accept(self.L, self.C, self.black, self.white, self.beta, self.lx, self.lxp, self.block, seed, t,
+                           self.accepted, self.dE, stream)
+
+
+def train_block_proposer(L: int, beta: float, n_configs: int = 100_000, batch: int = 64, steps: int = 2000,
+                         lr: float = 1e-3, seed: int = 0, sweeps_between: int = 10, equilibrate: int = 200,
+                         log_every: int = 10, device="cuda", stream=None):
+    """Train the proposal network on the GPU with the library's kernels.
+
+    Training data: n_configs configurations of side L from plain sweeps at
+    beta (up to 1024 chains, snapshots `sweeps_between` sweeps apart after
+    `equilibrate` sweeps).  Each step takes a minibatch of `batch` consecutive
+    configurations, regresses the block logits on min(0, -beta dE_b) and takes
+    an Adam step.  This function only sequences library calls; every
+    arithmetic step runs in the kernels.  Returns {"params", "loss", "steps"}.
+    """
+    import numpy as np
+    import torch
+
+    n_chains = min(n_configs, 1024)
+    gen = Batch([L] * n_chains, 1, [beta], device=device)
+    gen.init(ISING_INIT_RANDOM, seed, stream)
+    gen.run(equilibrate, seed, 0, 0, False, None, True, stream)
+    words = L * L // 32
+    data_b = torch.empty((n_configs, words * 8), dtype=torch.uint8, device=device)
+    data_w = torch.empty_like(data_b)
+    t, got = equilibrate, 0
+    while got < n_configs:
+        take = min(n_chains, n_configs - got)
+        data_b[got:got + take].copy_(gen.ws[gen._black_off:gen._black_off + 8 * words * take].view(take, words * 8))
+        data_w[got:got + take].copy_(gen.ws[gen._white_off:gen._white_off + 8 * words * take].view(take, words * 8))
+        got += take
+        gen.run(sweeps_between, seed, t, 0, False, None, True, stream)
+        t += sweeps_between
+    del gen
+    rng = np.random.default_rng(seed)
+    n_par = ising_net_param_count()
+    theta = np.zeros(n_par, dtype=np.float32)
+    o = 0
+    for size, fan_in, is_w in ((32 * 9, 9, True), (32, 0, False), (32 * 32 * 9, 288, True), (32, 0, False),
+                               (32 * 32 * 9, 288, True), (32, 0, False), (32 * 9, 288, True), (1, 0, False)):
+        if is_w:
+            theta[o:o + size] = rng.normal(0.0, np.sqrt(2.0 / fan_in), size)
+        o += size
+    params = torch.from_numpy(theta).to(device)
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    grad = torch.zeros_like(params)
+    nb = (L // 8) ** 2
+    work = torch.empty(ising_net_workspace_bytes(L, batch, True), dtype=torch.uint8, device=device)
+    logits = torch.zeros((batch, nb), dtype=torch.float32, device=device)
+    dlogits = torch.zeros_like(logits)
+    chain_sq = torch.zeros(batch, dtype=torch.float32, device=device)
+    loss = torch.zeros(1, dtype=torch.float32, device=device)
+    n_mb = n_configs // batch
+    order = rng.permutation(n_mb)
+    history = []
+    for step in range(1, steps + 1):
+        i0 = int(order[(step - 1) % n_mb]) * batch
+        blk, wht = data_b[i0:i0 + batch], data_w[i0:i0 + batch]
+        ising_net_forward(L, batch, blk, wht, None, params, logits, work, True, stream)
+        ising_net_targets_loss(L, batch, blk, wht, beta, logits, dlogits, chain_sq, loss, stream)
+        ising_net_backward(L, batch, blk, wht, params, dlogits, grad, work, stream)
+        ising_net_adam(params, grad, m, v, step, lr, stream)
+        if step == 1 or step % log_every == 0 or step == steps:
+            history.append(float(loss.item()))
+    return {"params": params, "loss": history, "steps": steps}

@@ -62,7 +62,7 @@ __host__ __device__ __forceinline__ uint32_t counter_word3(int colour, int purpo
     return (uint32_t)colour | ((uint32_t)purpose << 1) | ((uint32_t)(t >> 32) << 8);
 }
 
-enum Purpose { kPurposeMetropolis = 0, kPurposeInit = 1, kPurposeExchange = 2 };
+enum Purpose { kPurposeMetropolis = 0, kPurposeInit = 1, kPurposeExchange = 2, kPurposeLearned = 3 };
 
 // ---------------------------------------------------------------------------
 // Acceptance, in the form the kernels consume.  For beta >= 0, T[0..2] = 2^32
