@@ -50,8 +50,12 @@ def parse_args(argv=None):
     p.add_argument("--no-extras", action="store_true", help="skip per-beta, rng probe, e2e and cpu legs")
     p.add_argument("--no-batch", action="store_true", help="skip the batched parallel-tempering leg")
     p.add_argument("--pt-sweeps", type=int, default=10000)
-    p.add_argument("--workload", choices=["sweep", "pt"], default="sweep",
-                   help="sweep: the 65536^2 lattice (default); pt: only the batched parallel-tempering leg")
+    p.add_argument("--workload", choices=["sweep", "pt", "learned"], default="sweep",
+                   help="sweep: the 65536^2 lattice (default); pt / learned: only that leg")
+    p.add_argument("--no-learned", action="store_true", help="skip the learned block-proposal leg")
+    p.add_argument("--learned-steps", type=int, default=1000, help="training steps of the proposal network")
+    p.add_argument("--learned-cycles", type=int, default=400, help="measured sweep + move cycles")
+    p.add_argument("--learned-configs", type=int, default=100000, help="training configurations")
     return p.parse_args(argv)
 
 
@@ -304,6 +308,8 @@ def run_ours(args, world, rank, local):
         result["cpu_baseline"] = cpu_baseline(args)
         if not args.no_batch:
             result["pt_batch"] = run_pt_batch(ising, torch, args, device, stream)
+        if not args.no_learned:
+            result["learned"] = run_learned(ising, torch, args, device, stream)
     if world > 1:
         import torch.distributed as dist
 
@@ -479,6 +485,68 @@ def run_pt_only(args, world, rank, local):
             "pt_batch": pt}
 
 
+def run_learned(ising, torch, args, device, stream):
+    """The learned form at beta_c on 128 x 128 lattices: train the proposal
+    network on configurations from the plain sweep (10 sweeps apart), then
+    compare, from the same starting states, cycles of (one sweep) with cycles
+    of (one sweep + one uniform block move) and (one sweep + one network block
+    move): integrated autocorrelation times per cycle of |m| and E, their
+    effective samples per GPU second, and block acceptance rates."""
+    import numpy as np
+
+    from paper_1906_06297_gb300 import analysis
+
+    L, beta, seed = 128, BETA_C_CONFIG, args.seed
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tr = ising.train_block_proposer(L, beta, n_configs=args.learned_configs, batch=64, steps=args.learned_steps,
+                                    lr=2e-3, seed=seed, log_every=max(1, args.learned_steps // 10), device=device,
+                                    stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    C, cycles, warm = 128, args.learned_cycles, 500
+    variants = {}
+    for name in ("plain", "uniform", "learned"):
+        mv = ising.BlockMove(L, C, beta, device=device)
+        mv.batch.init(ising.ISING_INIT_RANDOM, seed, stream)
+        mv.batch.run(warm, seed, 0, 0, False, None, True, stream)
+        trace = torch.zeros((cycles, C, 2), dtype=torch.int64, device=device)
+        # the move writes each cycle's acceptance flags straight into its row
+        acc_rows = torch.zeros((cycles, C), dtype=torch.int32, device=device)
+        params = tr["params"] if name == "learned" else None
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for k in range(cycles):
+                t = warm + k
+                mv.batch.run(1, seed, t, 1, False, trace[k], True, stream)
+                if name != "plain":
+                    mv.accepted = acc_rows[k]
+                    mv.move(params, seed, t, stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        h = trace.cpu().numpy()
+        m = [np.abs(h[:, c, 0]) / (L * L) for c in range(C)]
+        e = [-h[:, c, 1] / (L * L) for c in range(C)]
+        em, ee = analysis.effective_samples(m), analysis.effective_samples(e)
+        variants[name] = {"ms": round(ms, 2), "ms_per_cycle": round(ms / cycles, 4),
+                          "tau_abs_m_cycles": round(em["tau_int"], 2), "tau_e_cycles": round(ee["tau_int"], 2),
+                          "ess_per_s_abs_m": round(em["effective"] / (ms * 1e-3), 1),
+                          "ess_per_s_e": round(ee["effective"] / (ms * 1e-3), 1),
+                          "block_acceptance": (round(float(acc_rows.sum().item()) / (C * cycles), 5)
+                                               if name != "plain" else None),
+                          "mean_e": round(float(np.mean(np.concatenate(e))), 5)}
+        del mv, trace
+    return {"workload": f"{C} chains of {L}x{L} at beta={beta}; network trained for {args.learned_steps} Adam steps "
+                        f"(batch 64) on {args.learned_configs} plain-sweep configurations 10 sweeps apart; "
+                        f"{cycles} measured cycles after {warm} sweeps",
+            "train_ms": round(train_ms, 1), "train_loss_first_last": [round(tr["loss"][0], 4), round(tr["loss"][-1], 4)],
+            "variants": variants,
+            "note": "tau from series of this length are lower bounds where they approach the run length"}
+
+
 def cpu_baseline(args):
     """The oracle as it stands, on the host cores: a bounded sample of the
     same workload (a smaller lattice, same beta and start)."""
@@ -535,6 +603,17 @@ def main(argv=None):
         res = run_reference(args, world, rank)
     elif args.workload == "pt":
         res = run_pt_only(args, world, rank, local)
+    elif args.workload == "learned":
+        import torch
+
+        import paper_1906_06297_gb300 as ising
+
+        ising.build()
+        torch.cuda.set_device(local)
+        device = torch.device("cuda", local)
+        lr = run_learned(ising, torch, args, device, torch.cuda.Stream(device=device))
+        res = {"metric": METRIC, "value": lr["variants"]["learned"]["ess_per_s_e"], "unit": "effective samples/s",
+               "impl": "ours", "config": {"workload": lr["workload"]}, "learned": lr}
     else:
         res = run_ours(args, world, rank, local)
     if rank == 0 and res is not None:

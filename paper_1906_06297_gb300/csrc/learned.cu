@@ -273,50 +273,104 @@ __global__ void __launch_bounds__(kThreads) conv32_bwd_data_kernel(int L, int64_
     }
 }
 
-// Weight gradients of one layer as per-CTA partial sums (fixed order):
-// partial[cta][o][i][k] = sum over the CTA's pixels of dz(p)[o] * a(p + off_k)[i],
-// and the bias gradient sum dz(p)[o].  CIN = 1 reads spins; COUT = 1 reads the
-// block-mean gradient d4 of layer 4.
+// Weight gradients as per-CTA partial sums (fixed order).  The pixels are cut
+// into tiles of 8 rows x 32 columns of one chain; CTA j handles tiles j,
+// j + gridDim.x, ... in order.  A tile's output gradients dz (and the layer's
+// input a, with a one-pixel halo) are staged in shared memory; thread (oq, iq)
+// of 16 x 16 accumulates the 2 x 2 (output, input) channel pairs 2 oq + {0, 1}
+// x 2 iq + {0, 1} for all 9 taps, and threads with iq = 0 the bias sums.
+// partial[cta][e]: e = (o * CIN + i) * 9 + k for weights, then the biases.
+constexpr int kTy = 8, kTx = 32;
+
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kThreads) wgrad_kernel(Chains ch, int64_t C, const float *a_prev, const float *dz,
-                                                         const float *dlogits, int64_t pix_per_cta, float *partial)
+__device__ __forceinline__ void wgrad_stage(const Chains &ch, const float *a_prev, const float *dz,
+                                            const float *dlogits, int64_t c, int y0, int x0, float *sa, float *sd)
 {
-    constexpr int NW = COUT * CIN * 9, NB = COUT, NE = NW + NB;
     const int L = ch.L, nb1 = L / kBlk;
-    const int64_t npix = C * (int64_t)L * L;
-    const int64_t p0 = (int64_t)blockIdx.x * pix_per_cta;
-    const int64_t p1 = min(npix, p0 + pix_per_cta);
-    const int64_t c0 = p0 / ((int64_t)L * L);
-    const int yx0 = (int)(p0 - c0 * (int64_t)L * L);
-    for (int e = threadIdx.x; e < NE; e += blockDim.x) {
-        float acc = 0.0f;
-        const bool is_w = e < NW;
-        const int o = is_w ? e / (CIN * 9) : e - NW;
-        const int rem = is_w ? e - o * CIN * 9 : 0, i = rem / 9, k = rem - i * 9;
-        const int dy = k / 3 - 1, dx = k % 3 - 1;
-        int64_t c = c0;
-        int y = yx0 / L, x = yx0 - (yx0 / L) * L;
-        for (int64_t p = p0; p < p1; ++p) {
-            const float g = COUT == 1 ? dlogits[c * nb1 * nb1 + (y / kBlk) * nb1 + x / kBlk] * (1.0f / (kBlk * kBlk))
-                                      : dz[p * COUT + o];
-            if (is_w) {
-                int yy = y + dy, xx = x + dx;
-                yy = yy < 0 ? yy + L : (yy >= L ? yy - L : yy);
-                xx = xx < 0 ? xx + L : (xx >= L ? xx - L : xx);
-                const float a = CIN == 1 ? spin_at(ch, c, yy, xx, -1) : a_prev[((c * L + yy) * (int64_t)L + xx) * CIN + i];
-                acc = fmaf(g, a, acc);
-            } else {
-                acc += g;
-            }
-            if (++x == L) {
-                x = 0;
-                if (++y == L) {
-                    y = 0;
-                    ++c;
+    // input tile with halo: (kTy + 2) x (kTx + 2) pixels x CIN channels
+    for (int e = threadIdx.x; e < (kTy + 2) * (kTx + 2) * CIN; e += blockDim.x) {
+        const int pix = e / CIN, i = e - pix * CIN;
+        const int ty = pix / (kTx + 2), tx = pix - ty * (kTx + 2);
+        int y = y0 + ty - 1, x = x0 + tx - 1;
+        y = y < 0 ? y + L : (y >= L ? y - L : y);
+        x = x < 0 ? x + L : (x >= L ? x - L : x);
+        sa[e] = CIN == 1 ? spin_at(ch, c, y, x, -1) : a_prev[((c * L + y) * (int64_t)L + x) * CIN + i];
+    }
+    for (int e = threadIdx.x; e < kTy * kTx * COUT; e += blockDim.x) {
+        const int pix = e / COUT, o = e - pix * COUT;
+        const int y = y0 + pix / kTx, x = x0 + pix % kTx;
+        sd[e] = COUT == 1 ? dlogits[c * nb1 * nb1 + (y / kBlk) * nb1 + x / kBlk] * (1.0f / (kBlk * kBlk))
+                          : dz[((c * L + y) * (int64_t)L + x) * COUT + o];
+    }
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) wgrad_kernel(Chains ch, int64_t C, const float *a_prev, const float *dz,
+                                                    const float *dlogits, float *partial)
+{
+    extern __shared__ float smem[];
+    float *sa = smem;                                 // (kTy+2) (kTx+2) CIN
+    float *sd = smem + (kTy + 2) * (kTx + 2) * CIN;   // kTy kTx COUT
+    constexpr int NE = COUT * CIN * 9 + COUT;
+    const int L = ch.L;
+    const int tiles_x = L / kTx, tiles_y = L / kTy;
+    const int64_t n_tiles = C * tiles_x * tiles_y;
+    // thread roles: oq, iq in 0..15 cover output / input channel pairs; for
+    // CIN == 1 or COUT == 1 the unused index collapses
+    constexpr int OQ = COUT == 1 ? 1 : COUT / 2, IQ = CIN == 1 ? 1 : CIN / 2;
+    constexpr int OPT = COUT == 1 ? 1 : 2, IPT = CIN == 1 ? 1 : 2;
+    const int role = threadIdx.x;
+    const bool active = role < OQ * IQ;
+    const int oq = active ? role / IQ : 0, iq = active ? role - (role / IQ) * IQ : 0;
+    float acc[OPT][IPT][9];
+    float bacc[OPT];
+#pragma unroll
+    for (int a = 0; a < OPT; ++a) {
+        bacc[a] = 0.0f;
+#pragma unroll
+        for (int b = 0; b < IPT; ++b)
+#pragma unroll
+            for (int k = 0; k < 9; ++k) acc[a][b][k] = 0.0f;
+    }
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t c = tile / (tiles_x * tiles_y);
+        const int rem = (int)(tile - c * tiles_x * tiles_y);
+        const int y0 = (rem / tiles_x) * kTy, x0 = (rem % tiles_x) * kTx;
+        __syncthreads();
+        wgrad_stage<CIN, COUT>(ch, a_prev, dz, dlogits, c, y0, x0, sa, sd);
+        __syncthreads();
+        if (active) {
+            for (int pix = 0; pix < kTy * kTx; ++pix) {
+                const int ty = pix / kTx, tx = pix - ty * kTx;
+                float g[OPT];
+#pragma unroll
+                for (int a = 0; a < OPT; ++a) g[a] = sd[pix * COUT + OPT * oq + a];
+#pragma unroll
+                for (int a = 0; a < OPT; ++a) bacc[a] += g[a];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const int hp = (ty + k / 3) * (kTx + 2) + (tx + k % 3);
+#pragma unroll
+                    for (int b = 0; b < IPT; ++b) {
+                        const float av = sa[hp * CIN + IPT * iq + b];
+#pragma unroll
+                        for (int a = 0; a < OPT; ++a) acc[a][b][k] = fmaf(g[a], av, acc[a][b][k]);
+                    }
                 }
             }
         }
-        partial[(int64_t)blockIdx.x * NE + e] = acc;
+    }
+    if (active) {
+        float *out = partial + (int64_t)blockIdx.x * NE;
+#pragma unroll
+        for (int a = 0; a < OPT; ++a)
+#pragma unroll
+            for (int b = 0; b < IPT; ++b)
+#pragma unroll
+                for (int k = 0; k < 9; ++k) out[((OPT * oq + a) * CIN + IPT * iq + b) * 9 + k] = acc[a][b][k];
+        if (iq == 0)
+#pragma unroll
+            for (int a = 0; a < OPT; ++a) out[COUT * CIN * 9 + OPT * oq + a] = bacc[a];
     }
 }
 
@@ -512,7 +566,7 @@ struct NetWork {
     size_t bytes;
 };
 
-constexpr int64_t kWgradPix = 4096;  // pixels per CTA in the weight-gradient kernels
+constexpr int64_t kWgradCtasPerSm = 2;  // persistent CTAs per SM in the weight-gradient kernels
 
 NetWork net_layout(int64_t L, int64_t C, int train, char *base)
 {
@@ -528,7 +582,9 @@ NetWork net_layout(int64_t L, int64_t C, int train, char *base)
     if (train) {
         w.z1 = take(act); w.a1 = take(act); w.z2 = take(act); w.a2 = take(act);
         w.z3 = take(act); w.a3 = take(act); w.da = take(act); w.db = take(act);
-        w.n_cta = (C * L * L + kWgradPix - 1) / kWgradPix;
+        DeviceInfo info{152};
+        device_info(&info);
+        w.n_cta = (int64_t)info.sm_count * kWgradCtasPerSm;
         w.partial = take((size_t)w.n_cta * (kN2 + kCh) * sizeof(float));
     } else {
         w.a1 = take(act); w.a2 = take(act);
@@ -605,20 +661,26 @@ ISING_API int ising_net_backward(int64_t L, int64_t C, const void *black_dev, co
     const size_t smem = (size_t)kN2 * sizeof(float);
     const unsigned gw = (unsigned)w.n_cta;
     cudaFuncSetAttribute(conv32_bwd_data_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t sm32 = (size_t)((kTy + 2) * (kTx + 2) * kCh + kTy * kTx * kCh) * sizeof(float);
+    const size_t sm4 = (size_t)((kTy + 2) * (kTx + 2) * kCh + kTy * kTx) * sizeof(float);
+    const size_t sm1 = (size_t)((kTy + 2) * (kTx + 2) + kTy * kTx * kCh) * sizeof(float);
+    cudaFuncSetAttribute(wgrad_kernel<kCh, kCh>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm32);
+    cudaFuncSetAttribute(wgrad_kernel<kCh, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
+    cudaFuncSetAttribute(wgrad_kernel<1, kCh>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     // layer 4
-    wgrad_kernel<kCh, 1><<<gw, kThreads, 0, s>>>(ch, C, w.a3, nullptr, dlogits_dev, kWgradPix, w.partial);
+    wgrad_kernel<kCh, 1><<<gw, 256, sm4, s>>>(ch, C, w.a3, nullptr, dlogits_dev, w.partial);
     reduce_partials_kernel<<<4, 256, 0, s>>>(w.partial, w.n_cta, kN1 + 1, kN1, grad_dev, kOffW4, kOffB4);
     l4_bwd_data_kernel<<<g, kThreads, 0, s>>>((int)L, C, params_dev, dlogits_dev, w.z3, w.da);  // dz3
     // layer 3
-    wgrad_kernel<kCh, kCh><<<gw, kThreads, 0, s>>>(ch, C, w.a2, w.da, nullptr, kWgradPix, w.partial);
+    wgrad_kernel<kCh, kCh><<<gw, 256, sm32, s>>>(ch, C, w.a2, w.da, nullptr, w.partial);
     reduce_partials_kernel<<<40, 256, 0, s>>>(w.partial, w.n_cta, kN2 + kCh, kN2, grad_dev, kOffW3, kOffB3);
     conv32_bwd_data_kernel<<<g, kThreads, smem, s>>>((int)L, C, params_dev, kOffW3, w.da, w.z2, w.db);  // dz2
     // layer 2
-    wgrad_kernel<kCh, kCh><<<gw, kThreads, 0, s>>>(ch, C, w.a1, w.db, nullptr, kWgradPix, w.partial);
+    wgrad_kernel<kCh, kCh><<<gw, 256, sm32, s>>>(ch, C, w.a1, w.db, nullptr, w.partial);
     reduce_partials_kernel<<<40, 256, 0, s>>>(w.partial, w.n_cta, kN2 + kCh, kN2, grad_dev, kOffW2, kOffB2);
     conv32_bwd_data_kernel<<<g, kThreads, smem, s>>>((int)L, C, params_dev, kOffW2, w.db, w.z1, w.da);  // dz1
     // layer 1
-    wgrad_kernel<1, kCh><<<gw, kThreads, 0, s>>>(ch, C, nullptr, w.da, nullptr, kWgradPix, w.partial);
+    wgrad_kernel<1, kCh><<<gw, 256, sm1, s>>>(ch, C, nullptr, w.da, nullptr, w.partial);
     reduce_partials_kernel<<<4, 256, 0, s>>>(w.partial, w.n_cta, kN1 + kCh, kN1, grad_dev, kOffW1, kOffB1);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ISING_OK : nfail(ISING_ECUDA, cudaGetErrorString(e));
