@@ -50,7 +50,8 @@ def parse_args(argv=None):
     p.add_argument("--no-extras", action="store_true", help="skip per-beta, rng probe, e2e and cpu legs")
     p.add_argument("--no-batch", action="store_true", help="skip the batched parallel-tempering leg")
     p.add_argument("--pt-sweeps", type=int, default=10000)
-    p.add_argument("--workload", choices=["sweep", "pt", "learned"], default="sweep",
+    p.add_argument("--slabs", type=int, default=4, help="slabs on one GPU for the slab leg / workload")
+    p.add_argument("--workload", choices=["sweep", "pt", "learned", "slabs"], default="sweep",
                    help="sweep: the 65536^2 lattice (default); pt / learned: only that leg")
     p.add_argument("--no-learned", action="store_true", help="skip the learned block-proposal leg")
     p.add_argument("--learned-steps", type=int, default=1000, help="training steps of the proposal network")
@@ -177,7 +178,7 @@ def source_digest() -> str:
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("msc4.cu", "common.cuh"):
+    for f in ("msc4.cu", "sweep_core.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_1906_06297_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -310,11 +311,116 @@ def run_ours(args, world, rank, local):
             result["pt_batch"] = run_pt_batch(ising, torch, args, device, stream)
         if not args.no_learned:
             result["learned"] = run_learned(ising, torch, args, device, stream)
+        result["slab_leg"] = run_slab_leg(ising, torch, args, device, stream, value / world)
     if world > 1:
         import torch.distributed as dist
 
         dist.destroy_process_group()
     return result
+
+
+def time_slab_sweeps(ising, torch, slabs, beta, seed, steps, warmup, trace, stream):
+    """K slabs of one lattice on this GPU (halo copies + per-slab half-sweeps,
+    one public call per batch of sweeps): warm-up, then `steps` sweeps timed
+    with CUDA events on `stream`.  Returns total ms."""
+    ising.ising_slab_sweep(slabs, beta, warmup, seed, 0, trace[:max(warmup, 1)], stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        ising.ising_slab_sweep(slabs, beta, steps, seed, warmup, trace[:steps], stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_slab_leg(ising, torch, args, device, stream, whole_flips_per_ns):
+    """The lattice of the headline workload held as K horizontal slabs with
+    halo rows on this GPU (Sec. 4 layout): flips/ns and the cost of the halo
+    copies relative to the whole-lattice sweep."""
+    L, k, steps = args.L, args.slabs, 20
+    seed = replica_seed(args.seed, 0)
+    slabs = []
+    for row0, rows in ising.slab_partition(L, k):
+        sl = ising.Slab(L, row0, rows, device=device)
+        ising.ising_slab_init(sl, ising.ISING_INIT_RANDOM, seed, stream)
+        slabs.append(sl)
+    trace = torch.zeros((steps, 2), dtype=torch.int64, device=device)
+    ms = time_slab_sweeps(ising, torch, slabs, args.beta, seed, steps, 3, trace, stream)
+    rate = L * L * steps / (ms * 1e6)
+    del slabs
+    torch.cuda.empty_cache()
+    return {"slabs": k, "L": L, "sweeps": steps, "flips_per_ns": round(rate, 2),
+            "vs_whole_lattice": round(rate / whole_flips_per_ns, 4),
+            "gpu_launches_per_sweep": 2 * (k + 1)}
+
+
+def run_slabs(args, world, rank, local):
+    """One L x L lattice cut into horizontal slabs (Sec. 4).  One process:
+    args.slabs slabs on this GPU, halos by the library's copy kernel.  Several
+    ranks: one slab per rank, halo rows exchanged point to point (NCCL) before
+    each half-sweep, the trace all-reduced once at the end.  Strong scaling:
+    the lattice is the same for every N."""
+    import torch
+
+    import paper_1906_06297_gb300 as ising
+
+    ising.build()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=device)
+    L, beta, seed = args.L, args.beta, args.seed
+    stream = torch.cuda.Stream(device=device)
+    n = max(args.steps, 1)
+    trace = torch.zeros((n, 2), dtype=torch.int64, device=device)
+    with torch.cuda.stream(stream):
+        if world == 1:
+            slabs = []
+            for row0, rows in ising.slab_partition(L, args.slabs):
+                sl = ising.Slab(L, row0, rows, device=device)
+                ising.ising_slab_init(sl, ising.ISING_INIT_RANDOM, seed)
+                slabs.append(sl)
+            def step(count, off):
+                ising.ising_slab_sweep(slabs, beta, count, seed, off, trace[:count])
+            launches = 2 * (args.slabs + 1)
+        else:
+            row0, rows = ising.slab_partition(L, world)[rank]
+            sl = ising.Slab(L, row0, rows, device=device)
+            ising.ising_slab_init(sl, ising.ISING_INIT_RANDOM, seed)
+            def step(count, off):
+                ising.slab_sweep(sl, beta, count, seed, off, trace[:count])
+            launches = 4
+        step(max(args.warmup, 1), 0)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk, torch.cuda.stream(stream):
+        e0.record(stream)
+        step(args.steps, args.warmup)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    max_ms = max_over_ranks(e0.elapsed_time(e1), world, device)
+    value = L * L * args.steps / (max_ms * 1e6)
+    res = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "ours",
+        "config": {"workload": f"msc4 L={L} random start seed {seed} beta={beta} as "
+                               f"{args.slabs if world == 1 else world} horizontal slabs with halo rows",
+                   "L": L, "layout": "msc4", "beta": beta, "parallelism": f"slabs{world}",
+                   "l2": "inputs larger than L2, no flush"},
+        "gpu_launches": launches * args.steps,
+        "clocks": clk.summary(),
+    }
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return res
 
 
 def rng_probe(ising, torch, L, seed, stream):
@@ -603,6 +709,8 @@ def main(argv=None):
         res = run_reference(args, world, rank)
     elif args.workload == "pt":
         res = run_pt_only(args, world, rank, local)
+    elif args.workload == "slabs":
+        res = run_slabs(args, world, rank, local)
     elif args.workload == "learned":
         import torch
 

@@ -135,6 +135,70 @@ ISING_API int ising_rng_probe(uint64_t n_blocks, uint64_t seed, uint64_t t, int3
                               uint64_t *count_dev, ising_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Horizontal slabs (Sec. 4: the lattice is cut into horizontal slabs, each   */
+/* kept in the single-GPU layout, and a slab's update needs only the boundary */
+/* rows of the slabs above and below).  Here those boundary rows are staged   */
+/* explicitly into halo rows: a slab holds rows row0 .. row0+rows-1 of the    */
+/* L x L lattice plus, in each colour plane, one halo row above (global row   */
+/* row0-1 mod L) and one below (row0+rows mod L).  The paper reaches the      */
+/* neighbours' rows through unified memory instead; explicit halos give the   */
+/* same reads and work within one process, across processes and across GPUs.  */
+/* Because the random numbers are keyed by the global site, a lattice swept   */
+/* as slabs is bit-identical to the same lattice swept whole.  MSC4 only.     */
+/* ------------------------------------------------------------------------ */
+
+/* One slab: two caller-owned device planes of rows + 2 rows each (plane row
+ * 0 = halo above, rows 1 .. rows = the slab's own rows, row rows + 1 = halo
+ * below), row stride row_stride_bytes (multiple of 16, planes 16-byte
+ * aligned, as for an MSC4 lattice).  Plain data; copy freely. */
+typedef struct {
+    void *black;              /* device pointer, colour 0, halo row above first */
+    void *white;              /* device pointer, colour 1 */
+    int64_t L;                /* side of the whole lattice (multiple of 64) */
+    int64_t row0;             /* global row of the first own row, 0 <= row0 < L */
+    int64_t rows;             /* own rows, 1 <= rows, row0 + rows <= L */
+    int32_t layout;           /* must be ISING_MSC4 */
+    int32_t reserved;         /* must be 0 */
+    int64_t row_stride_bytes; /* bytes between plane rows; >= L / 4 */
+} ising_slab_t;
+
+/* Bytes of one slab plane row (`row_bytes` = L / 4) and of one dense slab
+ * plane (`plane_bytes` = (rows + 2) * row_bytes).  Either output may be NULL.
+ * EINVAL: bad L, rows < 1, layout other than MSC4. */
+ISING_API int ising_slab_bytes(int64_t L, int64_t rows, int32_t layout, size_t *row_bytes, size_t *plane_bytes);
+
+/* Fill the slab's own rows of both planes exactly as ising_init_lattice fills
+ * those rows of the whole lattice; halo rows are not touched. */
+ISING_API int ising_slab_init(const ising_slab_t *slab, int32_t init, uint64_t seed, ising_stream_t stream);
+
+/* One half-sweep of colour `colour` over the slab's own rows at sweep index t
+ * (same rule and random numbers as ising_half_sweep).  The halo rows of the
+ * OTHER colour must hold the current neighbour rows (ising_slab_exchange, or
+ * the caller's own transfer).  obs_dev (colour 1 only) receives ADDED
+ * {sum of spins, sum over bonds} of the slab's own rows after the update,
+ * counting each bond once at its white end: summed over the slabs of a
+ * lattice they give the lattice's values. */
+ISING_API int ising_slab_half_sweep(const ising_slab_t *slab, double beta, int32_t colour, uint64_t seed,
+                                    uint64_t t, int64_t *obs_dev, ising_stream_t stream);
+
+/* Make the colour-`colour` halo rows of n slabs current, for slabs on the
+ * current device that together form one lattice: slab k covers the rows
+ * right after slab k-1 (slab 0 starts at row 0, slab n-1 ends at row L-1).
+ * The halo above slab k receives the last own row of slab k-1, the halo below
+ * it the first own row of slab k+1 (periodic: slab 0's upper neighbour is
+ * slab n-1; one slab is its own neighbour).  One launch, 2n row copies;
+ * 1 <= n <= 64. */
+ISING_API int ising_slab_exchange(const ising_slab_t *slabs, int32_t n, int32_t colour, ising_stream_t stream);
+
+/* n_sweeps sweeps of the lattice held as n slabs (arranged as for
+ * ising_slab_exchange): per sweep, white halos, every slab's black half-sweep,
+ * black halos, every slab's white half-sweep.  trace_dev as for ising_sweep
+ * (whole-lattice sums; the call zeroes it first).  The result equals
+ * ising_sweep on the whole lattice, bit for bit. */
+ISING_API int ising_slab_sweep(const ising_slab_t *slabs, int32_t n, double beta, int64_t n_sweeps, uint64_t seed,
+                               uint64_t sweep_offset, int64_t *trace_dev, ising_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Batches of lattices with replica exchange.  Not in the paper: the batched */
 /* form of its sweep.  n lattices (sides L[i], multiples of 32 up to 65536,  */
 /* MSC4 planes) are swept together in ONE persistent cooperative launch with */

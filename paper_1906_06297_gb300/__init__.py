@@ -43,6 +43,19 @@ class ising_lattice_t(ctypes.Structure):
     ]
 
 
+class ising_slab_t(ctypes.Structure):
+    _fields_ = [
+        ("black", ctypes.c_void_p),
+        ("white", ctypes.c_void_p),
+        ("L", ctypes.c_int64),
+        ("row0", ctypes.c_int64),
+        ("rows", ctypes.c_int64),
+        ("layout", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("row_stride_bytes", ctypes.c_int64),
+    ]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -62,6 +75,7 @@ def _load():
         P, i32, i64, u32, u64, dbl = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
                                       ctypes.c_uint64, ctypes.c_double)
         LP = ctypes.POINTER(ising_lattice_t)
+        SP = ctypes.POINTER(ising_slab_t)
         sig = {
             "ising_lattice_bytes": [i64, i32, P, P],
             "ising_thresholds": [dbl, P],
@@ -73,6 +87,11 @@ def _load():
             "ising_pack": [LP, LP, P],
             "ising_unpack": [LP, LP, P],
             "ising_rng_probe": [u64, u64, u64, i32, u32, P, P],
+            "ising_slab_bytes": [i64, i64, i32, P, P],
+            "ising_slab_init": [SP, i32, u64, P],
+            "ising_slab_half_sweep": [SP, dbl, i32, u64, u64, P, P],
+            "ising_slab_exchange": [SP, i32, i32, P],
+            "ising_slab_sweep": [SP, i32, dbl, i64, u64, u64, P, P],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -261,6 +280,162 @@ def _struct(lat) -> ising_lattice_t:
     if isinstance(lat, ising_lattice_t):
         return lat
     return lat.struct()
+
+
+# ---------------------------------------------------------------------------
+# Horizontal slabs with halo rows (Sec. 4)
+# ---------------------------------------------------------------------------
+def ising_slab_bytes(L: int, rows: int, layout: int = ISING_MSC4):
+    row = ctypes.c_size_t()
+    plane = ctypes.c_size_t()
+    _check(_load().ising_slab_bytes(L, rows, layout, ctypes.byref(row), ctypes.byref(plane)), "ising_slab_bytes")
+    return row.value, plane.value
+
+
+def _slab_struct(sl) -> ising_slab_t:
+    return sl if isinstance(sl, ising_slab_t) else sl.struct()
+
+
+def _slab_array(slabs):
+    arr = (ising_slab_t * len(slabs))(*[_slab_struct(x) for x in slabs])
+    return arr, len(slabs)
+
+
+def ising_slab_init(slab, init: int = ISING_INIT_RANDOM, seed: int = 0, stream=None):
+    _check(_load().ising_slab_init(ctypes.byref(_slab_struct(slab)), init, seed, _stream(stream)), "ising_slab_init")
+
+
+def ising_slab_half_sweep(slab, beta: float, colour: int, seed: int, t: int, obs=None, stream=None):
+    _check(_load().ising_slab_half_sweep(ctypes.byref(_slab_struct(slab)), float(beta), colour, seed, t, _addr(obs),
+                                         _stream(stream)), "ising_slab_half_sweep")
+
+
+def ising_slab_exchange(slabs, colour: int, stream=None):
+    arr, n = _slab_array(slabs)
+    _check(_load().ising_slab_exchange(arr, n, colour, _stream(stream)), "ising_slab_exchange")
+
+
+def ising_slab_sweep(slabs, beta: float, n_sweeps: int, seed: int, sweep_offset: int = 0, trace=None, stream=None):
+    arr, n = _slab_array(slabs)
+    _check(_load().ising_slab_sweep(arr, n, float(beta), n_sweeps, seed, sweep_offset, _addr(trace),
+                                    _stream(stream)), "ising_slab_sweep")
+
+
+def slab_partition(L: int, n: int):
+    """(row0, rows) of n horizontal slabs of an L x L lattice, sizes differing
+    by at most one row, in order from row 0."""
+    if n < 1 or n > L:
+        raise ValueError(f"cannot cut {L} rows into {n} slabs")
+    out, r0 = [], 0
+    for k in range(n):
+        rows = L // n + (1 if k < L % n else 0)
+        out.append((r0, rows))
+        r0 += rows
+    return out
+
+
+class Slab:
+    """Rows row0 .. row0+rows-1 of an L x L MSC4 lattice with one halo row
+    above and one below in each colour plane (plane row 0 and rows + 1), as
+    ``ising_slab_t`` describes.  The planes are uint8 tensors of shape
+    (rows + 2, row_bytes); ``device`` may be a CUDA device or, for the halo
+    exchange alone, the CPU."""
+
+    def __init__(self, L: int, row0: int, rows: int, device="cuda"):
+        import torch
+
+        self.L, self.row0, self.rows = int(L), int(row0), int(rows)
+        self.row_bytes, _ = ising_slab_bytes(self.L, self.rows)
+        self.black = torch.zeros((self.rows + 2, self.row_bytes), dtype=torch.uint8, device=device)
+        self.white = torch.zeros((self.rows + 2, self.row_bytes), dtype=torch.uint8, device=device)
+
+    def struct(self) -> ising_slab_t:
+        return ising_slab_t(self.black.data_ptr(), self.white.data_ptr(), self.L, self.row0, self.rows, ISING_MSC4, 0,
+                            self.row_bytes)
+
+    def plane(self, colour: int):
+        return self.black if colour == 0 else self.white
+
+    def own_numpy(self):
+        """Host copies of the own rows of both planes as uint64 words (rows x L/32)."""
+        import numpy as np
+
+        return tuple(np.ascontiguousarray(p[1:self.rows + 1].cpu().numpy()).view(np.uint64)
+                     for p in (self.black, self.white))
+
+    def load_own_numpy(self, black, white):
+        """Copy host words (rows x L/32 uint64) into the own rows of both planes."""
+        import numpy as np
+        import torch
+
+        for dst, src in ((self.black, black), (self.white, white)):
+            a = np.ascontiguousarray(src, dtype=np.uint64).view(np.uint8).reshape(self.rows, self.row_bytes)
+            dst[1:self.rows + 1].copy_(torch.from_numpy(a))
+
+
+def _world(group):
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return 0, 1
+    return dist.get_rank(group), dist.get_world_size(group)
+
+
+def exchange_halos(slab: Slab, colour: int, group=None, stream=None):
+    """Make the colour-`colour` halo rows of this rank's slab current.  Rank r
+    holds the r-th slab of the lattice (ranks in row order, periodic): its
+    halo above receives the last own row of rank r-1, its halo below the first
+    own row of rank r+1.  One process: the library's copy (the slab is its own
+    neighbour).  Several: point-to-point messages of one row each through
+    torch.distributed (NCCL between GPUs), tagged 0 for rows travelling down
+    and 1 for rows travelling up; with two ranks both messages between the
+    pair are posted in the same order on both sides, so they also match where
+    tags are ignored."""
+    import torch.distributed as dist
+
+    rank, world = _world(group)
+    if world == 1:
+        ising_slab_exchange([slab], colour, stream)
+        return
+    p = slab.plane(colour)
+    up, down = (rank - 1) % world, (rank + 1) % world
+    peer = (lambda r: dist.get_global_rank(group, r)) if group is not None else (lambda r: r)
+    ops = [
+        dist.P2POp(dist.isend, p[slab.rows], peer(down), group, tag=0),  # my last row: halo above `down`
+        dist.P2POp(dist.isend, p[1], peer(up), group, tag=1),            # my first row: halo below `up`
+        dist.P2POp(dist.irecv, p[0], peer(up), group, tag=0),
+        dist.P2POp(dist.irecv, p[slab.rows + 1], peer(down), group, tag=1),
+    ]
+    for w in dist.batch_isend_irecv(ops):
+        w.wait()
+
+
+def slab_sweep(slab: Slab, beta: float, n_sweeps: int, seed: int, sweep_offset: int = 0, trace=None, group=None,
+               half_sweep=None, stream=None):
+    """n_sweeps sweeps of a lattice distributed as one slab per rank (Sec. 4).
+    Per sweep: white halos, black half-sweep, black halos, white half-sweep;
+    `trace` (n_sweeps x 2 int64, on the slab's device) ends with the
+    whole-lattice sums {sum of spins, sum over bonds} after each sweep.  The
+    lattice equals ising_sweep of the whole lattice bit for bit.
+
+    ``half_sweep(slab, beta, colour, seed, t, obs)`` does the update of one
+    colour of the slab's own rows; the default is the library's
+    ising_slab_half_sweep.  Replacing it lets the exchange and ordering logic
+    run against another implementation of the same rule."""
+    import torch.distributed as dist
+
+    hs = half_sweep or (lambda sl, b, c, sd, t, obs: ising_slab_half_sweep(sl, b, c, sd, t, obs, stream))
+    _, world = _world(group)
+    if trace is not None:
+        trace.zero_()
+    for k in range(n_sweeps):
+        t = sweep_offset + k
+        exchange_halos(slab, 1, group, stream)
+        hs(slab, beta, 0, seed, t, None)
+        exchange_halos(slab, 0, group, stream)
+        hs(slab, beta, 1, seed, t, trace[k] if trace is not None else None)
+    if trace is not None and world > 1:
+        dist.all_reduce(trace, group=group)
 
 
 # ---------------------------------------------------------------------------

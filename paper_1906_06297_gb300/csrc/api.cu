@@ -114,6 +114,11 @@ int half_sweep_impl(const ising_lattice_t *lat, const Accept &acc, const RoundKe
         p.tgt = (uint64_t *)(colour == 0 ? lat->black : lat->white);
         p.src = (const uint64_t *)(colour == 0 ? lat->white : lat->black);
         p.L = lat->L;
+        p.rows = lat->L;
+        p.row0 = 0;
+        p.wrap_row = lat->L;  // periodic: row L is row 0
+        p.wrap_to = 0;
+        p.first_up = lat->L - 1;
         p.wpr = lat->L / 32;
         p.stride = lat->row_stride_bytes / 8;
         p.qrow = lat->L / 8;
@@ -140,6 +145,113 @@ int half_sweep_impl(const ising_lattice_t *lat, const Accept &acc, const RoundKe
         e = int8_half_sweep(p, colour, s);
     }
     return e == cudaSuccess ? ISING_OK : cuda_fail(e, "half-sweep launch");
+}
+
+constexpr int kMaxSlabs = kMaxHaloRows / 2;
+
+size_t slab_plane_bytes(const ising_slab_t *sl)
+{
+    return (size_t)(sl->rows + 1) * (size_t)sl->row_stride_bytes + (size_t)(sl->L / 4);
+}
+
+int check_slab(const ising_slab_t *sl)
+{
+    if (sl == nullptr) return fail(ISING_EINVAL, "slab is NULL");
+    if (sl->layout != ISING_MSC4) return fail(ISING_EINVAL, "slabs support the MSC4 layout only");
+    size_t row = 0;
+    int rc = row_bytes_of(sl->L, sl->layout, &row);
+    if (rc) return rc;
+    if (sl->reserved != 0) return fail(ISING_EINVAL, "reserved field must be 0");
+    if (sl->rows < 1) return fail(ISING_EINVAL, "slab rows = %lld must be >= 1", (long long)sl->rows);
+    if (sl->row0 < 0 || sl->row0 >= sl->L || sl->rows > sl->L - sl->row0)
+        return fail(ISING_EINVAL, "slab rows [%lld, %lld) are not inside 0..L-1 (L = %lld)", (long long)sl->row0,
+                    (long long)(sl->row0 + sl->rows), (long long)sl->L);
+    if (sl->row_stride_bytes < (int64_t)row)
+        return fail(ISING_EINVAL, "row stride %lld < row size %zu", (long long)sl->row_stride_bytes, row);
+    if (sl->row_stride_bytes % 16 != 0) return fail(ISING_EINVAL, "MSC4 row stride must be a multiple of 16");
+    if (((uintptr_t)sl->black | (uintptr_t)sl->white) % 16 != 0)
+        return fail(ISING_EINVAL, "MSC4 planes must be 16-byte aligned");
+    const size_t plane = slab_plane_bytes(sl);
+    const char *b = (const char *)sl->black, *w = (const char *)sl->white;
+    if (b == w || (b < w && b + plane > w) || (w < b && w + plane > b)) return fail(ISING_EINVAL, "planes overlap");
+    rc = check_device_range(sl->black, plane, "black slab plane");
+    if (rc) return rc;
+    return check_device_range(sl->white, plane, "white slab plane");
+}
+
+// n slabs that tile the rows of one lattice in order, with no plane shared.
+int check_slab_set(const ising_slab_t *slabs, int32_t n)
+{
+    if (slabs == nullptr) return fail(ISING_EINVAL, "slabs is NULL");
+    if (n < 1 || n > kMaxSlabs) return fail(ISING_EINVAL, "n = %d slabs, must be 1..%d", (int)n, kMaxSlabs);
+    int64_t next = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        int rc = check_slab(&slabs[k]);
+        if (rc) return rc;
+        if (slabs[k].L != slabs[0].L) return fail(ISING_EINVAL, "slab %d has another L", (int)k);
+        if (slabs[k].row0 != next)
+            return fail(ISING_EINVAL, "slab %d starts at row %lld, expected %lld", (int)k, (long long)slabs[k].row0,
+                        (long long)next);
+        next += slabs[k].rows;
+    }
+    if (next != slabs[0].L)
+        return fail(ISING_EINVAL, "slabs cover rows 0..%lld, not the lattice's %lld", (long long)next - 1,
+                    (long long)slabs[0].L);
+    for (int32_t a = 0; a < n; ++a)
+        for (int32_t b = a + 1; b < n; ++b) {
+            const char *pa[2] = {(const char *)slabs[a].black, (const char *)slabs[a].white};
+            const char *pb[2] = {(const char *)slabs[b].black, (const char *)slabs[b].white};
+            const size_t na = slab_plane_bytes(&slabs[a]), nb = slab_plane_bytes(&slabs[b]);
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j)
+                    if (pa[i] < pb[j] + nb && pb[j] < pa[i] + na)
+                        return fail(ISING_EINVAL, "planes of slabs %d and %d overlap", (int)a, (int)b);
+        }
+    return ISING_OK;
+}
+
+int slab_half_sweep_impl(const ising_slab_t *sl, const Accept &acc, const RoundKeys &rk, int colour, uint64_t t,
+                         int64_t *obs, cudaStream_t s)
+{
+    const int64_t stride = sl->row_stride_bytes / 8;
+    Msc4SweepParams p;
+    // local row 0 = plane row 1; the halos are local rows -1 and `rows`
+    p.tgt = (uint64_t *)(colour == 0 ? sl->black : sl->white) + stride;
+    p.src = (const uint64_t *)(colour == 0 ? sl->white : sl->black) + stride;
+    p.L = sl->L;
+    p.rows = sl->rows;
+    p.row0 = sl->row0;
+    p.wrap_row = sl->rows + 1;  // only the prefetch after the last row gets there
+    p.wrap_to = -1;
+    p.first_up = -1;
+    p.wpr = sl->L / 32;
+    p.stride = stride;
+    p.qrow = sl->L / 8;
+    p.total = ((p.wpr + 63) / 64) * sl->rows;
+    p.c2 = (uint32_t)t;
+    p.c3 = counter_word3(colour, kPurposeMetropolis, t);
+    p.acc = acc;
+    p.rk = rk;
+    p.obs = (long long *)obs;
+    cudaError_t e = msc4_half_sweep(p, colour, s);
+    return e == cudaSuccess ? ISING_OK : cuda_fail(e, "slab half-sweep launch");
+}
+
+int slab_exchange_impl(const ising_slab_t *slabs, int32_t n, int colour, cudaStream_t s)
+{
+    HaloCopy c;
+    for (int32_t k = 0; k < n; ++k) {
+        const ising_slab_t &me = slabs[k], &up = slabs[(k + n - 1) % n], &dn = slabs[(k + 1) % n];
+        auto row = [colour](const ising_slab_t &sl, int64_t r) {
+            return (uint64_t *)((char *)(colour == 0 ? sl.black : sl.white) + r * sl.row_stride_bytes);
+        };
+        c.src[2 * k] = row(up, up.rows);  // last own row of the slab above
+        c.dst[2 * k] = row(me, 0);
+        c.src[2 * k + 1] = row(dn, 1);  // first own row of the slab below
+        c.dst[2 * k + 1] = row(me, me.rows + 1);
+    }
+    cudaError_t e = msc4_copy_rows(c, 2 * n, slabs[0].L / 32, s);
+    return e == cudaSuccess ? ISING_OK : cuda_fail(e, "halo copy launch");
 }
 
 }  // namespace
@@ -260,7 +372,8 @@ ISING_API int ising_init_lattice(const ising_lattice_t *lat, int32_t init, uint6
     for (int colour = 0; colour < 2; ++colour) {
         void *plane = colour == 0 ? lat->black : lat->white;
         cudaError_t e = lat->layout == ISING_MSC4
-                            ? msc4_init((uint64_t *)plane, colour, lat->L, lat->row_stride_bytes / 8, init, seed, s)
+                            ? msc4_init((uint64_t *)plane, colour, lat->L, lat->L, 0, lat->row_stride_bytes / 8,
+                                        init, seed, s)
                             : int8_init((int8_t *)plane, colour, lat->L, lat->row_stride_bytes, init, seed, s);
         if (e != cudaSuccess) return cuda_fail(e, "init launch");
     }
@@ -309,6 +422,92 @@ ISING_API int ising_sweep(const ising_lattice_t *lat, double beta, int64_t n_swe
         if (rc) return rc;
         rc = half_sweep_impl(lat, acc, rk, 1, t, trace_dev ? trace_dev + 2 * k : nullptr, s);
         if (rc) return rc;
+    }
+    return ISING_OK;
+}
+
+ISING_API int ising_slab_bytes(int64_t L, int64_t rows, int32_t layout, size_t *row_bytes, size_t *plane_bytes)
+{
+    if (layout != ISING_MSC4) return fail(ISING_EINVAL, "slabs support the MSC4 layout only");
+    size_t row = 0;
+    int rc = row_bytes_of(L, layout, &row);
+    if (rc) return rc;
+    if (rows < 1 || rows > L) return fail(ISING_EINVAL, "slab rows = %lld must be in 1..L", (long long)rows);
+    if (row_bytes) *row_bytes = row;
+    if (plane_bytes) *plane_bytes = row * (size_t)(rows + 2);
+    return ISING_OK;
+}
+
+ISING_API int ising_slab_init(const ising_slab_t *slab, int32_t init, uint64_t seed, ising_stream_t stream)
+{
+    int rc = check_slab(slab);
+    if (rc) return rc;
+    if (init < ISING_INIT_RANDOM || init > ISING_INIT_DOWN) return fail(ISING_EINVAL, "unknown init mode %d", init);
+    const int64_t stride = slab->row_stride_bytes / 8;
+    for (int colour = 0; colour < 2; ++colour) {
+        uint64_t *own = (uint64_t *)(colour == 0 ? slab->black : slab->white) + stride;
+        cudaError_t e = msc4_init(own, colour, slab->L, slab->rows, slab->row0, stride, init, seed,
+                                  (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "slab init launch");
+    }
+    return ISING_OK;
+}
+
+ISING_API int ising_slab_half_sweep(const ising_slab_t *slab, double beta, int32_t colour, uint64_t seed,
+                                    uint64_t t, int64_t *obs_dev, ising_stream_t stream)
+{
+    int rc = check_slab(slab);
+    if (rc) return rc;
+    if (colour != 0 && colour != 1) return fail(ISING_EINVAL, "colour must be 0 or 1");
+    if (obs_dev != nullptr) {
+        if (colour != 1) return fail(ISING_EINVAL, "observables are fused into the white half-sweep only");
+        rc = check_device_range(obs_dev, 2 * sizeof(int64_t), "obs");
+        if (rc) return rc;
+    }
+    Accept acc;
+    uint64_t T[5];
+    rc = build_accept(beta, &acc, T);
+    if (rc) return rc;
+    return slab_half_sweep_impl(slab, acc, make_round_keys(seed), colour, t, obs_dev, (cudaStream_t)stream);
+}
+
+ISING_API int ising_slab_exchange(const ising_slab_t *slabs, int32_t n, int32_t colour, ising_stream_t stream)
+{
+    int rc = check_slab_set(slabs, n);
+    if (rc) return rc;
+    if (colour != 0 && colour != 1) return fail(ISING_EINVAL, "colour must be 0 or 1");
+    return slab_exchange_impl(slabs, n, colour, (cudaStream_t)stream);
+}
+
+ISING_API int ising_slab_sweep(const ising_slab_t *slabs, int32_t n, double beta, int64_t n_sweeps, uint64_t seed,
+                               uint64_t sweep_offset, int64_t *trace_dev, ising_stream_t stream)
+{
+    int rc = check_slab_set(slabs, n);
+    if (rc) return rc;
+    if (n_sweeps < 0) return fail(ISING_EINVAL, "n_sweeps = %lld < 0", (long long)n_sweeps);
+    Accept acc;
+    uint64_t T[5];
+    rc = build_accept(beta, &acc, T);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (trace_dev != nullptr && n_sweeps > 0) {
+        rc = check_device_range(trace_dev, (size_t)n_sweeps * 2 * sizeof(int64_t), "trace");
+        if (rc) return rc;
+        cudaError_t e = cudaMemsetAsync(trace_dev, 0, (size_t)n_sweeps * 2 * sizeof(int64_t), s);
+        if (e != cudaSuccess) return cuda_fail(e, "trace memset");
+    }
+    const RoundKeys rk = make_round_keys(seed);
+    for (int64_t k = 0; k < n_sweeps; ++k) {
+        const uint64_t t = sweep_offset + (uint64_t)k;
+        for (int colour = 0; colour < 2; ++colour) {
+            rc = slab_exchange_impl(slabs, n, 1 - colour, s);  // halos of the source colour
+            if (rc) return rc;
+            for (int32_t j = 0; j < n; ++j) {
+                rc = slab_half_sweep_impl(&slabs[j], acc, rk, colour, t,
+                                          colour == 1 && trace_dev ? trace_dev + 2 * k : nullptr, s);
+                if (rc) return rc;
+            }
+        }
     }
     return ISING_OK;
 }

@@ -79,10 +79,21 @@ struct Accept {
 // ---------------------------------------------------------------------------
 // Launch parameter blocks (passed by value: they live in the constant bank).
 // ---------------------------------------------------------------------------
+// The planes hold `rows` target rows (local rows 0 .. rows-1, global rows
+// row0 .. row0+rows-1 of the L x L lattice).  Source rows are addressed by
+// local index too: for the whole periodic lattice (rows = L, row0 = 0) the
+// row above row 0 is row L-1 and the row below row L-1 is row 0; for a slab
+// with halo rows, local rows -1 and `rows` are the halos and nothing wraps.
+// wrap_row / wrap_to say where the downward walk over source rows jumps back
+// (L -> 0 for the periodic lattice; rows+1 -> -1 for a slab, a row that is
+// fetched but never used), first_up is the source row above local row 0.
 struct Msc4SweepParams {
-    uint64_t *tgt;        // plane being updated
-    const uint64_t *src;  // other colour
-    int64_t L;            // side
+    uint64_t *tgt;        // target plane, local row 0
+    const uint64_t *src;  // source plane (other colour), local row 0
+    int64_t L;            // side of the whole lattice
+    int64_t rows;         // target rows in this plane
+    int64_t row0;         // global row of local row 0
+    int64_t wrap_row, wrap_to, first_up;
     int64_t wpr;          // words per row = L / 32
     int64_t stride;       // row stride in words
     int64_t qrow;         // Philox blocks per plane row = L / 8

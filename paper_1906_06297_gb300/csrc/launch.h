@@ -15,9 +15,18 @@ struct DeviceInfo {
 };
 
 // Multi-spin-coded (4 bits per spin) lattice.
-cudaError_t msc4_init(uint64_t *plane, int colour, int64_t L, int64_t stride_words, int mode,
-                      uint64_t seed, cudaStream_t s);
+// Rows row0 .. row0+rows-1 of an L x L lattice's plane of one colour; `plane`
+// points at the first of them.
+cudaError_t msc4_init(uint64_t *plane, int colour, int64_t L, int64_t rows, int64_t row0, int64_t stride_words,
+                      int mode, uint64_t seed, cudaStream_t s);
 cudaError_t msc4_half_sweep(const Msc4SweepParams &p, int colour, cudaStream_t s);
+// Copies n rows of `words` uint64 each: row k from src[k] to dst[k] (n <= kMaxHaloRows).
+constexpr int kMaxHaloRows = 128;
+struct HaloCopy {
+    const uint64_t *src[kMaxHaloRows];
+    uint64_t *dst[kMaxHaloRows];
+};
+cudaError_t msc4_copy_rows(const HaloCopy &c, int n, int64_t words, cudaStream_t s);
 cudaError_t msc4_observables(const uint64_t *black, const uint64_t *white, int64_t L,
                              int64_t stride_words, long long *out, cudaStream_t s);
 cudaError_t msc4_pack(const int8_t *src, int64_t src_stride, uint64_t *dst, int64_t dst_stride_words,

@@ -96,14 +96,16 @@ __global__ void __launch_bounds__(kThreads, ISING_MSC4_MIN_BLOCKS)
     const int64_t nw = (int64_t)gridDim.x * kWarps;
     const int64_t begin = gw * p.total / nw;
     const int64_t end = (gw + 1) * p.total / nw;
-    const int64_t L = p.L, stride = p.stride;
+    const int64_t R = p.rows, stride = p.stride;
+    // row r (local) has the neighbour word on the left iff r + pofs is even
+    const int64_t pofs = p.row0 + COLOR;
 
     uint32_t ones = 0, dsum = 0, nrows = 0;
 
     for (int64_t lin = begin; lin < end;) {
-        const int64_t chunk = lin / L;
-        const int64_t r0 = lin - chunk * L;
-        const int64_t r1 = min(L, r0 + (end - lin));
+        const int64_t chunk = lin / R;
+        const int64_t r0 = lin - chunk * R;
+        const int64_t r1 = min(R, r0 + (end - lin));
         lin += r1 - r0;
 
         const int64_t w0 = chunk * 64 + 2 * lane;
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(kThreads, ISING_MSC4_MIN_BLOCKS)
 
         const uint64_t *col = p.src + w0;  // this lane's column of the source plane
         auto edge_of = [&](const uint64_t *row, int64_t r) -> uint32_t {
-            const bool left = ((r + COLOR) & 1) == 0;
+            const bool left = ((r + pofs) & 1) == 0;
             const uint32_t *h = reinterpret_cast<const uint32_t *>(row) + (left ? off_left : off_right);
             return ld32_if(h, left ? edge_left : edge_right);
         };
@@ -127,11 +129,12 @@ __global__ void __launch_bounds__(kThreads, ISING_MSC4_MIN_BLOCKS)
         // rows r-1, r, r+1 of the source and row r of the target are in
         // registers at the top of each iteration; rows r+2 / r+1 are fetched
         // before the arithmetic of row r
-        int64_t rn = r0 + 2 >= L ? r0 + 2 - L : r0 + 2;  // row of the next source fetch
+        // row of the next source fetch
+        int64_t rn = r0 + 2 >= p.wrap_row ? r0 + 2 - p.wrap_row + p.wrap_to : r0 + 2;
         const uint64_t *pn = col + rn * stride;
-        const uint64_t *p_up = col + (r0 == 0 ? L - 1 : r0 - 1) * stride;
+        const uint64_t *p_up = col + (r0 == 0 ? p.first_up : r0 - 1) * stride;
         const uint64_t *p_cur = col + r0 * stride;
-        const uint64_t *p_dn = col + (r0 + 1 == L ? 0 : r0 + 1) * stride;
+        const uint64_t *p_dn = col + (r0 + 1 == p.wrap_row ? p.wrap_to : r0 + 1) * stride;
         uint4 up = ld128_if(p_up, valid);
         uint4 cur = ld128_if(p_cur, valid);
         uint4 dn = ld128_if(p_dn, valid);
@@ -139,7 +142,7 @@ __global__ void __launch_bounds__(kThreads, ISING_MSC4_MIN_BLOCKS)
         uint32_t edge_dn = edge_of(p_dn, r0 + 1);
         uint64_t *tp = p.tgt + w0 + r0 * stride;  // target row r
         uint4 tg = ld128_if(tp, valid);
-        uint64_t q0 = (uint64_t)r0 * (uint64_t)p.qrow + 4 * (uint64_t)w0;
+        uint64_t q0 = (uint64_t)(p.row0 + r0) * (uint64_t)p.qrow + 4 * (uint64_t)w0;
 
         for (int64_t r = r0; r < r1; ++r) {
             const uint4 nxt = ld128_if(pn, valid);
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(kThreads, ISING_MSC4_MIN_BLOCKS)
 
             // side words, as 32-bit halves: .x/.y = lo/hi of word w0, .z/.w of w0+1
             uint4 sd;
-            if (((r + COLOR) & 1) == 0) {  // left neighbour word: shift up one spin
+            if (((r + pofs) & 1) == 0) {  // left neighbour word: shift up one spin
                 const uint32_t prev = __shfl_up_sync(0xffffffffu, cur.w, 1);
                 const uint32_t W = edge_left ? edge : prev;
                 sd.x = __funnelshift_l(W, cur.x, 4);
@@ -194,9 +197,9 @@ __global__ void __launch_bounds__(kThreads, ISING_MSC4_MIN_BLOCKS)
             tp += stride;
             q0 += (uint64_t)p.qrow;
             pn += stride;
-            if (++rn == L) {
-                rn = 0;
-                pn = col;
+            if (++rn == p.wrap_row) {
+                rn = p.wrap_to;
+                pn = col + rn * stride;
             }
         }
     }
@@ -258,14 +261,14 @@ cudaError_t launch_sweep_colour(const Msc4SweepParams &p, cudaStream_t s)
 // Initial state: thread per word.  Random: spin n of word (i, w) has plane site
 // i*L/2 + 16w + n and is +1 iff its purpose-1 draw at t = 0 is below 2^31.
 // ---------------------------------------------------------------------------
-__global__ void msc4_init_kernel(uint64_t *plane, int64_t L, int64_t stride, int mode, uint32_t c3,
-                                 const __grid_constant__ RoundKeys rk)
+__global__ void msc4_init_kernel(uint64_t *plane, int64_t L, int64_t rows, int64_t row0, int64_t stride, int mode,
+                                 uint32_t c3, const __grid_constant__ RoundKeys rk)
 {
     const int64_t wpr = L / 32, qrow = L / 8;
-    const int64_t n = L * wpr;
+    const int64_t n = rows * wpr;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx / wpr, w = idx - i * wpr;
+        const int64_t i = idx / wpr, w = idx - i * wpr;  // local row i = global row row0 + i
         uint64_t word;
         if (mode == 1) {
             word = 0x1111111111111111ull;
@@ -273,7 +276,7 @@ __global__ void msc4_init_kernel(uint64_t *plane, int64_t L, int64_t stride, int
             word = 0;
         } else {
             word = 0;
-            const uint64_t q0 = (uint64_t)i * qrow + 4 * (uint64_t)w;
+            const uint64_t q0 = (uint64_t)(row0 + i) * qrow + 4 * (uint64_t)w;
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const uint4 u = philox((uint32_t)q0 + b, (uint32_t)(q0 >> 32), 0u, c3, rk);
@@ -367,13 +370,31 @@ cudaError_t msc4_half_sweep(const Msc4SweepParams &p, int colour, cudaStream_t s
     return colour == 0 ? launch_sweep_colour<0>(p, s) : launch_sweep_colour<1>(p, s);
 }
 
-cudaError_t msc4_init(uint64_t *plane, int colour, int64_t L, int64_t stride_words, int mode, uint64_t seed,
-                      cudaStream_t s)
+cudaError_t msc4_init(uint64_t *plane, int colour, int64_t L, int64_t rows, int64_t row0, int64_t stride_words,
+                      int mode, uint64_t seed, cudaStream_t s)
 {
     const RoundKeys rk = make_round_keys(seed);
-    const int64_t n = L * (L / 32);
-    msc4_init_kernel<<<grid_for(n, 256), 256, 0, s>>>(plane, L, stride_words, mode,
+    const int64_t n = rows * (L / 32);
+    msc4_init_kernel<<<grid_for(n, 256), 256, 0, s>>>(plane, L, rows, row0, stride_words, mode,
                                                       counter_word3(colour, kPurposeInit, 0), rk);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Halo rows of slabs: block k copies row k (16-byte aligned, an even number of
+// words) with 128-bit accesses.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) msc4_copy_rows_kernel(const __grid_constant__ HaloCopy c, int64_t words)
+{
+    const uint4 *src = reinterpret_cast<const uint4 *>(c.src[blockIdx.x]);
+    uint4 *dst = reinterpret_cast<uint4 *>(c.dst[blockIdx.x]);
+    for (int64_t v = threadIdx.x; v < words / 2; v += blockDim.x) dst[v] = src[v];
+}
+
+cudaError_t msc4_copy_rows(const HaloCopy &c, int n, int64_t words, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    msc4_copy_rows_kernel<<<n, 256, 0, s>>>(c, words);
     return cudaGetLastError();
 }
 
