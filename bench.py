@@ -51,7 +51,9 @@ def parse_args(argv=None):
     p.add_argument("--no-batch", action="store_true", help="skip the batched parallel-tempering leg")
     p.add_argument("--pt-sweeps", type=int, default=10000)
     p.add_argument("--slabs", type=int, default=4, help="slabs on one GPU for the slab leg / workload")
-    p.add_argument("--workload", choices=["sweep", "pt", "learned", "slabs"], default="sweep",
+    p.add_argument("--no-binder", action="store_true", help="skip the Binder-crossing leg")
+    p.add_argument("--binder-sweeps", type=int, default=100000)
+    p.add_argument("--workload", choices=["sweep", "pt", "learned", "slabs", "binder"], default="sweep",
                    help="sweep: the 65536^2 lattice (default); pt / learned: only that leg")
     p.add_argument("--no-learned", action="store_true", help="skip the learned block-proposal leg")
     p.add_argument("--learned-steps", type=int, default=1000, help="training steps of the proposal network")
@@ -312,6 +314,8 @@ def run_ours(args, world, rank, local):
         if not args.no_learned:
             result["learned"] = run_learned(ising, torch, args, device, stream)
         result["slab_leg"] = run_slab_leg(ising, torch, args, device, stream, value / world)
+        if not args.no_binder:
+            result["binder"] = run_binder_leg(args, device, stream)
     if world > 1:
         import torch.distributed as dist
 
@@ -353,6 +357,36 @@ def run_slab_leg(ising, torch, args, device, stream, whole_flips_per_ns):
     return {"slabs": k, "L": L, "sweeps": steps, "flips_per_ns": round(rate, 2),
             "vs_whole_lattice": round(rate / whole_flips_per_ns, 4),
             "gpu_launches_per_sweep": 2 * (k + 1)}
+
+
+def run_binder_leg(args, device, stream):
+    """Binder cumulant crossing (Sec. 5.3, Fig. 6) of 64^2, 128^2 and 256^2
+    lattices from the batched sampler with replica exchange: 8 ladders of 16
+    betas in [0.42, 0.46] per size, all sizes in one batch."""
+    import torch
+
+    from paper_1906_06297_gb300 import binder
+
+    sizes, ladders, S = (64, 128, 256), 8, 16
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    res = binder.binder_study(sizes=sizes, ladders=ladders, ladder_size=S, beta_lo=0.42, beta_hi=0.46,
+                              sweeps=args.binder_sweeps, thermalize=args.binder_sweeps // 10, record_every=2,
+                              chunks=10, seed=args.seed, device=device, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    spins = ladders * S * sum(x * x for x in sizes)
+    total_sweeps = res["sweeps"] + res["thermalize"]
+    return {"workload": f"sizes {list(sizes)}, {ladders} ladders x {S} betas in [0.42, 0.46] per size, "
+                        f"exchange every 2 sweeps, {res['thermalize']} + {res['sweeps']} sweeps",
+            "beta_c": round(binder.BETA_C, 7),
+            "crossings": {k: [round(x, 5) for x in v] for k, v in res["crossings"].items()},
+            "beta_nearest_c": round(res["beta_nearest_c"], 5),
+            "U_at_beta_nearest_c": {k: round(v, 4) for k, v in res["U_at_beta_nearest_c"].items()},
+            "U_err_max": {k: round(max(v), 4) for k, v in res["U_err"].items()},
+            "ms": round(ms, 1), "flips_per_ns": round(spins * total_sweeps / (ms * 1e6), 1)}
 
 
 def run_slabs(args, world, rank, local):
@@ -713,6 +747,17 @@ def main(argv=None):
         res = run_pt_only(args, world, rank, local)
     elif args.workload == "slabs":
         res = run_slabs(args, world, rank, local)
+    elif args.workload == "binder":
+        import torch
+
+        import paper_1906_06297_gb300 as ising
+
+        ising.build()
+        torch.cuda.set_device(local)
+        device = torch.device("cuda", local)
+        bl = run_binder_leg(args, device, torch.cuda.Stream(device=device))
+        res = {"metric": METRIC, "value": bl["flips_per_ns"], "unit": UNIT, "impl": "ours",
+               "config": {"workload": bl["workload"]}, "binder": bl}
     elif args.workload == "learned":
         import torch
 
