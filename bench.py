@@ -59,6 +59,7 @@ def parse_args(argv=None):
     p.add_argument("--learned-steps", type=int, default=1000, help="training steps of the proposal network")
     p.add_argument("--learned-cycles", type=int, default=400, help="measured sweep + move cycles")
     p.add_argument("--learned-configs", type=int, default=100000, help="training configurations")
+    p.add_argument("--learned-chains", type=int, default=1024, help="chains of the measured learned cycles")
     return p.parse_args(argv)
 
 
@@ -627,12 +628,55 @@ def run_pt_only(args, world, rank, local):
             "pt_batch": pt}
 
 
+def time_network(ising, torch, L, C, params, beta, seed, device, stream, reps=10):
+    """CUDA-event times of one network evaluation of C chains of side L: the
+    full forward (the state before a move) and the flipped-band forward (the
+    proposed state), with the tensor-core FLOPs of the two 32 -> 32 layers."""
+    import numpy as np
+
+    mv = ising.BlockMove(L, C, beta, device=device)
+    mv.batch.init(ising.ISING_INIT_RANDOM, seed, stream)
+    mv.batch.run(20, seed, 0, 0, False, None, True, stream)
+    nb = (L // 8) ** 2
+    flips = torch.from_numpy(np.random.default_rng(seed).integers(0, nb, C).astype(np.int32)).to(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, fn in (("full_forward", lambda: ising.ising_net_forward(L, C, mv.black, mv.white, None, params, mv.lx,
+                                                                      mv.work, False, stream)),
+                     ("flipped_band_forward", lambda: ising.ising_net_forward_flipped(
+                         L, C, mv.black, mv.white, flips, params, mv.lx, mv.lxp, mv.work, stream))):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        out[name + "_ms"] = round(e0.elapsed_time(e1) / reps, 4)
+    ising.ising_net_check(stream)
+    px = C * L * L
+    conv_flops = 2 * 2 * (9 * 32) * 32 * px  # two 32 -> 32 layers, 2 flops per multiply-add
+    peaks, source = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    ach = conv_flops / (out["full_forward_ms"] * 1e-3) / 1e12
+    out["conv_tflop_per_forward"] = round(conv_flops / 1e12, 4)
+    out["roofline_lower_bound"] = {
+        "bound": "tensor", "achieved": round(ach, 2), "peak": peak, "unit": "TFLOP/s",
+        "frac": round(ach / peak, 4), "peak_source": f"bf16 burst, {source}",
+        "note": "tensor-core FLOPs of the two 32->32 layers over the whole forward (4 kernels); the conv "
+                "kernel's own share of the forward is in the ncu launch list"}
+    del mv
+    return out
+
+
 def run_learned(ising, torch, args, device, stream):
-    """The learned form at beta_c on 128 x 128 lattices: train the proposal
-    network on configurations from the plain sweep (10 sweeps apart), then
-    compare, from the same starting states, cycles of (one sweep) with cycles
-    of (one sweep + one uniform block move) and (one sweep + one network block
-    move): integrated autocorrelation times per cycle of |m| and E, their
+    """The learned form at beta_c on 1024 chains of 128 x 128: train the
+    proposal network on configurations from the plain sweep (10 sweeps apart),
+    then compare, from the same starting states, cycles of (one sweep) with
+    cycles of (one sweep + one uniform block move) and (one sweep + one network
+    block move): integrated autocorrelation times per cycle of |m| and E, their
     effective samples per GPU second, and block acceptance rates."""
     import numpy as np
 
@@ -647,7 +691,8 @@ def run_learned(ising, torch, args, device, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     train_ms = e0.elapsed_time(e1)
-    C, cycles, warm = 128, args.learned_cycles, 500
+    C, cycles, warm = args.learned_chains, args.learned_cycles, 500
+    net = time_network(ising, torch, L, C, tr["params"], beta, seed, device, stream)
     variants = {}
     for name in ("plain", "uniform", "learned"):
         mv = ising.BlockMove(L, C, beta, device=device)
@@ -681,11 +726,12 @@ def run_learned(ising, torch, args, device, stream):
                                                if name != "plain" else None),
                           "mean_e": round(float(np.mean(np.concatenate(e))), 5)}
         del mv, trace
+    ising.ising_net_check(stream)
     return {"workload": f"{C} chains of {L}x{L} at beta={beta}; network trained for {args.learned_steps} Adam steps "
                         f"(batch 64) on {args.learned_configs} plain-sweep configurations 10 sweeps apart; "
                         f"{cycles} measured cycles after {warm} sweeps",
             "train_ms": round(train_ms, 1), "train_loss_first_last": [round(tr["loss"][0], 4), round(tr["loss"][-1], 4)],
-            "variants": variants,
+            "network": net, "variants": variants,
             "note": "tau from series of this length are lower bounds where they approach the run length"}
 
 

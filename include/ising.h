@@ -306,10 +306,12 @@ ISING_API int ising_batch_run_noalloc(int64_t n, const int64_t *L, int32_t ladde
 /* lattice c's planes at word c * L * L/32 of the black and white buffers.    */
 /* Network: three 3x3 periodic conv layers of 32 channels with GELU (the    */
 /* first reads the spins), a 3x3 conv to one channel, and the mean over each  */
-/* 8 x 8 block gives that block's logit (b = by * L/8 + bx).  Weights are    */
-/* rounded to bfloat16 for every use; products accumulate in FP32; every    */
-/* reduction has a fixed order, so logits are a deterministic function of    */
-/* the state.  Parameters: one FP32 vector of ising_net_param_count() values, */
+/* 8 x 8 block gives that block's logit (b = by * L/8 + bx).  A BF16 network: */
+/* weights are rounded to bfloat16 for every use and each activation is      */
+/* stored as bfloat16 (round to nearest even); products accumulate in FP32;  */
+/* the 32 -> 32 layers run on the tensor cores.  Every reduction has a fixed  */
+/* order, so logits are a deterministic function of the state.               */
+/* Parameters: one FP32 vector of ising_net_param_count() values,            */
 /* W1[32][9], b1[32], W2[32][32][9], b2[32], W3[32][32][9], b3[32], W4[32][9], */
 /* b4[1] (tap k = 3 (dy + 1) + (dx + 1)).                                     */
 /* ------------------------------------------------------------------------ */
@@ -325,6 +327,25 @@ ISING_API int ising_net_workspace_bytes(int64_t L, int64_t C, int32_t train, siz
 ISING_API int ising_net_forward(int64_t L, int64_t C, const void *black_dev, const void *white_dev,
                                 const int32_t *flip_block_dev, const float *params_dev, float *logits_dev,
                                 void *work_dev, size_t work_bytes, int32_t train, ising_stream_t stream);
+
+/* The logits of the flipped states, the second network evaluation of a block
+ * move: logits_dev[c] = the logits of chain c with block flip_block_dev[c]
+ * flipped, given logits_x_dev = this network's logits of the unflipped chains
+ * (same params, same planes; another buffer).  A flipped block changes the
+ * activations only within 4 rows of it (four 3 x 3 layers), so for L a
+ * multiple of 128 only a band of 30 rows per chain is recomputed and the
+ * logits outside the block row and its two neighbours are copied from
+ * logits_x_dev; the result equals ising_net_forward with flip_block_dev bit
+ * for bit.  Other L compute the whole forward.  Inference workspace. */
+ISING_API int ising_net_forward_flipped(int64_t L, int64_t C, const void *black_dev, const void *white_dev,
+                                        const int32_t *flip_block_dev, const float *params_dev,
+                                        const float *logits_x_dev, float *logits_dev, void *work_dev,
+                                        size_t work_bytes, ising_stream_t stream);
+
+/* Synchronises `stream`, then reports ISING_ETIMEOUT (and clears the flag) if
+ * a tensor-core kernel of the network gave up waiting for its MMAs since the
+ * last check (each such wait is bounded at about 2 s), else ISING_OK. */
+ISING_API int ising_net_check(ising_stream_t stream);
 
 /* grad_dev = d(sum dlogits * logits)/d(params) for the last training forward
  * on the same chains and parameters (straight-through the bfloat16 rounding). */

@@ -114,6 +114,8 @@ def _load():
             "ising_batch_run_noalloc": [i64, P, i32, P, P, P, P, P, i64, u64, u64, i32, i32, P, P],
             "ising_net_workspace_bytes": [i64, i64, i32, P],
             "ising_net_forward": [i64, i64, P, P, P, P, P, P, ctypes.c_size_t, i32, P],
+            "ising_net_forward_flipped": [i64, i64, P, P, P, P, P, P, P, ctypes.c_size_t, P],
+            "ising_net_check": [P],
             "ising_net_backward": [i64, i64, P, P, P, P, P, P, ctypes.c_size_t, P],
             "ising_net_targets_loss": [i64, i64, P, P, dbl, P, P, P, P, P],
             "ising_net_adam": [P, P, P, P, i64, ctypes.c_float, P],
@@ -579,6 +581,17 @@ def ising_net_forward(L, C, black, white, flip_block, params, logits, work, trai
                                      int(bool(train)), _stream(stream)), "ising_net_forward")
 
 
+def ising_net_forward_flipped(L, C, black, white, flip_block, params, logits_x, logits, work, stream=None):
+    _check(_load().ising_net_forward_flipped(L, C, _addr(black), _addr(white), _addr(flip_block), _addr(params),
+                                             _addr(logits_x), _addr(logits), _addr(work),
+                                             work.numel() * work.element_size(), _stream(stream)),
+           "ising_net_forward_flipped")
+
+
+def ising_net_check(stream=None):
+    _check(_load().ising_net_check(_stream(stream)), "ising_net_check")
+
+
 def ising_net_backward(L, C, black, white, params, dlogits, grad, work, stream=None):
     _check(_load().ising_net_backward(L, C, _addr(black), _addr(white), _addr(params), _addr(dlogits), _addr(grad),
                                       _addr(work), work.numel() * work.element_size(), _stream(stream)),
@@ -639,8 +652,8 @@ class BlockMove:
             return
         ising_net_forward(self.L, self.C, self.black, self.white, None, params, self.lx, self.work, False, stream)
         ising_block_propose(self.L, self.C, self.lx, seed, t, self.block, stream)
-        ising_net_forward(self.L, self.C, self.black, self.white, self.block, params, self.lxp, self.work, False,
-                          stream)
+        ising_net_forward_flipped(self.L, self.C, self.black, self.white, self.block, params, self.lx, self.lxp,
+                                  self.work, stream)
         ising_block_accept(self.L, self.C, self.black, self.white, self.beta, self.lx, self.lxp, self.block, seed, t,
                            self.accepted, self.dE, stream)
 

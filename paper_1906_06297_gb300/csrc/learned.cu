@@ -8,15 +8,18 @@
 // batched MSC4 layout: lattice c's colour planes start at word c * L * L/32 of
 // one black and one white buffer (as a batch of equal sides).
 //
-// Network (3 x 3 periodic cross-correlations, 32 channels; weights rounded to
-// bfloat16 for every use, products accumulated in FP32):
+// Network (3 x 3 periodic cross-correlations, 32 channels; a BF16 network:
+// weights and the activations a1..a3 are bfloat16 (round to nearest even),
+// products are accumulated in FP32):
 //   a1 = gelu(conv(spins; W1, b1)), a2 = gelu(conv(a1; W2, b2)),
 //   a3 = gelu(conv(a2; W3, b3)), z4 = conv(a3; W4, b4) (one channel),
 //   logit of block b = mean of z4 over the block; q(b) = softmax(logits)_b.
 // gelu(z) = z * Phi(z).  Parameters are one FP32 vector in the order
 // W1[32][9], b1[32], W2[32][32][9], b2[32], W3[32][32][9], b3[32], W4[32][9], b4[1].
-// Activations are NHWC FP32 (32 channels per pixel).  All reductions have a
-// fixed order, so a forward pass is a deterministic function of the state.
+// Activations are NHWC bfloat16 (32 channels, 64 bytes per pixel); the
+// pre-activations z kept for training are NHWC FP32.  The two 32 -> 32 layers
+// run on the tensor cores (tcgen05, see conv32_tc_kernel); every reduction has
+// a fixed order, so a forward pass is a deterministic function of the state.
 //
 // Move.  Block b is drawn by inverse CDF of q_x (purpose-3 draw, site 0, in
 // the chain's stream) or uniformly; x' = x with block b flipped; the flip is
@@ -24,6 +27,7 @@
 // floor(2^32 min(1, exp(-beta dE + log q_x'(b) - log q_x(b)))), dE the exact
 // integer energy change (twice the boundary bond sum).  Softmax sums run in
 // block order in FP64.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,6 +38,7 @@
 #include "../../include/ising.h"
 #include "common.cuh"
 #include "launch.h"
+#include "tc.cuh"
 
 namespace ising {
 
@@ -53,6 +58,15 @@ __device__ __forceinline__ float bf16r(float x)
     u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
     return __uint_as_float(u);
 }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 
@@ -85,89 +99,291 @@ __device__ __forceinline__ float spin_at(const Chains &ch, int64_t c, int y, int
 // ---------------------------------------------------------------------------
 // Forward
 // ---------------------------------------------------------------------------
-// Layer 1: thread per pixel.  z stored when z_out != nullptr.
-__global__ void __launch_bounds__(kThreads) l1_kernel(Chains ch, int64_t C, const int32_t *flip, const float *params,
-                                                      float *z_out, float *a_out)
+// Which rows a forward launch computes.  A full pass covers every row of every
+// chain (flip == nullptr here).  A band pass, used for the flipped state of a
+// block move, covers per chain `rows` consecutive rows starting `lead` rows
+// above the first row of the chain's flipped block (periodically): the rows
+// whose values can differ from the unflipped state's and that the recomputed
+// logits need.
+struct Band {
+    int L;
+    int rows;             // rows per chain (L for a full pass)
+    int lead;             // band pass: first row = 8 by - lead (mod L)
+    const int32_t *flip;  // band pass: the flipped block of each chain
+    int64_t C;
+};
+
+__device__ __forceinline__ int band_row0(const Band &b, int64_t c)
+{
+    if (b.flip == nullptr) return 0;
+    const int f = b.flip[c];
+    const int by = f < 0 ? 0 : f / (b.L / kBlk);
+    const int r = by * kBlk - b.lead;
+    return r < 0 ? r + b.L : r;
+}
+
+// Pixel pb of the band (0 <= pb < C rows L) -> chain c and the offset yx =
+// y L + x of its pixel within the chain.
+__device__ __forceinline__ void band_pixel(const Band &b, int64_t pb, int64_t &c, int &yx)
+{
+    const int64_t per = (int64_t)b.rows * b.L;
+    c = pb / per;
+    const int r = (int)(pb - c * per);
+    const int ry = r / b.L;
+    int y = band_row0(b, c) + ry;
+    if (y >= b.L) y -= b.L;
+    yx = y * b.L + (r - ry * b.L);
+}
+
+__device__ __forceinline__ int wrap(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
+
+// Layer 1 (1 -> 32 channels, from the spins): thread per pixel of the band.
+// Writes a1 (bfloat16) and, when z_out != nullptr, z1 (FP32).
+__global__ void __launch_bounds__(kThreads) l1_kernel(Chains ch, Band bd, const int32_t *flip, const float *params,
+                                                      float *z_out, __nv_bfloat16 *a_out)
 {
     __shared__ float W[kN1], Bs[kCh];
     for (int i = threadIdx.x; i < kN1; i += blockDim.x) W[i] = bf16r(params[kOffW1 + i]);
     for (int i = threadIdx.x; i < kCh; i += blockDim.x) Bs[i] = bf16r(params[kOffB1 + i]);
     __syncthreads();
     const int L = ch.L;
-    const int64_t npix = C * (int64_t)L * L;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = p / ((int64_t)L * L);
-        const int yx = (int)(p - c * (int64_t)L * L);
+    const int64_t npix = bd.C * (int64_t)bd.rows * L;
+    for (int64_t pb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pb < npix; pb += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c;
+        int yx;
+        band_pixel(bd, pb, c, yx);
         const int y = yx / L, x = yx - y * L;
         const int fb = flip ? flip[c] : -1;
         float s[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int yy = (y + k / 3 - 1 + L) % L, xx = (x + k % 3 - 1 + L) % L;
-            s[k] = spin_at(ch, c, yy, xx, fb);
-        }
-        float *zo = z_out ? z_out + p * kCh : nullptr;
-        float *ao = a_out + p * kCh;
-#pragma unroll 4
-        for (int o = 0; o < kCh; ++o) {
-            float z = Bs[o];
+        for (int k = 0; k < 9; ++k) s[k] = spin_at(ch, c, wrap(y + k / 3 - 1, L), wrap(x + k % 3 - 1, L), fb);
+        const int64_t q = c * (int64_t)L * L + yx;
+        float *zo = z_out ? z_out + q * kCh : nullptr;
+        uint4 *ao = reinterpret_cast<uint4 *>(a_out + q * kCh);
 #pragma unroll
-            for (int k = 0; k < 9; ++k) z = fmaf(W[o * 9 + k], s[k], z);
-            if (zo) zo[o] = z;
-            ao[o] = gelu(z);
+        for (int o8 = 0; o8 < kCh / 8; ++o8) {
+            uint32_t w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float g[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int o = 8 * o8 + 2 * j + h;
+                    float z = Bs[o];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) z = fmaf(W[o * 9 + k], s[k], z);
+                    if (zo) zo[o] = z;
+                    g[h] = gelu(z);
+                }
+                w[j] = pack_bf16x2(g[0], g[1]);
+            }
+            ao[o8] = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
 
-// Layers 2 and 3: thread per pixel, 32 accumulators; weights in shared memory
-// as Ws[k][i][o] so that a tap and input channel give 32 contiguous outputs.
-__global__ void __launch_bounds__(kThreads) conv32_kernel(int L, int64_t C, const float *params, int w_off, int b_off,
-                                                          const float *a_in, float *z_out, float *a_out)
+// Layers 2 and 3 (32 -> 32 channels) on the tensor cores, as an implicit GEMM
+// per tile of 128 consecutive pixels of the band:
+//   Z[m][o] = sum over taps k and input channels i of A_k[m][i] W[o][i][k],
+// M = 128 pixels, N = 32 output channels, K = 9 taps x 32 channels = 18 MMA
+// steps of K = 16 (tcgen05.mma kind::f16, BF16 operands, FP32 accumulator in
+// tensor memory).  A_k, the input activations of the pixels shifted by tap k
+// (periodic), is gathered into shared memory in the no-swizzle K-major layout:
+// for tap k and channel group g (8 channels = 16 bytes) a plane of 128 pixel
+// rows of 16 bytes, planes at 2 KiB steps, so one MMA step (two channel
+// groups of one tap) reads a core matrix of 8 pixels x 16 bytes at SBO = 128
+// bytes along M and LBO = 2 KiB along K.  The weights, B_k[o][i] =
+// bf16(W[o][i][k]), sit the same way (planes of 32 rows, LBO = 512 bytes),
+// staged once per CTA.  Persistent CTAs (one per SM) walk tiles j, j + grid,
+// ...; the gather of tile n+1 and the epilogue of tile n-1 overlap the MMAs of
+// tile n (two shared-memory stages, two accumulators of 32 TMEM columns).
+// Epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its pixels) and
+// columns 16 (w / 4) .. + 15 (its output channels), adds the bias, and writes
+// z (FP32, training) and bf16(gelu(z)).
+constexpr int kTileM = 128;
+constexpr int kConvThreads = 256;
+constexpr int kTaps = 9;
+constexpr int kGroups = kCh / 8;                                      // 16-byte channel groups per pixel
+constexpr uint32_t kAStage = kTaps * kGroups * kTileM * 16;           // 73728 bytes per stage
+constexpr uint32_t kBBytes = kTaps * kGroups * kCh * 16;              // 18432 bytes
+// + bias, barriers and the TMEM slot; padded to 180 KiB so that every
+// address an operand descriptor of this kernel can reach (even one read with
+// LBO and SBO exchanged) lies inside the CTA's own allocation
+constexpr uint32_t kConvSmemUsed = 2 * kAStage + kBBytes + kCh * 4 + 64;
+constexpr uint32_t kConvSmem = 180 * 1024;
+static_assert(kConvSmemUsed <= kConvSmem, "conv shared memory");
+constexpr uint32_t kTmemCols = 64;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ int g_tc_error;  // set to 1 when a tensor-core wait gives up
+
+struct ConvTc {
+    const __nv_bfloat16 *a_in;  // NHWC, C L^2 x 32
+    __nv_bfloat16 *a_out;
+    float *z_out;  // nullable
+    const float *params;
+    int w_off, b_off;
+    Band bd;
+    int64_t tiles;  // C rows L / 128
+};
+
+__device__ __forceinline__ void tile_origin(const ConvTc &p, int64_t tile, int64_t &c, int &yx0)
 {
-    extern __shared__ float Ws[];  // 9 * 32 * 32
-    __shared__ float Bs[kCh];
-    for (int i = threadIdx.x; i < kN2; i += blockDim.x) {
-        const int o = i / (kCh * 9), rem = i - o * kCh * 9, ci = rem / 9, k = rem - ci * 9;
-        Ws[(k * kCh + ci) * kCh + o] = bf16r(params[w_off + i]);
+    band_pixel(p.bd, tile * kTileM, c, yx0);
+}
+
+// Gathers A_k for the 9 taps of one tile.  Thread t moves channel group t % 4
+// of pixels m0 = t / 4 and m0 + 64 for every tap.
+__device__ __forceinline__ void conv_gather(const ConvTc &p, int64_t tile, uint8_t *sa)
+{
+    const int L = p.bd.L;
+    int64_t c;
+    int yx0;
+    tile_origin(p, tile, c, yx0);
+    const int g = threadIdx.x & 3, m0 = threadIdx.x >> 2;
+    int py[2], px[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int yx = yx0 + m0 + 64 * h;
+        py[h] = yx / L;
+        px[h] = yx - py[h] * L;
     }
-    for (int i = threadIdx.x; i < kCh; i += blockDim.x) Bs[i] = bf16r(params[b_off + i]);
+    const uint4 *src = reinterpret_cast<const uint4 *>(p.a_in) + c * (int64_t)L * L * kGroups;
+    uint4 v[2 * kTaps];
+#pragma unroll
+    for (int k = 0; k < kTaps; ++k)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int yy = wrap(py[h] + k / 3 - 1, L), xx = wrap(px[h] + k % 3 - 1, L);
+            v[2 * k + h] = __ldg(src + ((int64_t)yy * L + xx) * kGroups + g);
+        }
+#pragma unroll
+    for (int k = 0; k < kTaps; ++k)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            *reinterpret_cast<uint4 *>(sa + ((k * kGroups + g) * kTileM + m0 + 64 * h) * 16) = v[2 * k + h];
+}
+
+__device__ __forceinline__ void conv_epilogue(const ConvTc &p, int64_t tile, uint32_t tacc, const float *bias)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quad = warp & 3, half = warp >> 2;
+    int64_t c;
+    int yx0;
+    tile_origin(p, tile, c, yx0);
+    const int64_t q = c * (int64_t)p.bd.L * p.bd.L + yx0 + quad * 32 + lane;
+    float v[16];
+    tc::tmem_ld16(tacc + (uint32_t)(half * 16) + ((uint32_t)(quad * 32) << 16), v);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] += bias[half * 16 + j];
+    if (p.z_out) {
+        float4 *zo = reinterpret_cast<float4 *>(p.z_out + q * kCh + half * 16);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) zo[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    }
+    uint32_t w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) w[j] = pack_bf16x2(gelu(v[2 * j]), gelu(v[2 * j + 1]));
+    uint4 *ao = reinterpret_cast<uint4 *>(p.a_out + q * kCh + half * 16);
+    ao[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    ao[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+__global__ void __launch_bounds__(kConvThreads, 1) conv32_tc_kernel(const __grid_constant__ ConvTc p)
+{
+    extern __shared__ __align__(1024) uint8_t conv_smem[];
+    uint8_t *sA = conv_smem;
+    uint8_t *sB = conv_smem + 2 * kAStage;
+    float *sBias = reinterpret_cast<float *>(sB + kBBytes);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sBias + kCh);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+        tc::fence_mbar_init();
+    }
+    // B[k][g][o] = the 8 input channels 8g .. 8g+7 of W[o][.][k], bfloat16
+    for (int e = tid; e < kTaps * kGroups * kCh; e += blockDim.x) {
+        const int k = e / (kGroups * kCh), r = e - k * (kGroups * kCh), g = r / kCh, o = r - g * kCh;
+        const float *w = p.params + p.w_off + (o * kCh + 8 * g) * 9 + k;
+        *reinterpret_cast<uint4 *>(sB + e * 16) =
+            make_uint4(pack_bf16x2(w[0], w[9]), pack_bf16x2(w[18], w[27]), pack_bf16x2(w[36], w[45]),
+                       pack_bf16x2(w[54], w[63]));
+    }
+    if (tid < kCh) sBias[tid] = bf16r(p.params[p.b_off + tid]);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
     __syncthreads();
-    const int64_t npix = C * (int64_t)L * L;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = p / ((int64_t)L * L);
-        const int yx = (int)(p - c * (int64_t)L * L);
-        const int y = yx / L, x = yx - y * L;
-        float acc[kCh];
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = tc::idesc_bf16_f32(kTileM, kCh);
+    const uint32_t a_u32 = tc::smem_u32(sA), b_u32 = tc::smem_u32(sB);
+
+    bool ok = true;
+    int committed = 0;  // tiles whose MMAs were issued
+    for (int n = 0;; ++n) {
+        const int64_t tile = blockIdx.x + (int64_t)n * gridDim.x;
+        const bool has = tile < p.tiles;
+        const int buf = n & 1;
+        // stage `buf` was last read by the MMAs of tile n-2, waited for below at step n-1
+        if (has) conv_gather(p, tile, sA + buf * kAStage);
+        tc::fence_async_smem();
+        __syncthreads();
+        if (has && tid == 0) {
+            tc::fence_after_sync();
 #pragma unroll
-        for (int o = 0; o < kCh; ++o) acc[o] = Bs[o];
-        for (int k = 0; k < 9; ++k) {
-            const int yy = (y + k / 3 - 1 + L) % L, xx = (x + k % 3 - 1 + L) % L;
-            const float4 *src = reinterpret_cast<const float4 *>(a_in + ((c * L + yy) * (int64_t)L + xx) * kCh);
-#pragma unroll
-            for (int q = 0; q < kCh / 4; ++q) {
-                const float4 v = src[q];
-                const float in4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const float *w = Ws + (k * kCh + 4 * q + r) * kCh;
-#pragma unroll
-                    for (int o = 0; o < kCh; ++o) acc[o] = fmaf(w[o], in4[r], acc[o]);
-                }
+            for (int s = 0; s < 2 * kTaps; ++s) {
+                const int k = s >> 1, g = 2 * (s & 1);
+                const uint64_t ad =
+                    tc::smem_desc(a_u32 + buf * kAStage + (k * kGroups + g) * kTileM * 16, kTileM * 16, 128);
+                const uint64_t bd = tc::smem_desc(b_u32 + (k * kGroups + g) * kCh * 16, kCh * 16, 128);
+                tc::mma_bf16(tmem + (uint32_t)(buf * kCh), ad, bd, idesc, s > 0 ? 1u : 0u);
+            }
+            tc::mma_commit(&mbar[buf]);
+        }
+        if (has) committed = n + 1;
+        if (n >= 1) {
+            const int pn = n - 1, pb = pn & 1;
+            // ok stays warp-uniform: the TMEM loads below are warp-collective
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&mbar[pb], (uint32_t)((pn >> 1) & 1), kWaitCycles)))
+                ok = false;
+            tc::fence_after_sync();
+            if (ok) conv_epilogue(p, blockIdx.x + (int64_t)pn * gridDim.x, tmem + (uint32_t)(pb * kCh), sBias);
+            tc::fence_before_sync();
+        }
+        if (__syncthreads_or(!ok)) {
+            ok = false;
+            break;
+        }
+        if (!has) break;
+    }
+    if (!ok) {
+        if (tid == 0) {
+            atomicExch(&g_tc_error, 1);
+            // let the MMAs of the last issued tile finish before the TMEM is freed
+            if (committed > 0) {
+                const int ln = committed - 1;
+                tc::mbar_wait(&mbar[ln & 1], (uint32_t)((ln >> 1) & 1), kWaitCycles);
             }
         }
-        float *zo = z_out ? z_out + p * kCh : nullptr;
-        float4 *ao = reinterpret_cast<float4 *>(a_out + p * kCh);
-#pragma unroll
-        for (int q = 0; q < kCh / 4; ++q) {
-            if (zo) reinterpret_cast<float4 *>(zo)[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-            ao[q] = make_float4(gelu(acc[4 * q]), gelu(acc[4 * q + 1]), gelu(acc[4 * q + 2]), gelu(acc[4 * q + 3]));
-        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, kTmemCols);
     }
 }
 
-// Layer 4 and the block mean: warp per (chain, block), two pixels per lane,
-// lane sums in a fixed order then a fixed shuffle tree.
-__global__ void __launch_bounds__(kThreads) l4_pool_kernel(int L, int64_t C, const float *params, const float *a3,
+// Layer 4 and the block mean: warp per (chain, block) over `brows` block rows
+// per chain (all of them in a full pass; in a band pass the flipped block's
+// row and its two neighbours), two pixels per lane, lane sums in a fixed order
+// then a fixed shuffle tree.
+__global__ void __launch_bounds__(kThreads) l4_pool_kernel(int L, int64_t C, int brows, const int32_t *flip,
+                                                           const float *params, const __nv_bfloat16 *a3,
                                                            float *logits)
 {
     __shared__ float W[kN1];
@@ -178,19 +394,34 @@ __global__ void __launch_bounds__(kThreads) l4_pool_kernel(int L, int64_t C, con
     const int nb1 = L / kBlk, nb = nb1 * nb1;
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < C * nb; wi += nw) {
-        const int64_t c = wi / nb;
-        const int b = (int)(wi - c * nb), by = b / nb1, bx = b - by * nb1;
+    const int per = brows * nb1;
+    for (int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < C * per; wi += nw) {
+        const int64_t c = wi / per;
+        const int r = (int)(wi - c * per), rb = r / nb1, bx = r - rb * nb1;
+        int by = rb;
+        if (flip) {
+            const int f = flip[c];
+            by = wrap((f < 0 ? 0 : f / nb1) - 1 + rb, nb1);
+        }
+        const int b = by * nb1 + bx;
         float part = 0.0f;
         for (int e = 0; e < 2; ++e) {
             const int pix = lane + 32 * e;  // 0..63 within the block
             const int y = by * kBlk + pix / kBlk, x = bx * kBlk + pix % kBlk;
             float z = b4;
             for (int k = 0; k < 9; ++k) {
-                const int yy = (y + k / 3 - 1 + L) % L, xx = (x + k % 3 - 1 + L) % L;
-                const float *src = a3 + ((c * L + yy) * (int64_t)L + xx) * kCh;
+                const int yy = wrap(y + k / 3 - 1, L), xx = wrap(x + k % 3 - 1, L);
+                const uint4 *src = reinterpret_cast<const uint4 *>(a3 + ((c * L + yy) * (int64_t)L + xx) * kCh);
 #pragma unroll
-                for (int i = 0; i < kCh; ++i) z = fmaf(W[i * 9 + k], src[i], z);
+                for (int g = 0; g < kGroups; ++g) {
+                    const uint4 v = __ldg(src + g);
+                    const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        z = fmaf(W[(8 * g + 2 * j) * 9 + k], bf16_lo(u[j]), z);
+                        z = fmaf(W[(8 * g + 2 * j + 1) * 9 + k], bf16_hi(u[j]), z);
+                    }
+                }
             }
             part += z;
         }
@@ -283,7 +514,7 @@ __global__ void __launch_bounds__(kThreads) conv32_bwd_data_kernel(int L, int64_
 constexpr int kTy = 8, kTx = 32;
 
 template <int CIN, int COUT>
-__device__ __forceinline__ void wgrad_stage(const Chains &ch, const float *a_prev, const float *dz,
+__device__ __forceinline__ void wgrad_stage(const Chains &ch, const __nv_bfloat16 *a_prev, const float *dz,
                                             const float *dlogits, int64_t c, int y0, int x0, float *sa, float *sd)
 {
     const int L = ch.L, nb1 = L / kBlk;
@@ -294,7 +525,7 @@ __device__ __forceinline__ void wgrad_stage(const Chains &ch, const float *a_pre
         int y = y0 + ty - 1, x = x0 + tx - 1;
         y = y < 0 ? y + L : (y >= L ? y - L : y);
         x = x < 0 ? x + L : (x >= L ? x - L : x);
-        sa[e] = CIN == 1 ? spin_at(ch, c, y, x, -1) : a_prev[((c * L + y) * (int64_t)L + x) * CIN + i];
+        sa[e] = CIN == 1 ? spin_at(ch, c, y, x, -1) : __bfloat162float(a_prev[((c * L + y) * (int64_t)L + x) * CIN + i]);
     }
     for (int e = threadIdx.x; e < kTy * kTx * COUT; e += blockDim.x) {
         const int pix = e / COUT, o = e - pix * COUT;
@@ -305,7 +536,7 @@ __device__ __forceinline__ void wgrad_stage(const Chains &ch, const float *a_pre
 }
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(256) wgrad_kernel(Chains ch, int64_t C, const float *a_prev, const float *dz,
+__global__ void __launch_bounds__(256) wgrad_kernel(Chains ch, int64_t C, const __nv_bfloat16 *a_prev, const float *dz,
                                                     const float *dlogits, float *partial)
 {
     extern __shared__ float smem[];
@@ -558,10 +789,12 @@ int check_chains(int64_t L, int64_t C)
     return ISING_OK;
 }
 
-// Work layout: [z1 a1 z2 a2 z3 a3 d_a d_b] activations (8 x C L^2 32 floats)
-// in training mode, [a1 a2] in inference mode, then weight-gradient partials.
+// Work layout: training keeps z1 z2 z3 (FP32), a1 a2 a3 (bfloat16) and two
+// FP32 gradient buffers, then the weight-gradient partials; inference keeps
+// a1 and a2 (bfloat16; a3 reuses a1's buffer).
 struct NetWork {
-    float *z1, *a1, *z2, *a2, *z3, *a3, *da, *db, *partial;
+    float *z1, *z2, *z3, *da, *db, *partial;
+    __nv_bfloat16 *a1, *a2, *a3;
     int64_t n_cta;
     size_t bytes;
 };
@@ -572,26 +805,82 @@ NetWork net_layout(int64_t L, int64_t C, int train, char *base)
 {
     NetWork w;
     memset(&w, 0, sizeof(w));
-    const size_t act = (size_t)C * L * L * kCh * sizeof(float);
+    const size_t pix = (size_t)C * L * L * kCh;
     size_t o = 0;
     auto take = [&](size_t n) {
         char *p = base ? base + o : nullptr;
         o += (n + 255) & ~size_t(255);
-        return (float *)p;
+        return (void *)p;
     };
     if (train) {
-        w.z1 = take(act); w.a1 = take(act); w.z2 = take(act); w.a2 = take(act);
-        w.z3 = take(act); w.a3 = take(act); w.da = take(act); w.db = take(act);
+        w.z1 = (float *)take(pix * 4); w.z2 = (float *)take(pix * 4); w.z3 = (float *)take(pix * 4);
+        w.a1 = (__nv_bfloat16 *)take(pix * 2); w.a2 = (__nv_bfloat16 *)take(pix * 2);
+        w.a3 = (__nv_bfloat16 *)take(pix * 2);
+        w.da = (float *)take(pix * 4); w.db = (float *)take(pix * 4);
         DeviceInfo info{152};
         device_info(&info);
         w.n_cta = (int64_t)info.sm_count * kWgradCtasPerSm;
-        w.partial = take((size_t)w.n_cta * (kN2 + kCh) * sizeof(float));
+        w.partial = (float *)take((size_t)w.n_cta * (kN2 + kCh) * sizeof(float));
     } else {
-        w.a1 = take(act); w.a2 = take(act);
+        w.a1 = (__nv_bfloat16 *)take(pix * 2); w.a2 = (__nv_bfloat16 *)take(pix * 2);
         w.a3 = w.a1;
     }
     w.bytes = o;
     return w;
+}
+
+// Rows of each layer in a band pass.  Layer 4 recomputes the logits of block
+// rows by - 1 .. by + 1, i.e. z4 on rows 8 by - 8 .. 8 by + 15; every 3 x 3
+// layer below needs one more row on each side: a3 8 by - 9 .. 8 by + 16, a2
+// 8 by - 10 .. 8 by + 17, a1 8 by - 11 .. 8 by + 18.  No value outside these
+// rows (nor any logit outside those block rows) depends on the flipped block,
+// whose rows are 8 by .. 8 by + 7: its influence reaches 4 rows (4 layers).
+constexpr int kBandRows[4] = {30, 28, 26, 3};  // a1, a2, a3 rows; logit block rows
+constexpr int kBandLead[3] = {11, 10, 9};
+
+bool band_supported(int64_t L) { return L % kTileM == 0 && L >= 128; }
+
+int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, const float *params,
+                   float *logits, const NetWork &w, int train, cudaStream_t s)
+{
+    const int L = ch.L;
+    DeviceInfo info{152};
+    device_info(&info);
+    Band bd[3];
+    for (int l = 0; l < 3; ++l) {
+        bd[l].L = L;
+        bd[l].C = C;
+        bd[l].rows = band ? kBandRows[l] : L;
+        bd[l].lead = band ? kBandLead[l] : 0;
+        bd[l].flip = band ? flip : nullptr;
+    }
+    l1_kernel<<<grid1d(C * (int64_t)bd[0].rows * L, kThreads), kThreads, 0, s>>>(ch, bd[0], flip, params,
+                                                                                  train ? w.z1 : nullptr, w.a1);
+    cudaFuncSetAttribute(conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
+    __nv_bfloat16 *a3 = train ? w.a3 : w.a1;  // inference ping-pongs two buffers
+    const int off[2][2] = {{kOffW2, kOffB2}, {kOffW3, kOffB3}};
+    const __nv_bfloat16 *ins[2] = {w.a1, w.a2};
+    __nv_bfloat16 *outs[2] = {w.a2, a3};
+    float *zs[2] = {train ? w.z2 : nullptr, train ? w.z3 : nullptr};
+    for (int l = 0; l < 2; ++l) {
+        ConvTc p;
+        p.a_in = ins[l];
+        p.a_out = outs[l];
+        p.z_out = zs[l];
+        p.params = params;
+        p.w_off = off[l][0];
+        p.b_off = off[l][1];
+        p.bd = bd[l + 1];
+        p.tiles = C * (int64_t)bd[l + 1].rows * L / kTileM;
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.tiles, info.sm_count));
+        conv32_tc_kernel<<<grid, kConvThreads, kConvSmem, s>>>(p);
+    }
+    const int brows = band ? kBandRows[3] : L / kBlk;
+    const int64_t warps = C * brows * (L / kBlk);
+    l4_pool_kernel<<<grid1d(warps * 32, kThreads), kThreads, 0, s>>>(L, C, brows, band ? flip : nullptr, params, a3,
+                                                                     logits);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ISING_OK : nfail(ISING_ECUDA, cudaGetErrorString(e));
 }
 
 }  // namespace
@@ -625,22 +914,51 @@ ISING_API int ising_net_forward(int64_t L, int64_t C, const void *black_dev, con
     const size_t plane = (size_t)C * L * L / 32 * 8;
     if (check_device_range(black_dev, plane, "black") || check_device_range(white_dev, plane, "white") ||
         check_device_range(params_dev, kParams * 4, "params") ||
-        check_device_range(logits_dev, (size_t)C * (L / 8) * (L / 8) * 4, "logits"))
-        return nfail(ISING_EINVAL, "planes, params and logits must be device memory of their sizes");
+        check_device_range(logits_dev, (size_t)C * (L / 8) * (L / 8) * 4, "logits") ||
+        check_device_range(work_dev, w.bytes, "work"))
+        return nfail(ISING_EINVAL, "planes, params, logits and work must be device memory of their sizes");
+    Chains ch{(const uint64_t *)black_dev, (const uint64_t *)white_dev, (int)L, (int)(L / 32)};
+    return launch_forward(ch, C, flip_block_dev, false, params_dev, logits_dev, w, train, (cudaStream_t)stream);
+}
+
+ISING_API int ising_net_forward_flipped(int64_t L, int64_t C, const void *black_dev, const void *white_dev,
+                                        const int32_t *flip_block_dev, const float *params_dev,
+                                        const float *logits_x_dev, float *logits_dev, void *work_dev,
+                                        size_t work_bytes, ising_stream_t stream)
+{
+    int rc = check_chains(L, C);
+    if (rc) return rc;
+    NetWork w = net_layout(L, C, 0, (char *)work_dev);
+    if (work_dev == nullptr || work_bytes < w.bytes) return nfail(ISING_EINVAL, "work buffer too small");
+    const size_t plane = (size_t)C * L * L / 32 * 8;
+    const size_t lbytes = (size_t)C * (L / 8) * (L / 8) * 4;
+    if (check_device_range(black_dev, plane, "black") || check_device_range(white_dev, plane, "white") ||
+        check_device_range(params_dev, kParams * 4, "params") || check_device_range(logits_dev, lbytes, "logits") ||
+        check_device_range(logits_x_dev, lbytes, "logits_x") || check_device_range(flip_block_dev, (size_t)C * 4, "flip") ||
+        check_device_range(work_dev, w.bytes, "work"))
+        return nfail(ISING_EINVAL, "planes, params, logits, flip and work must be device memory of their sizes");
+    if (logits_x_dev == logits_dev) return nfail(ISING_EINVAL, "logits_x and logits must differ");
     cudaStream_t s = (cudaStream_t)stream;
     Chains ch{(const uint64_t *)black_dev, (const uint64_t *)white_dev, (int)L, (int)(L / 32)};
-    const int64_t npix = C * L * L;
-    const unsigned g = grid1d(npix, kThreads);
-    const size_t smem = (size_t)kN2 * sizeof(float);
-    cudaFuncSetAttribute(conv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    l1_kernel<<<g, kThreads, 0, s>>>(ch, C, flip_block_dev, params_dev, train ? w.z1 : nullptr, w.a1);
-    conv32_kernel<<<g, kThreads, smem, s>>>((int)L, C, params_dev, kOffW2, kOffB2, w.a1, train ? w.z2 : nullptr, w.a2);
-    float *a3 = train ? w.a3 : w.a1;  // inference ping-pongs two buffers
-    conv32_kernel<<<g, kThreads, smem, s>>>((int)L, C, params_dev, kOffW3, kOffB3, w.a2, train ? w.z3 : nullptr, a3);
-    const int64_t warps = C * (L / 8) * (L / 8);
-    l4_pool_kernel<<<grid1d(warps * 32, kThreads), kThreads, 0, s>>>((int)L, C, params_dev, a3, logits_dev);
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? ISING_OK : nfail(ISING_ECUDA, cudaGetErrorString(e));
+    if (!band_supported(L)) return launch_forward(ch, C, flip_block_dev, false, params_dev, logits_dev, w, 0, s);
+    cudaError_t e = cudaMemcpyAsync(logits_dev, logits_x_dev, lbytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return nfail(ISING_ECUDA, cudaGetErrorString(e));
+    return launch_forward(ch, C, flip_block_dev, true, params_dev, logits_dev, w, 0, s);
+}
+
+ISING_API int ising_net_check(ising_stream_t stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    int flag = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(&flag, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return nfail(ISING_ECUDA, cudaGetErrorString(e));
+    if (flag) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int));
+        return nfail(ISING_ETIMEOUT, "a tensor-core kernel gave up waiting for its MMAs");
+    }
+    return ISING_OK;
 }
 
 ISING_API int ising_net_backward(int64_t L, int64_t C, const void *black_dev, const void *white_dev,
@@ -651,6 +969,7 @@ ISING_API int ising_net_backward(int64_t L, int64_t C, const void *black_dev, co
     if (rc) return rc;
     NetWork w = net_layout(L, C, 1, (char *)work_dev);
     if (work_dev == nullptr || work_bytes < w.bytes) return nfail(ISING_EINVAL, "work buffer too small (train mode)");
+    if (check_device_range(work_dev, w.bytes, "work")) return nfail(ISING_EINVAL, "work must be device memory of its size");
     if (check_device_range(grad_dev, kParams * 4, "grad") ||
         check_device_range(dlogits_dev, (size_t)C * (L / 8) * (L / 8) * 4, "dlogits"))
         return nfail(ISING_EINVAL, "grad and dlogits must be device memory of their sizes");
