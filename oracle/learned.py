@@ -7,12 +7,16 @@ small convolutional network, interleaved with the checkerboard sweep.
 Network f (all convolutions 3 x 3, periodic, cross-correlation,
 z(y, x)[o] = b[o] + sum_{i, dy, dx} W[o][i][3(dy+1) + (dx+1)] a(y+dy, x+dx)[i]):
     a0 = spins (+1/-1), one channel
-    a1 = gelu(conv(a0; W1, b1))      1 -> 32 channels
-    a2 = gelu(conv(a1; W2, b2))     32 -> 32
-    a3 = gelu(conv(a2; W3, b3))     32 -> 32
+    a1 = r(gelu(conv(a0; W1, b1)))   1 -> 32 channels
+    a2 = r(gelu(conv(a1; W2, b2)))  32 -> 32
+    a3 = r(gelu(conv(a2; W3, b3)))  32 -> 32
     z4 = conv(a3; W4, b4)           32 -> 1
     l_b = mean of z4 over block b   (blocks of B x B, b = by * (L/B) + bx)
-gelu(z) = z Phi(z) (Phi the standard normal CDF).  The proposal picks block b
+gelu(z) = z Phi(z) (Phi the standard normal CDF).  It is a BF16 network: the
+caller passes bfloat16-valued weights, and r rounds each activation to the
+nearest bfloat16 (via float32, ties to even); everything else is float64 here.
+Gradients pass straight through r (the rounded activations enter the weight
+gradients).  The proposal picks block b
 with probability q_x(b) = softmax(l)_b; x' is x with block b flipped.
 
 Move (exact Metropolis-Hastings): accept with min(1, exp(-beta dE) q_x'(b) /
@@ -110,17 +114,20 @@ def flip_blocks(spins, blocks, B):
     return s
 
 
-def forward(theta, spins, B=8, flip=None, keep=False):
+def forward(theta, spins, B=8, flip=None, keep=False, round_act=True):
     """Logits (C, (L/B)^2) of the chains' spins (C, L, L); `flip` optionally
-    flips one block per chain first."""
+    flips one block per chain first.  round_act=False evaluates the same
+    network without rounding the activations (a smooth function of the
+    parameters, for finite-difference checks of the backward formulas)."""
     p = unflatten(theta)
     s = np.asarray(spins, dtype=np.float64)
     if flip is not None:
         s = flip_blocks(s, flip, B)
+    r = bf16_round if round_act else (lambda v: v)
     a0 = s[:, None]
-    z1 = conv(a0, p["W1"], p["b1"]); a1 = gelu(z1)
-    z2 = conv(a1, p["W2"], p["b2"]); a2 = gelu(z2)
-    z3 = conv(a2, p["W3"], p["b3"]); a3 = gelu(z3)
+    z1 = conv(a0, p["W1"], p["b1"]); a1 = r(gelu(z1))
+    z2 = conv(a1, p["W2"], p["b2"]); a2 = r(gelu(z2))
+    z3 = conv(a2, p["W3"], p["b3"]); a3 = r(gelu(z3))
     z4 = conv(a3, p["W4"], p["b4"])
     logits = block_pool(z4, B)
     if keep:
@@ -129,7 +136,8 @@ def forward(theta, spins, B=8, flip=None, keep=False):
 
 
 def backward(theta, cache, dlogits):
-    """Gradient (flat) of sum(dlogits * logits) w.r.t. the parameters."""
+    """Gradient (flat) of sum(dlogits * logits) w.r.t. the parameters, through
+    the activations kept in `cache` (straight through their rounding)."""
     p = unflatten(theta)
     B = cache["B"]
     C, nb = dlogits.shape
@@ -175,8 +183,8 @@ def targets(spins, beta, B=8):
     return t
 
 
-def loss_and_grad(theta, spins, beta, B=8):
-    logits, cache = forward(theta, spins, B, keep=True)
+def loss_and_grad(theta, spins, beta, B=8, round_act=True):
+    logits, cache = forward(theta, spins, B, keep=True, round_act=round_act)
     t = targets(np.asarray(spins), beta, B)
     r = logits - t
     loss = float((r * r).mean())

@@ -1,6 +1,10 @@
 """Pins for the learned block-proposal oracle (oracle/learned.py).
 
-- The hand-written backward pass against central finite differences.
+- The hand-written backward pass against central finite differences (of the
+  network without activation rounding, which is smooth; the rounded network
+  uses the same formulas straight through the rounding).
+- The bfloat16 activations: exactly representable, within half a bfloat16
+  step of the unrounded values, and the logits close to the unrounded ones.
 - The block energy change against the full Hamiltonian (Eq. 1) before and
   after the flip.
 - The Metropolis-Hastings block move, interleaved with checkerboard sweeps,
@@ -36,7 +40,7 @@ def test_backward_matches_finite_differences():
     theta = random_theta(1)
     spins = rng.choice([-1.0, 1.0], size=(2, 8, 8))
     dl = rng.normal(size=(2, 4))  # 8x8 lattice, 4x4 blocks
-    _, cache = ln.forward(theta, spins, B=4, keep=True)
+    _, cache = ln.forward(theta, spins, B=4, keep=True, round_act=False)
     g = ln.backward(theta, cache, dl)
     idx = np.concatenate([rng.choice(ln.N_PARAMS, 60, replace=False), [0, 300, 9600, ln.N_PARAMS - 1]])
     h = 1e-6
@@ -44,7 +48,8 @@ def test_backward_matches_finite_differences():
         tp, tm = theta.copy(), theta.copy()
         tp[i] += h
         tm[i] -= h
-        fd = (np.sum(dl * ln.forward(tp, spins, B=4)) - np.sum(dl * ln.forward(tm, spins, B=4))) / (2 * h)
+        fd = (np.sum(dl * ln.forward(tp, spins, B=4, round_act=False)) -
+              np.sum(dl * ln.forward(tm, spins, B=4, round_act=False))) / (2 * h)
         assert abs(fd - g[i]) < 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
 
 
@@ -52,12 +57,13 @@ def test_loss_gradient_matches_finite_differences():
     rng = np.random.default_rng(2)
     theta = random_theta(3, 0.1)
     spins = rng.choice([-1.0, 1.0], size=(2, 8, 8))
-    loss, g = ln.loss_and_grad(theta, spins, 0.44, B=4)
+    loss, g = ln.loss_and_grad(theta, spins, 0.44, B=4, round_act=False)
     for i in rng.choice(ln.N_PARAMS, 20, replace=False):
         tp, tm = theta.copy(), theta.copy()
         tp[i] += 1e-6
         tm[i] -= 1e-6
-        fd = (ln.loss_and_grad(tp, spins, 0.44, B=4)[0] - ln.loss_and_grad(tm, spins, 0.44, B=4)[0]) / 2e-6
+        fd = (ln.loss_and_grad(tp, spins, 0.44, B=4, round_act=False)[0] -
+              ln.loss_and_grad(tm, spins, 0.44, B=4, round_act=False)[0]) / 2e-6
         assert abs(fd - g[i]) < 1e-6 * max(1.0, abs(fd))
 
 
@@ -84,6 +90,26 @@ def test_bf16_rounding():
     r = ln.bf16_round(x)
     assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0078125  # ties to even, then round up
     assert r[3] == -2.5 and abs(r[4] - 3.140625) < 1e-12
+
+
+def test_activations_are_bf16_and_close_to_unrounded():
+    rng = np.random.default_rng(5)
+    theta = ln.bf16_round(random_theta(6, 0.2).astype(np.float32))
+    spins = rng.choice([-1.0, 1.0], size=(2, 16, 16))
+    lr, cr = ln.forward(theta, spins, B=8, keep=True)
+    lu, cu = ln.forward(theta, spins, B=8, keep=True, round_act=False)
+    for name in ("a1", "a2", "a3"):
+        a = cr[name]
+        bits = a.astype(np.float32).view(np.uint32)
+        assert np.all(bits & 0xFFFF == 0), name  # exactly bfloat16
+        assert np.array_equal(a.astype(np.float32).astype(np.float64), a)
+    # a1 sees the same z1 in both networks: within half a bfloat16 step (8
+    # significant bits: at most 2^-8 relative, plus the float32 step on the way)
+    assert np.all(np.abs(cr["a1"] - cu["a1"]) <= 2.0 ** -8 * (1 + 1e-6) * np.abs(cu["a1"]) + 1e-300)
+    assert np.abs(cr["a1"] - cu["a1"]).max() > 0  # rounding did happen
+    # the logits move by a small fraction of their spread, not by a different network
+    d = np.abs(lr - lu).max()
+    assert 0 < d < 0.05 * (np.abs(lu).max() + 1e-12), (d, np.abs(lu).max())
 
 
 def _chain_bond_sums(logits_fn, beta, n_cycles, seed, L=4, B=2):
