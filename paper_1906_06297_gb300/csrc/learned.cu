@@ -190,9 +190,10 @@ __global__ void __launch_bounds__(kThreads) l1_kernel(Chains ch, Band bd, const 
 // tensor memory).  A_k, the input activations of the pixels shifted by tap k
 // (periodic), is gathered into shared memory in the no-swizzle K-major layout:
 // for tap k and channel group g (8 channels = 16 bytes) a plane of 128 pixel
-// rows of 16 bytes, planes at 2 KiB steps, so one MMA step (two channel
-// groups of one tap) reads a core matrix of 8 pixels x 16 bytes at SBO = 128
-// bytes along M and LBO = 2 KiB along K.  The weights, B_k[o][i] =
+// rows of 16 bytes, planes 2080 bytes apart, so one MMA step (two channel
+// groups of one tap) reads core matrices of 8 pixels x 16 bytes at SBO = 128
+// bytes along M and LBO = 2080 bytes along K.  This kernel serves any L (a
+// multiple of 32); conv32_ring_kernel below is the one for L a multiple of 128.  The weights, B_k[o][i] =
 // bf16(W[o][i][k]), sit the same way (planes of 32 rows, LBO = 512 bytes),
 // staged once per CTA.  Persistent CTAs (one per SM) walk tiles j, j + grid,
 // ...; the gather of tile n+1 and the epilogue of tile n-1 overlap the MMAs of
@@ -204,7 +205,11 @@ constexpr int kTileM = 128;
 constexpr int kConvThreads = 256;
 constexpr int kTaps = 9;
 constexpr int kGroups = kCh / 8;                                      // 16-byte channel groups per pixel
-constexpr uint32_t kAStage = kTaps * kGroups * kTileM * 16;           // 73728 bytes per stage
+// One channel group of 128 (+2) pixel rows: 2080 bytes, so that the planes of
+// the 4 channel groups start 32 bytes apart modulo the 128-byte bank row and
+// 8 lanes storing 2 pixels x 4 groups hit 8 different 16-byte bank groups.
+constexpr uint32_t kPlane = (kTileM + 2) * 16;
+constexpr uint32_t kAStage = kTaps * kGroups * kPlane;                // 74880 bytes per stage
 constexpr uint32_t kBBytes = kTaps * kGroups * kCh * 16;              // 18432 bytes
 // + bias, barriers and the TMEM slot; padded to 180 KiB so that every
 // address an operand descriptor of this kernel can reach (even one read with
@@ -261,7 +266,7 @@ __device__ __forceinline__ void conv_gather(const ConvTc &p, int64_t tile, uint8
     for (int k = 0; k < kTaps; ++k)
 #pragma unroll
         for (int h = 0; h < 2; ++h)
-            *reinterpret_cast<uint4 *>(sa + ((k * kGroups + g) * kTileM + m0 + 64 * h) * 16) = v[2 * k + h];
+            *reinterpret_cast<uint4 *>(sa + (k * kGroups + g) * kPlane + (m0 + 64 * h) * 16) = v[2 * k + h];
 }
 
 __device__ __forceinline__ void conv_epilogue(const ConvTc &p, int64_t tile, uint32_t tacc, const float *bias)
@@ -338,7 +343,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv32_tc_kernel(const __grid
             for (int s = 0; s < 2 * kTaps; ++s) {
                 const int k = s >> 1, g = 2 * (s & 1);
                 const uint64_t ad =
-                    tc::smem_desc(a_u32 + buf * kAStage + (k * kGroups + g) * kTileM * 16, kTileM * 16, 128);
+                    tc::smem_desc(a_u32 + buf * kAStage + (k * kGroups + g) * kPlane, kPlane, 128);
                 const uint64_t bd = tc::smem_desc(b_u32 + (k * kGroups + g) * kCh * 16, kCh * 16, 128);
                 tc::mma_bf16(tmem + (uint32_t)(buf * kCh), ad, bd, idesc, s > 0 ? 1u : 0u);
             }
@@ -375,6 +380,233 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv32_tc_kernel(const __grid
     if (warp == 0) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// Layers 2 and 3 for L a multiple of 128: the same implicit GEMM per tile (one
+// 128-pixel row segment), fed from a ring of staged input rows.  A work unit
+// is up to kUnitRows consecutive output rows of one (chain, 128-column
+// segment); it stages its rows r0 - 1 .. r0 + n once each, as a halo row of
+// 130 pixels (x0 - 1 .. x0 + 128, periodic) in 4 channel-group planes of
+// kPlane bytes, so the operand of tap (dy, dx) is the staged row y + dy
+// offset by (1 + dx) x 16 bytes (LBO = kPlane, SBO = 128 as before).
+// Warp roles, linked by mbarriers (every wait bounded):
+//   warp 0: loader -- cp.async of each row (4 lanes per pixel: 64 contiguous
+//           bytes), up to kInFlight rows in flight per lane; after a row has
+//           landed each lane fences the async proxy and arrives on full[slot];
+//   warp 1: lane 0 issues the 18 MMAs of each tile into one of kAcc
+//           accumulators, then commits to accf[acc] and to empty[slot] of
+//           the row no later tile of the unit reads;
+//   warps 2-5: epilogue, warp w on TMEM lanes 32 (w % 4) .. + 31: loads its
+//           32 pixels x 32 channels, frees the accumulator (acce), adds the
+//           bias and writes z (training) and bf16(gelu(z)).
+constexpr int kRing = 10;       // staged rows
+constexpr int kInFlight = 4;    // rows a loader lane keeps in flight
+constexpr int kAcc = 4;         // accumulators of 32 TMEM columns
+constexpr int kUnitRows = 16;   // output rows per work unit
+constexpr int kRingThreads = 192;
+constexpr uint32_t kRowBytes = kGroups * kPlane;  // 8320
+constexpr uint32_t kRingSmemUsed = kRing * kRowBytes + kBBytes + kCh * 4 + (2 * kRing + 2 * kAcc + 1) * 8 + 16;
+// every address an operand descriptor can reach, even read with LBO and SBO
+// exchanged (< 111 KiB), lies inside the allocation
+constexpr uint32_t kRingSmem = 112 * 1024;
+static_assert(kRingSmemUsed <= kRingSmem, "ring shared memory");
+static_assert(kRing >= kInFlight + 2, "the loader must never wait for a row it has not published");
+
+struct RingConv {
+    const __nv_bfloat16 *a_in;
+    __nv_bfloat16 *a_out;
+    float *z_out;  // nullable
+    const float *params;
+    int w_off, b_off;
+    Band bd;
+    int segs;           // L / 128
+    int units_per_col;  // ceil(bd.rows / kUnitRows)
+    int64_t units;      // C segs units_per_col
+};
+
+struct RingUnit {
+    int64_t c;
+    int x0, r0, nrows;
+};
+
+__device__ __forceinline__ RingUnit ring_unit(const RingConv &p, int64_t u)
+{
+    RingUnit w;
+    const int64_t col = u / p.units_per_col;
+    const int rb = (int)(u - col * p.units_per_col);
+    w.c = col / p.segs;
+    w.x0 = (int)(col - w.c * p.segs) * kTileM;
+    w.r0 = rb * kUnitRows;
+    w.nrows = min(kUnitRows, p.bd.rows - w.r0);
+    return w;
+}
+
+// Lattice row of band row r (-1 <= r <= rows) of chain c.
+__device__ __forceinline__ int ring_row(const RingConv &p, int64_t c, int r)
+{
+    const int L = p.bd.L;
+    int y = band_row0(p.bd, c) + r;
+    y = y < 0 ? y + L : y;
+    return y >= L ? y - L : y;
+}
+
+__global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __grid_constant__ RingConv p)
+{
+    extern __shared__ __align__(1024) uint8_t ring_smem[];
+    uint8_t *ring = ring_smem;
+    uint8_t *sB = ring_smem + kRing * kRowBytes;
+    float *sBias = reinterpret_cast<float *>(sB + kBBytes);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sBias + kCh);
+    uint64_t *empty = full + kRing;
+    uint64_t *accf = empty + kRing;
+    uint64_t *acce = accf + kAcc;
+    uint64_t *drain = acce + kAcc;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(drain + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int L = p.bd.L;
+
+    if (warp == 1) tc::tmem_alloc(tslot, kAcc * kCh);
+    if (tid == 0) {
+        for (int s = 0; s < kRing; ++s) {
+            tc::mbar_init(&full[s], 32);
+            tc::mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < kAcc; ++a) {
+            tc::mbar_init(&accf[a], 1);
+            tc::mbar_init(&acce[a], 4);
+        }
+        tc::mbar_init(drain, 1);
+        tc::fence_mbar_init();
+    }
+    for (int e = tid; e < kTaps * kGroups * kCh; e += blockDim.x) {
+        const int k = e / (kGroups * kCh), r = e - k * (kGroups * kCh), g = r / kCh, o = r - g * kCh;
+        const float *w = p.params + p.w_off + (o * kCh + 8 * g) * 9 + k;
+        *reinterpret_cast<uint4 *>(sB + e * 16) =
+            make_uint4(pack_bf16x2(w[0], w[9]), pack_bf16x2(w[18], w[27]), pack_bf16x2(w[36], w[45]),
+                       pack_bf16x2(w[54], w[63]));
+    }
+    if (tid < kCh) sBias[tid] = bf16r(p.params[p.b_off + tid]);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    bool ok = true;
+
+    if (warp == 0) {
+        // loader
+        int64_t n = 0;  // rows staged so far
+        const int g = lane & 3;
+        for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+            const RingUnit w = ring_unit(p, u);
+            for (int j = -1; j <= w.nrows; ++j) {
+                const int s = (int)(n % kRing);
+                if (n >= kRing &&
+                    !__all_sync(0xffffffffu, tc::mbar_wait(&empty[s], (uint32_t)(((n / kRing) + 1) & 1), kWaitCycles))) {
+                    ok = false;
+                    break;
+                }
+                const int y = ring_row(p, w.c, w.r0 + j);
+                const uint8_t *src = reinterpret_cast<const uint8_t *>(p.a_in) + ((w.c * L + y) * (int64_t)L) * 64;
+                uint8_t *dst = ring + s * kRowBytes;
+                for (int e = lane >> 2; e < kTileM + 2; e += 8)
+                    tc::cp_async16(dst + g * kPlane + e * 16, src + (int64_t)wrap(w.x0 - 1 + e, L) * 64 + g * 16);
+                tc::cp_async_commit();
+                if (n >= kInFlight - 1) {
+                    tc::cp_async_wait<kInFlight - 1>();
+                    tc::fence_async_smem();
+                    tc::mbar_arrive(&full[(n - (kInFlight - 1)) % kRing]);
+                }
+                ++n;
+            }
+        }
+        tc::cp_async_wait<0>();
+        tc::fence_async_smem();
+        for (int64_t m = n > kInFlight - 1 ? n - (kInFlight - 1) : 0; m < n; ++m) tc::mbar_arrive(&full[m % kRing]);
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16_f32(kTileM, kCh);
+            const uint32_t ring_u32 = tc::smem_u32(ring), b_u32 = tc::smem_u32(sB);
+            int64_t n0 = 0, t = 0, ready = 0;
+            for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+                const RingUnit w = ring_unit(p, u);
+                for (int j = 0; j < w.nrows && ok; ++j, ++t) {
+                    while (ready < n0 + j + 3 && ok) {
+                        if (!tc::mbar_wait(&full[ready % kRing], (uint32_t)((ready / kRing) & 1), kWaitCycles)) ok = false;
+                        ++ready;
+                    }
+                    const int a = (int)(t % kAcc);
+                    if (ok && t >= kAcc && !tc::mbar_wait(&acce[a], (uint32_t)(((t / kAcc) + 1) & 1), kWaitCycles))
+                        ok = false;
+                    if (!ok) break;
+                    tc::fence_after_sync();
+#pragma unroll
+                    for (int st = 0; st < 2 * kTaps; ++st) {
+                        const int k = st >> 1, h = st & 1, dy = k / 3 - 1, dx = k % 3 - 1;
+                        const int slot = (int)((n0 + j + 1 + dy) % kRing);
+                        const uint64_t ad =
+                            tc::smem_desc(ring_u32 + slot * kRowBytes + 2 * h * kPlane + (1 + dx) * 16, kPlane, 128);
+                        const uint64_t bd = tc::smem_desc(b_u32 + (k * kGroups + 2 * h) * kCh * 16, kCh * 16, 128);
+                        tc::mma_bf16(tmem + (uint32_t)(a * kCh), ad, bd, idesc, st > 0 ? 1u : 0u);
+                    }
+                    tc::mma_commit(&accf[a]);
+                    tc::mma_commit(&empty[(n0 + j) % kRing]);
+                    if (j == w.nrows - 1) {
+                        tc::mma_commit(&empty[(n0 + j + 1) % kRing]);
+                        tc::mma_commit(&empty[(n0 + j + 2) % kRing]);
+                    }
+                }
+                n0 += w.nrows + 2;
+            }
+            // every MMA has completed before the TMEM is freed
+            tc::mma_commit(drain);
+            tc::mbar_wait(drain, 0, kWaitCycles);
+        }
+        __syncwarp();
+    } else {
+        const int quad = warp & 3;
+        int64_t t = 0;
+        for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+            const RingUnit w = ring_unit(p, u);
+            for (int j = 0; j < w.nrows; ++j, ++t) {
+                const int a = (int)(t % kAcc);
+                if (!__all_sync(0xffffffffu, tc::mbar_wait(&accf[a], (uint32_t)((t / kAcc) & 1), kWaitCycles))) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                float v[32];
+                const uint32_t ta = tmem + (uint32_t)(a * kCh) + ((uint32_t)(quad * 32) << 16);
+                tc::tmem_ld16(ta, *reinterpret_cast<float(*)[16]>(v));
+                tc::tmem_ld16(ta + 16, *reinterpret_cast<float(*)[16]>(v + 16));
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&acce[a]);
+                const int y = ring_row(p, w.c, w.r0 + j);
+                const int64_t q = (w.c * L + y) * (int64_t)L + w.x0 + quad * 32 + lane;
+#pragma unroll
+                for (int i = 0; i < kCh; ++i) v[i] += sBias[i];
+                if (p.z_out) {
+                    float4 *zo = reinterpret_cast<float4 *>(p.z_out + q * kCh);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) zo[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                }
+                uint32_t pk[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) pk[i] = pack_bf16x2(gelu(v[2 * i]), gelu(v[2 * i + 1]));
+                uint4 *ao = reinterpret_cast<uint4 *>(p.a_out + q * kCh);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) ao[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+            }
+        }
+    }
+    if (!ok) atomicExch(&g_tc_error, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, kAcc * kCh);
     }
 }
 
@@ -856,13 +1088,32 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
     }
     l1_kernel<<<grid1d(C * (int64_t)bd[0].rows * L, kThreads), kThreads, 0, s>>>(ch, bd[0], flip, params,
                                                                                   train ? w.z1 : nullptr, w.a1);
-    cudaFuncSetAttribute(conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
+    if (L % kTileM != 0)
+        cudaFuncSetAttribute(conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
     __nv_bfloat16 *a3 = train ? w.a3 : w.a1;  // inference ping-pongs two buffers
     const int off[2][2] = {{kOffW2, kOffB2}, {kOffW3, kOffB3}};
     const __nv_bfloat16 *ins[2] = {w.a1, w.a2};
     __nv_bfloat16 *outs[2] = {w.a2, a3};
     float *zs[2] = {train ? w.z2 : nullptr, train ? w.z3 : nullptr};
+    const bool ring = L % kTileM == 0;
+    if (ring) cudaFuncSetAttribute(conv32_ring_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmem);
     for (int l = 0; l < 2; ++l) {
+        if (ring) {
+            RingConv p;
+            p.a_in = ins[l];
+            p.a_out = outs[l];
+            p.z_out = zs[l];
+            p.params = params;
+            p.w_off = off[l][0];
+            p.b_off = off[l][1];
+            p.bd = bd[l + 1];
+            p.segs = L / kTileM;
+            p.units_per_col = (bd[l + 1].rows + kUnitRows - 1) / kUnitRows;
+            p.units = C * p.segs * p.units_per_col;
+            const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.units, 2 * info.sm_count));
+            conv32_ring_kernel<<<grid, kRingThreads, kRingSmem, s>>>(p);
+            continue;
+        }
         ConvTc p;
         p.a_in = ins[l];
         p.a_out = outs[l];

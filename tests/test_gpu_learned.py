@@ -58,9 +58,11 @@ def test_param_count_matches_oracle():
 
 
 # (L, C): one row spans 1/4, 1/2, 1 and 2 tiles of 128 pixels, a ragged
-# 160-pixel row, and 40 chains of 64^2 = 1280 tiles, several per CTA (both
-# shared-memory stages and both barrier phases in use)
-@pytest.mark.parametrize("L,C", [(32, 3), (64, 2), (96, 2), (128, 2), (160, 1), (256, 1), (64, 40)])
+# 160-pixel row, 40 chains of 64^2 = 1280 tiles (several per CTA of the
+# general kernel: both shared-memory stages and both barrier phases in use),
+# and 40 chains of 128^2 = 320 units of 16 rows for the row-ring kernel (more
+# units than CTAs; the ring of 10 rows and the 4 accumulators wrap)
+@pytest.mark.parametrize("L,C", [(32, 3), (64, 2), (96, 2), (128, 2), (160, 1), (256, 1), (64, 40), (128, 40)])
 def test_forward_matches_oracle(L, C):
     mv = chains(L, C, 11)
     th = theta32(1)
@@ -129,8 +131,8 @@ def test_flipped_band_pass_rejects_bad_arguments():
                                         mv.work[:1024])
 
 
-def test_backward_and_loss_match_oracle():
-    L, C = 32, 2
+@pytest.mark.parametrize("L,C", [(32, 2), (128, 2)])
+def test_backward_and_loss_match_oracle(L, C):
     mv = chains(L, C, 5)
     th = theta32(2, 0.15)
     params = torch.from_numpy(th).cuda()
