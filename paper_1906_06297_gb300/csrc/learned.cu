@@ -137,8 +137,9 @@ __device__ __forceinline__ void band_pixel(const Band &b, int64_t pb, int64_t &c
 
 __device__ __forceinline__ int wrap(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
 
-// Layer 1 (1 -> 32 channels, from the spins): thread per pixel of the band.
-// Writes a1 (bfloat16) and, when z_out != nullptr, z1 (FP32).
+// Layer 1 (1 -> 32 channels, from the spins): four threads per pixel of the
+// band, thread g computing output channels 8g .. 8g+7.  Writes a1 (bfloat16)
+// and, when z_out != nullptr, z1 (FP32).
 __global__ void __launch_bounds__(kThreads) l1_kernel(Chains ch, Band bd, const int32_t *flip, const float *params,
                                                       float *z_out, __nv_bfloat16 *a_out)
 {
@@ -147,38 +148,35 @@ __global__ void __launch_bounds__(kThreads) l1_kernel(Chains ch, Band bd, const 
     for (int i = threadIdx.x; i < kCh; i += blockDim.x) Bs[i] = bf16r(params[kOffB1 + i]);
     __syncthreads();
     const int L = ch.L;
-    const int64_t npix = bd.C * (int64_t)bd.rows * L;
-    for (int64_t pb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pb < npix; pb += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = bd.C * (int64_t)bd.rows * L * 4;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int g = (int)(e & 3);
         int64_t c;
         int yx;
-        band_pixel(bd, pb, c, yx);
+        band_pixel(bd, e >> 2, c, yx);
         const int y = yx / L, x = yx - y * L;
         const int fb = flip ? flip[c] : -1;
         float s[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) s[k] = spin_at(ch, c, wrap(y + k / 3 - 1, L), wrap(x + k % 3 - 1, L), fb);
         const int64_t q = c * (int64_t)L * L + yx;
-        float *zo = z_out ? z_out + q * kCh : nullptr;
-        uint4 *ao = reinterpret_cast<uint4 *>(a_out + q * kCh);
+        float z[8];
 #pragma unroll
-        for (int o8 = 0; o8 < kCh / 8; ++o8) {
-            uint32_t w[4];
+        for (int j = 0; j < 8; ++j) {
+            const int o = 8 * g + j;
+            float v = Bs[o];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float g[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int o = 8 * o8 + 2 * j + h;
-                    float z = Bs[o];
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) z = fmaf(W[o * 9 + k], s[k], z);
-                    if (zo) zo[o] = z;
-                    g[h] = gelu(z);
-                }
-                w[j] = pack_bf16x2(g[0], g[1]);
-            }
-            ao[o8] = make_uint4(w[0], w[1], w[2], w[3]);
+            for (int k = 0; k < 9; ++k) v = fmaf(W[o * 9 + k], s[k], v);
+            z[j] = v;
         }
+        if (z_out) {
+            float4 *zo = reinterpret_cast<float4 *>(z_out + q * kCh + 8 * g);
+            zo[0] = make_float4(z[0], z[1], z[2], z[3]);
+            zo[1] = make_float4(z[4], z[5], z[6], z[7]);
+        }
+        *reinterpret_cast<uint4 *>(a_out + q * kCh + 8 * g) =
+            make_uint4(pack_bf16x2(gelu(z[0]), gelu(z[1])), pack_bf16x2(gelu(z[2]), gelu(z[3])),
+                       pack_bf16x2(gelu(z[4]), gelu(z[5])), pack_bf16x2(gelu(z[6]), gelu(z[7])));
     }
 }
 
@@ -211,12 +209,8 @@ constexpr int kGroups = kCh / 8;                                      // 16-byte
 constexpr uint32_t kPlane = (kTileM + 2) * 16;
 constexpr uint32_t kAStage = kTaps * kGroups * kPlane;                // 74880 bytes per stage
 constexpr uint32_t kBBytes = kTaps * kGroups * kCh * 16;              // 18432 bytes
-// + bias, barriers and the TMEM slot; padded to 180 KiB so that every
-// address an operand descriptor of this kernel can reach (even one read with
-// LBO and SBO exchanged) lies inside the CTA's own allocation
-constexpr uint32_t kConvSmemUsed = 2 * kAStage + kBBytes + kCh * 4 + 64;
-constexpr uint32_t kConvSmem = 180 * 1024;
-static_assert(kConvSmemUsed <= kConvSmem, "conv shared memory");
+// + bias, barriers and the TMEM slot
+constexpr uint32_t kConvSmem = 2 * kAStage + kBBytes + kCh * 4 + 64;
 constexpr uint32_t kTmemCols = 64;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
@@ -399,24 +393,42 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv32_tc_kernel(const __grid
 //           the row no later tile of the unit reads;
 //   warps 2-5: epilogue, warp w on TMEM lanes 32 (w % 4) .. + 31: loads its
 //           32 pixels x 32 channels, frees the accumulator (acce), adds the
-//           bias and writes z (training) and bf16(gelu(z)).
-constexpr int kRing = 10;       // staged rows
+//           bias and writes z (training) and a = bf16(gelu(z)).
+// PROJ (the last 32-channel layer): layer 4's channel contraction is done
+// here, on the tensor cores, as P[m][k] = sum_i a[m][i] W4[i][k] for the 9
+// taps k (N padded to 16): the epilogue stages the tile's a in shared memory
+// (a3full), the MMA thread multiplies it by W4^T into 16 more TMEM columns
+// (pfull, a3empty), and the epilogue stores P one tile later (pempty), as 9
+// FP32 planes P[k][pixel].  Then a3 itself need not reach global memory
+// (it still does when training, for the backward pass).
+// Dependencies: MMA step t waits on epilogue steps < t only, epilogue step t
+// on MMA steps <= t only, so no wait can close a cycle.
+constexpr int kRing = 8;        // staged rows
 constexpr int kInFlight = 4;    // rows a loader lane keeps in flight
 constexpr int kAcc = 4;         // accumulators of 32 TMEM columns
 constexpr int kUnitRows = 16;   // output rows per work unit
 constexpr int kRingThreads = 192;
-constexpr uint32_t kRowBytes = kGroups * kPlane;  // 8320
-constexpr uint32_t kRingSmemUsed = kRing * kRowBytes + kBBytes + kCh * 4 + (2 * kRing + 2 * kAcc + 1) * 8 + 16;
-// every address an operand descriptor can reach, even read with LBO and SBO
-// exchanged (< 111 KiB), lies inside the allocation
-constexpr uint32_t kRingSmem = 112 * 1024;
-static_assert(kRingSmemUsed <= kRingSmem, "ring shared memory");
+constexpr int kProjN = 16;      // the 9 taps of layer 4, padded to an MMA N
+constexpr uint32_t kRowBytes = kGroups * kPlane;       // 8320: one staged row, or one a3 tile
+constexpr uint32_t kW4Bytes = kGroups * kProjN * 16;   // 1024
+constexpr uint32_t kSmRing = 0;
+constexpr uint32_t kSmA3 = kSmRing + kRing * kRowBytes;
+constexpr uint32_t kSmB = kSmA3 + 2 * kRowBytes;
+constexpr uint32_t kSmW4 = kSmB + kBBytes;
+constexpr uint32_t kSmBias = kSmW4 + kW4Bytes;
+constexpr uint32_t kSmBar = kSmBias + kCh * 4;
+constexpr int kRingBars = 2 * kRing + 2 * kAcc + 8 + 1;
+constexpr uint32_t kRingSmem = kSmBar + kRingBars * 8 + 16;
+constexpr uint32_t kRingTmemCols = 256;  // 4 x 32 accumulator + 2 x 16 projection columns, as a power of two
 static_assert(kRing >= kInFlight + 2, "the loader must never wait for a row it has not published");
+static_assert(2 * kRingSmem <= 228 * 1024, "two CTAs per SM");
+static_assert(kAcc * kCh + 2 * kProjN <= (int)kRingTmemCols && 2 * kRingTmemCols <= 512, "TMEM columns");
 
 struct RingConv {
     const __nv_bfloat16 *a_in;
-    __nv_bfloat16 *a_out;
-    float *z_out;  // nullable
+    __nv_bfloat16 *a_out;  // nullable when PROJ
+    float *z_out;          // nullable
+    float *P;              // PROJ: 9 planes of C L^2
     const float *params;
     int w_off, b_off;
     Band bd;
@@ -451,22 +463,25 @@ __device__ __forceinline__ int ring_row(const RingConv &p, int64_t c, int r)
     return y >= L ? y - L : y;
 }
 
+template <bool PROJ>
 __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __grid_constant__ RingConv p)
 {
     extern __shared__ __align__(1024) uint8_t ring_smem[];
-    uint8_t *ring = ring_smem;
-    uint8_t *sB = ring_smem + kRing * kRowBytes;
-    float *sBias = reinterpret_cast<float *>(sB + kBBytes);
-    uint64_t *full = reinterpret_cast<uint64_t *>(sBias + kCh);
-    uint64_t *empty = full + kRing;
-    uint64_t *accf = empty + kRing;
-    uint64_t *acce = accf + kAcc;
-    uint64_t *drain = acce + kAcc;
+    uint8_t *ring = ring_smem + kSmRing;
+    uint8_t *a3s = ring_smem + kSmA3;
+    uint8_t *sB = ring_smem + kSmB;
+    uint8_t *sW4 = ring_smem + kSmW4;
+    float *sBias = reinterpret_cast<float *>(ring_smem + kSmBias);
+    uint64_t *full = reinterpret_cast<uint64_t *>(ring_smem + kSmBar);
+    uint64_t *empty = full + kRing, *accf = empty + kRing, *acce = accf + kAcc;
+    uint64_t *a3full = acce + kAcc, *a3empty = a3full + 2, *pfull = a3empty + 2, *pempty = pfull + 2;
+    uint64_t *drain = pempty + 2;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(drain + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int L = p.bd.L;
+    const int64_t npix = p.bd.C * (int64_t)L * L;
 
-    if (warp == 1) tc::tmem_alloc(tslot, kAcc * kCh);
+    if (warp == 1) tc::tmem_alloc(tslot, kRingTmemCols);
     if (tid == 0) {
         for (int s = 0; s < kRing; ++s) {
             tc::mbar_init(&full[s], 32);
@@ -475,6 +490,12 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
         for (int a = 0; a < kAcc; ++a) {
             tc::mbar_init(&accf[a], 1);
             tc::mbar_init(&acce[a], 4);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&a3full[b], 4);
+            tc::mbar_init(&a3empty[b], 1);
+            tc::mbar_init(&pfull[b], 1);
+            tc::mbar_init(&pempty[b], 4);
         }
         tc::mbar_init(drain, 1);
         tc::fence_mbar_init();
@@ -486,12 +507,26 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
             make_uint4(pack_bf16x2(w[0], w[9]), pack_bf16x2(w[18], w[27]), pack_bf16x2(w[36], w[45]),
                        pack_bf16x2(w[54], w[63]));
     }
+    if (PROJ) {
+        // W4^T as an N = 16 x K = 32 operand: row n = tap n (zero for n >= 9),
+        // channel group g = input channels 8g .. 8g+7; W4[i][k] at kOffW4 + 9 i + k
+        for (int e = tid; e < kGroups * kProjN; e += blockDim.x) {
+            const int g = e / kProjN, n = e - g * kProjN;
+            uint32_t u[4] = {0u, 0u, 0u, 0u};
+            if (n < 9) {
+                const float *w = p.params + kOffW4 + (8 * g) * 9 + n;
+                for (int j = 0; j < 4; ++j) u[j] = pack_bf16x2(w[(2 * j) * 9], w[(2 * j + 1) * 9]);
+            }
+            *reinterpret_cast<uint4 *>(sW4 + e * 16) = make_uint4(u[0], u[1], u[2], u[3]);
+        }
+    }
     if (tid < kCh) sBias[tid] = bf16r(p.params[p.b_off + tid]);
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
+    const uint32_t tproj = tmem + (uint32_t)(kAcc * kCh);
     bool ok = true;
 
     if (warp == 0) {
@@ -527,7 +562,25 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_bf16_f32(kTileM, kCh);
+            const uint32_t idesc_p = tc::idesc_bf16_f32(kTileM, kProjN);
             const uint32_t ring_u32 = tc::smem_u32(ring), b_u32 = tc::smem_u32(sB);
+            const uint32_t a3_u32 = tc::smem_u32(a3s), w4_u32 = tc::smem_u32(sW4);
+            // layer-4 projection of tile s (its a3 staged by the epilogue)
+            auto issue_proj = [&](int64_t s) -> bool {
+                const int b = (int)(s & 1);
+                if (!tc::mbar_wait(&a3full[b], (uint32_t)((s >> 1) & 1), kWaitCycles)) return false;
+                if (s >= 2 && !tc::mbar_wait(&pempty[b], (uint32_t)(((s >> 1) + 1) & 1), kWaitCycles)) return false;
+                tc::fence_after_sync();
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint64_t ad = tc::smem_desc(a3_u32 + b * kRowBytes + 2 * h * kPlane, kPlane, 128);
+                    const uint64_t bd = tc::smem_desc(w4_u32 + 2 * h * kProjN * 16, kProjN * 16, 128);
+                    tc::mma_bf16(tproj + (uint32_t)(b * kProjN), ad, bd, idesc_p, h > 0 ? 1u : 0u);
+                }
+                tc::mma_commit(&pfull[b]);
+                tc::mma_commit(&a3empty[b]);
+                return true;
+            };
             int64_t n0 = 0, t = 0, ready = 0;
             for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
                 const RingUnit w = ring_unit(p, u);
@@ -556,17 +609,34 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
                         tc::mma_commit(&empty[(n0 + j + 1) % kRing]);
                         tc::mma_commit(&empty[(n0 + j + 2) % kRing]);
                     }
+                    if (PROJ && t >= 1 && !issue_proj(t - 1)) ok = false;
                 }
                 n0 += w.nrows + 2;
             }
+            if (PROJ && ok && t >= 1 && !issue_proj(t - 1)) ok = false;
             // every MMA has completed before the TMEM is freed
             tc::mma_commit(drain);
             tc::mbar_wait(drain, 0, kWaitCycles);
         }
         __syncwarp();
     } else {
-        const int quad = warp & 3;
-        int64_t t = 0;
+        const int quad = warp & 3, m = quad * 32 + lane;
+        // P of tile s, pixel q (one tile behind the accumulators)
+        auto read_proj = [&](int64_t s, int64_t q) -> bool {
+            const int b = (int)(s & 1);
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&pfull[b], (uint32_t)((s >> 1) & 1), kWaitCycles)))
+                return false;
+            tc::fence_after_sync();
+            float pv[16];
+            tc::tmem_ld16(tproj + (uint32_t)(b * kProjN) + ((uint32_t)(quad * 32) << 16), pv);
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&pempty[b]);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) p.P[k * npix + q] = pv[k];
+            return true;
+        };
+        int64_t t = 0, q_prev = 0;
         for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
             const RingUnit w = ring_unit(p, u);
             for (int j = 0; j < w.nrows; ++j, ++t) {
@@ -584,7 +654,7 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&acce[a]);
                 const int y = ring_row(p, w.c, w.r0 + j);
-                const int64_t q = (w.c * L + y) * (int64_t)L + w.x0 + quad * 32 + lane;
+                const int64_t q = (w.c * L + y) * (int64_t)L + w.x0 + m;
 #pragma unroll
                 for (int i = 0; i < kCh; ++i) v[i] += sBias[i];
                 if (p.z_out) {
@@ -595,36 +665,94 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
                 uint32_t pk[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) pk[i] = pack_bf16x2(gelu(v[2 * i]), gelu(v[2 * i + 1]));
-                uint4 *ao = reinterpret_cast<uint4 *>(p.a_out + q * kCh);
+                if (p.a_out) {
+                    uint4 *ao = reinterpret_cast<uint4 *>(p.a_out + q * kCh);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) ao[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+                    for (int i = 0; i < 4; ++i) ao[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+                }
+                if (PROJ) {
+                    const int b = (int)(t & 1);
+                    if (t >= 2 && !__all_sync(0xffffffffu, tc::mbar_wait(&a3empty[b], (uint32_t)(((t >> 1) + 1) & 1),
+                                                                          kWaitCycles))) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *dst = a3s + b * kRowBytes + m * 16;
+#pragma unroll
+                    for (int g = 0; g < kGroups; ++g)
+                        *reinterpret_cast<uint4 *>(dst + g * kPlane) =
+                            make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
+                    tc::fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&a3full[b]);
+                    if (t >= 1 && !read_proj(t - 1, q_prev)) {
+                        ok = false;
+                        break;
+                    }
+                    q_prev = q;
+                }
             }
         }
+        if (PROJ && ok && t >= 1 && !read_proj(t - 1, q_prev)) ok = false;
     }
     if (!ok) atomicExch(&g_tc_error, 1);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 1) {
         tc::fence_after_sync();
-        tc::tmem_dealloc(tmem, kAcc * kCh);
+        tc::tmem_dealloc(tmem, kRingTmemCols);
     }
 }
 
-// Layer 4 and the block mean: warp per (chain, block) over `brows` block rows
-// per chain (all of them in a full pass; in a band pass the flipped block's
-// row and its two neighbours), two pixels per lane, lane sums in a fixed order
-// then a fixed shuffle tree.
-__global__ void __launch_bounds__(kThreads) l4_pool_kernel(int L, int64_t C, int brows, const int32_t *flip,
-                                                           const float *params, const __nv_bfloat16 *a3,
-                                                           float *logits)
+// Layer 4's channel contraction for the general conv kernel: thread per pixel
+// of the band, P[k][q] = sum_i W4[i][k] a3(q)[i] (i in order).
+__global__ void __launch_bounds__(kThreads) l4_project_kernel(Band bd, const float *params, const __nv_bfloat16 *a3,
+                                                              float *P)
 {
-    __shared__ float W[kN1];
-    __shared__ float b4;
+    __shared__ float W[kN1];  // W4[i][k] at 9 i + k
     for (int i = threadIdx.x; i < kN1; i += blockDim.x) W[i] = bf16r(params[kOffW4 + i]);
-    if (threadIdx.x == 0) b4 = bf16r(params[kOffB4]);
     __syncthreads();
+    const int L = bd.L;
+    const int64_t npix = bd.C * (int64_t)L * L;
+    const int64_t n = bd.C * (int64_t)bd.rows * L;
+    for (int64_t pb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pb < n; pb += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c;
+        int yx;
+        band_pixel(bd, pb, c, yx);
+        const int64_t q = c * (int64_t)L * L + yx;
+        const uint4 *src = reinterpret_cast<const uint4 *>(a3 + q * kCh);
+        float acc[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g) {
+            const uint4 v = __ldg(src + g);
+            const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float lo = bf16_lo(u[j]), hi = bf16_hi(u[j]);
+                const int i = 8 * g + 2 * j;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) acc[k] = fmaf(W[(i + 1) * 9 + k], hi, fmaf(W[i * 9 + k], lo, acc[k]));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) P[k * npix + q] = acc[k];
+    }
+}
+
+// Layer 4 and the block mean from the projections: z4(y, x) = b4 + sum over
+// taps k of P[k](y + dy_k, x + dx_k).  Warp per (chain, block) over `brows`
+// block rows per chain (all of them in a full pass; in a band pass the
+// flipped block's row and its two neighbours), two pixels per lane, taps in
+// order, then a fixed shuffle tree.
+__global__ void __launch_bounds__(kThreads) pool_kernel(int L, int64_t C, int brows, const int32_t *flip,
+                                                        const float *params, const float *P, float *logits)
+{
+    const float b4 = bf16r(params[kOffB4]);
     const int nb1 = L / kBlk, nb = nb1 * nb1;
     const int lane = threadIdx.x & 31;
+    const int64_t npix = C * (int64_t)L * L;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int per = brows * nb1;
     for (int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < C * per; wi += nw) {
@@ -635,31 +763,20 @@ __global__ void __launch_bounds__(kThreads) l4_pool_kernel(int L, int64_t C, int
             const int f = flip[c];
             by = wrap((f < 0 ? 0 : f / nb1) - 1 + rb, nb1);
         }
-        const int b = by * nb1 + bx;
+        const float *Pc = P + c * (int64_t)L * L;
         float part = 0.0f;
         for (int e = 0; e < 2; ++e) {
             const int pix = lane + 32 * e;  // 0..63 within the block
             const int y = by * kBlk + pix / kBlk, x = bx * kBlk + pix % kBlk;
             float z = b4;
-            for (int k = 0; k < 9; ++k) {
-                const int yy = wrap(y + k / 3 - 1, L), xx = wrap(x + k % 3 - 1, L);
-                const uint4 *src = reinterpret_cast<const uint4 *>(a3 + ((c * L + yy) * (int64_t)L + xx) * kCh);
 #pragma unroll
-                for (int g = 0; g < kGroups; ++g) {
-                    const uint4 v = __ldg(src + g);
-                    const uint32_t u[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        z = fmaf(W[(8 * g + 2 * j) * 9 + k], bf16_lo(u[j]), z);
-                        z = fmaf(W[(8 * g + 2 * j + 1) * 9 + k], bf16_hi(u[j]), z);
-                    }
-                }
-            }
+            for (int k = 0; k < 9; ++k)
+                z += __ldg(Pc + k * npix + wrap(y + k / 3 - 1, L) * (int64_t)L + wrap(x + k % 3 - 1, L));
             part += z;
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-        if (lane == 0) logits[c * nb + b] = part * (1.0f / (kBlk * kBlk));
+        if (lane == 0) logits[c * nb + by * nb1 + bx] = part * (1.0f / (kBlk * kBlk));
     }
 }
 
@@ -1023,9 +1140,10 @@ int check_chains(int64_t L, int64_t C)
 
 // Work layout: training keeps z1 z2 z3 (FP32), a1 a2 a3 (bfloat16) and two
 // FP32 gradient buffers, then the weight-gradient partials; inference keeps
-// a1 and a2 (bfloat16; a3 reuses a1's buffer).
+// a1 and a2 (bfloat16; where a3 is written at all it reuses a1's buffer).
+// Both end with the 9 FP32 planes P of layer 4's tap projections.
 struct NetWork {
-    float *z1, *z2, *z3, *da, *db, *partial;
+    float *z1, *z2, *z3, *da, *db, *partial, *P;
     __nv_bfloat16 *a1, *a2, *a3;
     int64_t n_cta;
     size_t bytes;
@@ -1057,6 +1175,7 @@ NetWork net_layout(int64_t L, int64_t C, int train, char *base)
         w.a1 = (__nv_bfloat16 *)take(pix * 2); w.a2 = (__nv_bfloat16 *)take(pix * 2);
         w.a3 = w.a1;
     }
+    w.P = (float *)take((size_t)C * L * L * 9 * sizeof(float));
     w.bytes = o;
     return w;
 }
@@ -1086,23 +1205,22 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
         bd[l].lead = band ? kBandLead[l] : 0;
         bd[l].flip = band ? flip : nullptr;
     }
-    l1_kernel<<<grid1d(C * (int64_t)bd[0].rows * L, kThreads), kThreads, 0, s>>>(ch, bd[0], flip, params,
-                                                                                  train ? w.z1 : nullptr, w.a1);
-    if (L % kTileM != 0)
-        cudaFuncSetAttribute(conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
-    __nv_bfloat16 *a3 = train ? w.a3 : w.a1;  // inference ping-pongs two buffers
+    l1_kernel<<<grid1d(C * (int64_t)bd[0].rows * L * 4, kThreads), kThreads, 0, s>>>(ch, bd[0], flip, params,
+                                                                                      train ? w.z1 : nullptr, w.a1);
     const int off[2][2] = {{kOffW2, kOffB2}, {kOffW3, kOffB3}};
     const __nv_bfloat16 *ins[2] = {w.a1, w.a2};
-    __nv_bfloat16 *outs[2] = {w.a2, a3};
     float *zs[2] = {train ? w.z2 : nullptr, train ? w.z3 : nullptr};
-    const bool ring = L % kTileM == 0;
-    if (ring) cudaFuncSetAttribute(conv32_ring_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmem);
-    for (int l = 0; l < 2; ++l) {
-        if (ring) {
+    if (L % kTileM == 0) {
+        // row-ring kernels; the second one also projects onto layer 4's taps
+        cudaFuncSetAttribute(conv32_ring_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmem);
+        cudaFuncSetAttribute(conv32_ring_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmem);
+        __nv_bfloat16 *outs[2] = {w.a2, train ? w.a3 : nullptr};
+        for (int l = 0; l < 2; ++l) {
             RingConv p;
             p.a_in = ins[l];
             p.a_out = outs[l];
             p.z_out = zs[l];
+            p.P = w.P;
             p.params = params;
             p.w_off = off[l][0];
             p.b_off = off[l][1];
@@ -1111,25 +1229,34 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
             p.units_per_col = (bd[l + 1].rows + kUnitRows - 1) / kUnitRows;
             p.units = C * p.segs * p.units_per_col;
             const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.units, 2 * info.sm_count));
-            conv32_ring_kernel<<<grid, kRingThreads, kRingSmem, s>>>(p);
-            continue;
+            if (l == 0)
+                conv32_ring_kernel<false><<<grid, kRingThreads, kRingSmem, s>>>(p);
+            else
+                conv32_ring_kernel<true><<<grid, kRingThreads, kRingSmem, s>>>(p);
         }
-        ConvTc p;
-        p.a_in = ins[l];
-        p.a_out = outs[l];
-        p.z_out = zs[l];
-        p.params = params;
-        p.w_off = off[l][0];
-        p.b_off = off[l][1];
-        p.bd = bd[l + 1];
-        p.tiles = C * (int64_t)bd[l + 1].rows * L / kTileM;
-        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.tiles, info.sm_count));
-        conv32_tc_kernel<<<grid, kConvThreads, kConvSmem, s>>>(p);
+    } else {
+        cudaFuncSetAttribute(conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
+        __nv_bfloat16 *outs[2] = {w.a2, w.a3};  // inference: a3 reuses a1's buffer
+        for (int l = 0; l < 2; ++l) {
+            ConvTc p;
+            p.a_in = ins[l];
+            p.a_out = outs[l];
+            p.z_out = zs[l];
+            p.params = params;
+            p.w_off = off[l][0];
+            p.b_off = off[l][1];
+            p.bd = bd[l + 1];
+            p.tiles = C * (int64_t)bd[l + 1].rows * L / kTileM;
+            const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.tiles, info.sm_count));
+            conv32_tc_kernel<<<grid, kConvThreads, kConvSmem, s>>>(p);
+        }
+        l4_project_kernel<<<grid1d(C * (int64_t)bd[2].rows * L, kThreads), kThreads, 0, s>>>(bd[2], params, w.a3,
+                                                                                             w.P);
     }
     const int brows = band ? kBandRows[3] : L / kBlk;
     const int64_t warps = C * brows * (L / kBlk);
-    l4_pool_kernel<<<grid1d(warps * 32, kThreads), kThreads, 0, s>>>(L, C, brows, band ? flip : nullptr, params, a3,
-                                                                     logits);
+    pool_kernel<<<grid1d(warps * 32, kThreads), kThreads, 0, s>>>(L, C, brows, band ? flip : nullptr, params, w.P,
+                                                                  logits);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ISING_OK : nfail(ISING_ECUDA, cudaGetErrorString(e));
 }
