@@ -68,7 +68,44 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// GELU z Phi(z), Phi(z) = erfc(-z / sqrt 2) / 2, with erfc from the Chebyshev
+// fit of Numerical Recipes (Press et al., 2nd ed., Sec. 6.2, "erfcc"):
+// erfc(x) = t exp(-x^2 + P(t)), t = 1 / (1 + x / 2), P of degree 9, fractional
+// error below 1.2e-7 for every x >= 0, so Phi keeps its relative accuracy for
+// negative z too.  Evaluated in FP32 with the hardware reciprocal and 2^x the
+// relative error of gelu is about 5e-6 for |z| < 6 (the rounding of the
+// exponent -x^2 + P), far below the bfloat16 step the result is rounded to.
+__device__ __forceinline__ float gelu(float z)
+{
+    const float x = fabsf(z) * 0.70710678118654752f;
+    const float t = rcp_approx(fmaf(0.5f, x, 1.0f));
+    float p = 0.17087277f;
+    p = fmaf(p, t, -0.82215223f);
+    p = fmaf(p, t, 1.48851587f);
+    p = fmaf(p, t, -1.13520398f);
+    p = fmaf(p, t, 0.27886807f);
+    p = fmaf(p, t, -0.18628806f);
+    p = fmaf(p, t, 0.09678418f);
+    p = fmaf(p, t, 0.37409196f);
+    p = fmaf(p, t, 1.00002368f);
+    p = fmaf(p, t, -1.26551223f);
+    const float half = 0.5f * t * ex2_approx(fmaf(-x, x, p) * 1.44269504088896341f);  // Phi(-|z|)
+    return z * (z >= 0.0f ? 1.0f - half : half);
+}
 
 __device__ __forceinline__ float gelu_grad(float z)
 {
@@ -137,46 +174,53 @@ __device__ __forceinline__ void band_pixel(const Band &b, int64_t pb, int64_t &c
 
 __device__ __forceinline__ int wrap(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
 
-// Layer 1 (1 -> 32 channels, from the spins): four threads per pixel of the
-// band, thread g computing output channels 8g .. 8g+7.  Writes a1 (bfloat16)
-// and, when z_out != nullptr, z1 (FP32).
-__global__ void __launch_bounds__(kThreads) l1_kernel(Chains ch, Band bd, const int32_t *flip, const float *params,
-                                                      float *z_out, __nv_bfloat16 *a_out)
+// Layer 1 (1 -> 32 channels, from the spins): thread per pixel of the band;
+// blockIdx.y walks the chains and blockIdx.x the 128-pixel tiles of a chain's
+// band, so all index arithmetic is 32-bit.  Writes a1 (bfloat16) and, when
+// z_out != nullptr, z1 (FP32).
+constexpr int kL1Threads = 128;
+
+__global__ void __launch_bounds__(kL1Threads, 6) l1_kernel(Chains ch, Band bd, const int32_t *flip, const float *params,
+                                                        float *z_out, __nv_bfloat16 *a_out)
 {
     __shared__ float W[kN1], Bs[kCh];
     for (int i = threadIdx.x; i < kN1; i += blockDim.x) W[i] = bf16r(params[kOffW1 + i]);
     for (int i = threadIdx.x; i < kCh; i += blockDim.x) Bs[i] = bf16r(params[kOffB1 + i]);
     __syncthreads();
     const int L = ch.L;
-    const int64_t n = bd.C * (int64_t)bd.rows * L * 4;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int g = (int)(e & 3);
-        int64_t c;
-        int yx;
-        band_pixel(bd, e >> 2, c, yx);
-        const int y = yx / L, x = yx - y * L;
+    const int per = bd.rows * L;  // band pixels per chain, a multiple of 128
+    for (int64_t c = blockIdx.y; c < bd.C; c += gridDim.y) {
+        const int row0 = band_row0(bd, c);
         const int fb = flip ? flip[c] : -1;
-        float s[9];
+        for (int r = blockIdx.x * kL1Threads + threadIdx.x; r < per; r += gridDim.x * kL1Threads) {
+            const int ry = r / L, x = r - ry * L;
+            int y = row0 + ry;
+            y = y >= L ? y - L : y;
+            float sp[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) s[k] = spin_at(ch, c, wrap(y + k / 3 - 1, L), wrap(x + k % 3 - 1, L), fb);
-        const int64_t q = c * (int64_t)L * L + yx;
-        float z[8];
+            for (int k = 0; k < 9; ++k) sp[k] = spin_at(ch, c, wrap(y + k / 3 - 1, L), wrap(x + k % 3 - 1, L), fb);
+            const int64_t q = (c * L + y) * (int64_t)L + x;
+            float4 *zo = z_out ? reinterpret_cast<float4 *>(z_out + q * kCh) : nullptr;
+            uint4 *ao = reinterpret_cast<uint4 *>(a_out + q * kCh);
+#pragma unroll 1
+            for (int g = 0; g < kCh / 8; ++g) {
+                float z[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int o = 8 * g + j;
-            float v = Bs[o];
+                for (int j = 0; j < 8; ++j) {
+                    const int o = 8 * g + j;
+                    float v = Bs[o];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) v = fmaf(W[o * 9 + k], s[k], v);
-            z[j] = v;
+                    for (int k = 0; k < 9; ++k) v = fmaf(W[o * 9 + k], sp[k], v);
+                    z[j] = v;
+                }
+                if (zo) {
+                    zo[2 * g] = make_float4(z[0], z[1], z[2], z[3]);
+                    zo[2 * g + 1] = make_float4(z[4], z[5], z[6], z[7]);
+                }
+                ao[g] = make_uint4(pack_bf16x2(gelu(z[0]), gelu(z[1])), pack_bf16x2(gelu(z[2]), gelu(z[3])),
+                                   pack_bf16x2(gelu(z[4]), gelu(z[5])), pack_bf16x2(gelu(z[6]), gelu(z[7])));
+            }
         }
-        if (z_out) {
-            float4 *zo = reinterpret_cast<float4 *>(z_out + q * kCh + 8 * g);
-            zo[0] = make_float4(z[0], z[1], z[2], z[3]);
-            zo[1] = make_float4(z[4], z[5], z[6], z[7]);
-        }
-        *reinterpret_cast<uint4 *>(a_out + q * kCh + 8 * g) =
-            make_uint4(pack_bf16x2(gelu(z[0]), gelu(z[1])), pack_bf16x2(gelu(z[2]), gelu(z[3])),
-                       pack_bf16x2(gelu(z[4]), gelu(z[5])), pack_bf16x2(gelu(z[6]), gelu(z[7])));
     }
 }
 
@@ -1205,8 +1249,14 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
         bd[l].lead = band ? kBandLead[l] : 0;
         bd[l].flip = band ? flip : nullptr;
     }
-    l1_kernel<<<grid1d(C * (int64_t)bd[0].rows * L * 4, kThreads), kThreads, 0, s>>>(ch, bd[0], flip, params,
-                                                                                      train ? w.z1 : nullptr, w.a1);
+    {
+        // enough CTAs for ~16 per SM, tiles of a chain first, then chains
+        const int64_t tiles = (int64_t)bd[0].rows * L / kL1Threads;
+        const int64_t want = (int64_t)info.sm_count * 16;
+        const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, want));
+        const unsigned gy = (unsigned)std::max<int64_t>(1, std::min<int64_t>({C, 65535, (want + gx - 1) / gx}));
+        l1_kernel<<<dim3(gx, gy), kL1Threads, 0, s>>>(ch, bd[0], flip, params, train ? w.z1 : nullptr, w.a1);
+    }
     const int off[2][2] = {{kOffW2, kOffB2}, {kOffW3, kOffB3}};
     const __nv_bfloat16 *ins[2] = {w.a1, w.a2};
     float *zs[2] = {train ? w.z2 : nullptr, train ? w.z3 : nullptr};
