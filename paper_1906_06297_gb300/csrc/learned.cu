@@ -16,8 +16,11 @@
 //   logit of block b = mean of z4 over the block; q(b) = softmax(logits)_b.
 // gelu(z) = z * Phi(z).  Parameters are one FP32 vector in the order
 // W1[32][9], b1[32], W2[32][32][9], b2[32], W3[32][32][9], b3[32], W4[32][9], b4[1].
-// Activations are NHWC bfloat16 (32 channels, 64 bytes per pixel); the
-// pre-activations z kept for training are NHWC FP32.  The two 32 -> 32 layers
+// Activations are bfloat16, 32 channels (64 bytes) per pixel, in rows of L + 2
+// pixels: column 0 repeats pixel L - 1 and column L + 1 pixel 0 (the periodic
+// halo, written by the producer), so that one rectangular copy fetches a row
+// segment with both neighbours.  The pre-activations z kept for training and
+// the gradients are NHWC FP32 without halo.  The two 32 -> 32 layers
 // run on the tensor cores (tcgen05, see conv32_tc_kernel); every reduction has
 // a fixed order, so a forward pass is a deterministic function of the state.
 //
@@ -27,6 +30,7 @@
 // floor(2^32 min(1, exp(-beta dE + log q_x'(b) - log q_x(b)))), dE the exact
 // integer energy change (twice the boundary bond sum).  Softmax sums run in
 // block order in FP64.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -34,6 +38,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/ising.h"
 #include "common.cuh"
@@ -174,6 +179,19 @@ __device__ __forceinline__ void band_pixel(const Band &b, int64_t pb, int64_t &c
 
 __device__ __forceinline__ int wrap(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
 
+// Index of pixel (y, x), -1 <= x <= L, of chain c in an activation buffer
+// (rows of L + 2 pixels with the periodic halo columns).
+__device__ __forceinline__ int64_t apix(int L, int64_t c, int y, int x) { return (c * L + y) * (int64_t)(L + 2) + x + 1; }
+
+// Stores one 16-byte part of pixel (y, x)'s activations and, for x = 0 or
+// x = L - 1, its copy in the halo column.
+__device__ __forceinline__ void store_act(__nv_bfloat16 *a, int L, int64_t c, int y, int x, int off, uint4 v)
+{
+    *reinterpret_cast<uint4 *>(a + apix(L, c, y, x) * kCh + off) = v;
+    if (x == 0) *reinterpret_cast<uint4 *>(a + apix(L, c, y, L) * kCh + off) = v;
+    if (x == L - 1) *reinterpret_cast<uint4 *>(a + apix(L, c, y, -1) * kCh + off) = v;
+}
+
 // Layer 1 (1 -> 32 channels, from the spins): thread per pixel of the band;
 // blockIdx.y walks the chains and blockIdx.x the 128-pixel tiles of a chain's
 // band, so all index arithmetic is 32-bit.  Writes a1 (bfloat16) and, when
@@ -201,7 +219,6 @@ __global__ void __launch_bounds__(kL1Threads, 6) l1_kernel(Chains ch, Band bd, c
             for (int k = 0; k < 9; ++k) sp[k] = spin_at(ch, c, wrap(y + k / 3 - 1, L), wrap(x + k % 3 - 1, L), fb);
             const int64_t q = (c * L + y) * (int64_t)L + x;
             float4 *zo = z_out ? reinterpret_cast<float4 *>(z_out + q * kCh) : nullptr;
-            uint4 *ao = reinterpret_cast<uint4 *>(a_out + q * kCh);
 #pragma unroll 1
             for (int g = 0; g < kCh / 8; ++g) {
                 float z[8];
@@ -217,8 +234,9 @@ __global__ void __launch_bounds__(kL1Threads, 6) l1_kernel(Chains ch, Band bd, c
                     zo[2 * g] = make_float4(z[0], z[1], z[2], z[3]);
                     zo[2 * g + 1] = make_float4(z[4], z[5], z[6], z[7]);
                 }
-                ao[g] = make_uint4(pack_bf16x2(gelu(z[0]), gelu(z[1])), pack_bf16x2(gelu(z[2]), gelu(z[3])),
-                                   pack_bf16x2(gelu(z[4]), gelu(z[5])), pack_bf16x2(gelu(z[6]), gelu(z[7])));
+                store_act(a_out, L, c, y, x, 8 * g,
+                          make_uint4(pack_bf16x2(gelu(z[0]), gelu(z[1])), pack_bf16x2(gelu(z[2]), gelu(z[3])),
+                                     pack_bf16x2(gelu(z[4]), gelu(z[5])), pack_bf16x2(gelu(z[6]), gelu(z[7]))));
             }
         }
     }
@@ -291,14 +309,14 @@ __device__ __forceinline__ void conv_gather(const ConvTc &p, int64_t tile, uint8
         py[h] = yx / L;
         px[h] = yx - py[h] * L;
     }
-    const uint4 *src = reinterpret_cast<const uint4 *>(p.a_in) + c * (int64_t)L * L * kGroups;
+    const uint4 *src = reinterpret_cast<const uint4 *>(p.a_in);
     uint4 v[2 * kTaps];
 #pragma unroll
     for (int k = 0; k < kTaps; ++k)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int yy = wrap(py[h] + k / 3 - 1, L), xx = wrap(px[h] + k % 3 - 1, L);
-            v[2 * k + h] = __ldg(src + ((int64_t)yy * L + xx) * kGroups + g);
+            v[2 * k + h] = __ldg(src + apix(L, c, yy, xx) * kGroups + g);
         }
 #pragma unroll
     for (int k = 0; k < kTaps; ++k)
@@ -314,7 +332,9 @@ __device__ __forceinline__ void conv_epilogue(const ConvTc &p, int64_t tile, uin
     int64_t c;
     int yx0;
     tile_origin(p, tile, c, yx0);
-    const int64_t q = c * (int64_t)p.bd.L * p.bd.L + yx0 + quad * 32 + lane;
+    const int L = p.bd.L;
+    const int yx = yx0 + quad * 32 + lane, y = yx / L, x = yx - y * L;
+    const int64_t q = c * (int64_t)L * L + yx;
     float v[16];
     tc::tmem_ld16(tacc + (uint32_t)(half * 16) + ((uint32_t)(quad * 32) << 16), v);
 #pragma unroll
@@ -327,9 +347,8 @@ __device__ __forceinline__ void conv_epilogue(const ConvTc &p, int64_t tile, uin
     uint32_t w[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) w[j] = pack_bf16x2(gelu(v[2 * j]), gelu(v[2 * j + 1]));
-    uint4 *ao = reinterpret_cast<uint4 *>(p.a_out + q * kCh + half * 16);
-    ao[0] = make_uint4(w[0], w[1], w[2], w[3]);
-    ao[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    store_act(p.a_out, L, c, y, x, half * 16, make_uint4(w[0], w[1], w[2], w[3]));
+    store_act(p.a_out, L, c, y, x, half * 16 + 8, make_uint4(w[4], w[5], w[6], w[7]));
 }
 
 __global__ void __launch_bounds__(kConvThreads, 1) conv32_tc_kernel(const __grid_constant__ ConvTc p)
@@ -426,34 +445,40 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv32_tc_kernel(const __grid
 // is up to kUnitRows consecutive output rows of one (chain, 128-column
 // segment); it stages its rows r0 - 1 .. r0 + n once each, as a halo row of
 // 130 pixels (x0 - 1 .. x0 + 128, periodic) in 4 channel-group planes of
-// kPlane bytes, so the operand of tap (dy, dx) is the staged row y + dy
-// offset by (1 + dx) x 16 bytes (LBO = kPlane, SBO = 128 as before).
+// kRingPlane bytes, so the operand of tap (dy, dx) is the staged row y + dy
+// offset by (1 + dx) x 16 bytes (LBO = kRingPlane, SBO = 128).
 // Warp roles, linked by mbarriers (every wait bounded):
-//   warp 0: loader -- cp.async of each row (4 lanes per pixel: 64 contiguous
-//           bytes), up to kInFlight rows in flight per lane; after a row has
-//           landed each lane fences the async proxy and arrives on full[slot];
+//   warp 0: loader -- lane 0 fetches each row with four tensor copies (TMA),
+//           one per channel group: a box of 8 channels x 130 pixels of the
+//           padded row (its halo columns included), completing on full[slot];
 //   warp 1: lane 0 issues the 18 MMAs of each tile into one of kAcc
 //           accumulators, then commits to accf[acc] and to empty[slot] of
 //           the row no later tile of the unit reads;
-//   warps 2-5: epilogue, warp w on TMEM lanes 32 (w % 4) .. + 31: loads its
-//           32 pixels x 32 channels, frees the accumulator (acce), adds the
-//           bias and writes z (training) and a = bf16(gelu(z)).
+//   warps 2-9: epilogue, warp w on TMEM lanes 32 (w % 4) .. + 31 (its 32
+//           pixels) and columns 16 h .. 16 h + 15, h = (w - 2) / 4 (its 16
+//           channels): loads them, frees the accumulator (acce, 8 arrivals),
+//           adds the bias and writes z (training) and a = bf16(gelu(z)).
+//           Two warps per TMEM lane quadrant, four per SM sub-partition with
+//           two CTAs per SM, hide the latency of the GELU arithmetic.
 // PROJ (the last 32-channel layer): layer 4's channel contraction is done
 // here, on the tensor cores, as P[m][k] = sum_i a[m][i] W4[i][k] for the 9
 // taps k (N padded to 16): the epilogue stages the tile's a in shared memory
 // (a3full), the MMA thread multiplies it by W4^T into 16 more TMEM columns
-// (pfull, a3empty), and the epilogue stores P one tile later (pempty), as 9
-// FP32 planes P[k][pixel].  Then a3 itself need not reach global memory
+// (pfull, a3empty), and the epilogue warps of the first channel half store P
+// one tile later (pempty), as 9 FP32 planes P[k][pixel].  Then a3 itself need not reach global memory
 // (it still does when training, for the backward pass).
 // Dependencies: MMA step t waits on epilogue steps < t only, epilogue step t
 // on MMA steps <= t only, so no wait can close a cycle.
-constexpr int kRing = 8;        // staged rows
-constexpr int kInFlight = 4;    // rows a loader lane keeps in flight
+constexpr int kRing = 8;        // staged rows (a power of two)
 constexpr int kAcc = 4;         // accumulators of 32 TMEM columns
 constexpr int kUnitRows = 16;   // output rows per work unit
-constexpr int kRingThreads = 192;
+constexpr int kEpiWarps = 8;
+constexpr int kRingThreads = 64 + 32 * kEpiWarps;
 constexpr int kProjN = 16;      // the 9 taps of layer 4, padded to an MMA N
-constexpr uint32_t kRowBytes = kGroups * kPlane;       // 8320: one staged row, or one a3 tile
+// channel-group planes 2176 bytes apart: each tensor copy lands on a 128-byte
+// boundary; 130 of its 136 16-byte entries are used
+constexpr uint32_t kRingPlane = 17 * 128;
+constexpr uint32_t kRowBytes = kGroups * kRingPlane;   // one staged row, or one a3 tile
 constexpr uint32_t kW4Bytes = kGroups * kProjN * 16;   // 1024
 constexpr uint32_t kSmRing = 0;
 constexpr uint32_t kSmA3 = kSmRing + kRing * kRowBytes;
@@ -464,11 +489,12 @@ constexpr uint32_t kSmBar = kSmBias + kCh * 4;
 constexpr int kRingBars = 2 * kRing + 2 * kAcc + 8 + 1;
 constexpr uint32_t kRingSmem = kSmBar + kRingBars * 8 + 16;
 constexpr uint32_t kRingTmemCols = 256;  // 4 x 32 accumulator + 2 x 16 projection columns, as a power of two
-static_assert(kRing >= kInFlight + 2, "the loader must never wait for a row it has not published");
+static_assert((kRing & (kRing - 1)) == 0 && kRing >= 6, "ring of a power-of-two rows, 3 in use and 3 ahead");
 static_assert(2 * kRingSmem <= 228 * 1024, "two CTAs per SM");
 static_assert(kAcc * kCh + 2 * kProjN <= (int)kRingTmemCols && 2 * kRingTmemCols <= 512, "TMEM columns");
 
 struct RingConv {
+    CUtensorMap tmap[kGroups];  // a_in viewed as (8 channels, L + 2 pixels, L rows, C chains), channel group g
     const __nv_bfloat16 *a_in;
     __nv_bfloat16 *a_out;  // nullable when PROJ
     float *z_out;          // nullable
@@ -528,15 +554,15 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
     if (warp == 1) tc::tmem_alloc(tslot, kRingTmemCols);
     if (tid == 0) {
         for (int s = 0; s < kRing; ++s) {
-            tc::mbar_init(&full[s], 32);
+            tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
         for (int a = 0; a < kAcc; ++a) {
             tc::mbar_init(&accf[a], 1);
-            tc::mbar_init(&acce[a], 4);
+            tc::mbar_init(&acce[a], kEpiWarps);
         }
         for (int b = 0; b < 2; ++b) {
-            tc::mbar_init(&a3full[b], 4);
+            tc::mbar_init(&a3full[b], kEpiWarps);
             tc::mbar_init(&a3empty[b], 1);
             tc::mbar_init(&pfull[b], 1);
             tc::mbar_init(&pempty[b], 4);
@@ -575,34 +601,26 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
 
     if (warp == 0) {
         // loader
-        int64_t n = 0;  // rows staged so far
-        const int g = lane & 3;
-        for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
-            const RingUnit w = ring_unit(p, u);
-            for (int j = -1; j <= w.nrows; ++j) {
-                const int s = (int)(n % kRing);
-                if (n >= kRing &&
-                    !__all_sync(0xffffffffu, tc::mbar_wait(&empty[s], (uint32_t)(((n / kRing) + 1) & 1), kWaitCycles))) {
-                    ok = false;
-                    break;
+        if (lane == 0) {
+            uint32_t n = 0;  // rows staged so far
+            for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+                const RingUnit w = ring_unit(p, u);
+                for (int j = -1; j <= w.nrows; ++j, ++n) {
+                    const uint32_t s = n & (kRing - 1);
+                    if (n >= kRing && !tc::mbar_wait(&empty[s], ((n / kRing) + 1) & 1, kWaitCycles)) {
+                        ok = false;
+                        break;
+                    }
+                    const int y = ring_row(p, w.c, w.r0 + j);
+                    tc::mbar_arrive_expect_tx(&full[s], kGroups * (kTileM + 2) * 16);
+                    uint8_t *dst = ring + s * kRowBytes;
+#pragma unroll
+                    for (int g = 0; g < kGroups; ++g)
+                        tc::tma_load_4d(dst + g * kRingPlane, &p.tmap[g], 0, w.x0, y, (int)w.c, &full[s]);
                 }
-                const int y = ring_row(p, w.c, w.r0 + j);
-                const uint8_t *src = reinterpret_cast<const uint8_t *>(p.a_in) + ((w.c * L + y) * (int64_t)L) * 64;
-                uint8_t *dst = ring + s * kRowBytes;
-                for (int e = lane >> 2; e < kTileM + 2; e += 8)
-                    tc::cp_async16(dst + g * kPlane + e * 16, src + (int64_t)wrap(w.x0 - 1 + e, L) * 64 + g * 16);
-                tc::cp_async_commit();
-                if (n >= kInFlight - 1) {
-                    tc::cp_async_wait<kInFlight - 1>();
-                    tc::fence_async_smem();
-                    tc::mbar_arrive(&full[(n - (kInFlight - 1)) % kRing]);
-                }
-                ++n;
             }
         }
-        tc::cp_async_wait<0>();
-        tc::fence_async_smem();
-        for (int64_t m = n > kInFlight - 1 ? n - (kInFlight - 1) : 0; m < n; ++m) tc::mbar_arrive(&full[m % kRing]);
+        __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_bf16_f32(kTileM, kCh);
@@ -617,7 +635,7 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
                 tc::fence_after_sync();
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const uint64_t ad = tc::smem_desc(a3_u32 + b * kRowBytes + 2 * h * kPlane, kPlane, 128);
+                    const uint64_t ad = tc::smem_desc(a3_u32 + b * kRowBytes + 2 * h * kRingPlane, kRingPlane, 128);
                     const uint64_t bd = tc::smem_desc(w4_u32 + 2 * h * kProjN * 16, kProjN * 16, 128);
                     tc::mma_bf16(tproj + (uint32_t)(b * kProjN), ad, bd, idesc_p, h > 0 ? 1u : 0u);
                 }
@@ -643,7 +661,7 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
                         const int k = st >> 1, h = st & 1, dy = k / 3 - 1, dx = k % 3 - 1;
                         const int slot = (int)((n0 + j + 1 + dy) % kRing);
                         const uint64_t ad =
-                            tc::smem_desc(ring_u32 + slot * kRowBytes + 2 * h * kPlane + (1 + dx) * 16, kPlane, 128);
+                            tc::smem_desc(ring_u32 + slot * kRowBytes + 2 * h * kRingPlane + (1 + dx) * 16, kRingPlane, 128);
                         const uint64_t bd = tc::smem_desc(b_u32 + (k * kGroups + 2 * h) * kCh * 16, kCh * 16, 128);
                         tc::mma_bf16(tmem + (uint32_t)(a * kCh), ad, bd, idesc, st > 0 ? 1u : 0u);
                     }
@@ -664,7 +682,7 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
         }
         __syncwarp();
     } else {
-        const int quad = warp & 3, m = quad * 32 + lane;
+        const int quad = warp & 3, half = (warp - 2) >> 2, m = quad * 32 + lane;
         // P of tile s, pixel q (one tile behind the accumulators)
         auto read_proj = [&](int64_t s, int64_t q) -> bool {
             const int b = (int)(s & 1);
@@ -690,29 +708,26 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
                     break;
                 }
                 tc::fence_after_sync();
-                float v[32];
-                const uint32_t ta = tmem + (uint32_t)(a * kCh) + ((uint32_t)(quad * 32) << 16);
-                tc::tmem_ld16(ta, *reinterpret_cast<float(*)[16]>(v));
-                tc::tmem_ld16(ta + 16, *reinterpret_cast<float(*)[16]>(v + 16));
+                float v[16];
+                tc::tmem_ld16(tmem + (uint32_t)(a * kCh + 16 * half) + ((uint32_t)(quad * 32) << 16), v);
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&acce[a]);
                 const int y = ring_row(p, w.c, w.r0 + j);
                 const int64_t q = (w.c * L + y) * (int64_t)L + w.x0 + m;
 #pragma unroll
-                for (int i = 0; i < kCh; ++i) v[i] += sBias[i];
+                for (int i = 0; i < 16; ++i) v[i] += sBias[16 * half + i];
                 if (p.z_out) {
-                    float4 *zo = reinterpret_cast<float4 *>(p.z_out + q * kCh);
+                    float4 *zo = reinterpret_cast<float4 *>(p.z_out + q * kCh + 16 * half);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) zo[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    for (int i = 0; i < 4; ++i) zo[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
                 }
-                uint32_t pk[16];
+                uint32_t pk[8];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) pk[i] = pack_bf16x2(gelu(v[2 * i]), gelu(v[2 * i + 1]));
+                for (int i = 0; i < 8; ++i) pk[i] = pack_bf16x2(gelu(v[2 * i]), gelu(v[2 * i + 1]));
                 if (p.a_out) {
-                    uint4 *ao = reinterpret_cast<uint4 *>(p.a_out + q * kCh);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) ao[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+                    store_act(p.a_out, L, w.c, y, w.x0 + m, 16 * half, make_uint4(pk[0], pk[1], pk[2], pk[3]));
+                    store_act(p.a_out, L, w.c, y, w.x0 + m, 16 * half + 8, make_uint4(pk[4], pk[5], pk[6], pk[7]));
                 }
                 if (PROJ) {
                     const int b = (int)(t & 1);
@@ -721,15 +736,13 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
                         ok = false;
                         break;
                     }
-                    uint8_t *dst = a3s + b * kRowBytes + m * 16;
-#pragma unroll
-                    for (int g = 0; g < kGroups; ++g)
-                        *reinterpret_cast<uint4 *>(dst + g * kPlane) =
-                            make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
+                    uint8_t *dst = a3s + b * kRowBytes + 2 * half * kRingPlane + m * 16;
+                    *reinterpret_cast<uint4 *>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    *reinterpret_cast<uint4 *>(dst + kRingPlane) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                     tc::fence_async_smem();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&a3full[b]);
-                    if (t >= 1 && !read_proj(t - 1, q_prev)) {
+                    if (half == 0 && t >= 1 && !read_proj(t - 1, q_prev)) {
                         ok = false;
                         break;
                     }
@@ -737,7 +750,7 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
                 }
             }
         }
-        if (PROJ && ok && t >= 1 && !read_proj(t - 1, q_prev)) ok = false;
+        if (PROJ && ok && half == 0 && t >= 1 && !read_proj(t - 1, q_prev)) ok = false;
     }
     if (!ok) atomicExch(&g_tc_error, 1);
     tc::fence_before_sync();
@@ -764,7 +777,8 @@ __global__ void __launch_bounds__(kThreads) l4_project_kernel(Band bd, const flo
         int yx;
         band_pixel(bd, pb, c, yx);
         const int64_t q = c * (int64_t)L * L + yx;
-        const uint4 *src = reinterpret_cast<const uint4 *>(a3 + q * kCh);
+        const int y = yx / L;
+        const uint4 *src = reinterpret_cast<const uint4 *>(a3 + apix(L, c, y, yx - y * L) * kCh);
         float acc[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
@@ -918,7 +932,7 @@ __device__ __forceinline__ void wgrad_stage(const Chains &ch, const __nv_bfloat1
         int y = y0 + ty - 1, x = x0 + tx - 1;
         y = y < 0 ? y + L : (y >= L ? y - L : y);
         x = x < 0 ? x + L : (x >= L ? x - L : x);
-        sa[e] = CIN == 1 ? spin_at(ch, c, y, x, -1) : __bfloat162float(a_prev[((c * L + y) * (int64_t)L + x) * CIN + i]);
+        sa[e] = CIN == 1 ? spin_at(ch, c, y, x, -1) : __bfloat162float(a_prev[apix(L, c, y, x) * CIN + i]);
     }
     for (int e = threadIdx.x; e < kTy * kTx * COUT; e += blockDim.x) {
         const int pix = e / COUT, o = e - pix * COUT;
@@ -1199,7 +1213,8 @@ NetWork net_layout(int64_t L, int64_t C, int train, char *base)
 {
     NetWork w;
     memset(&w, 0, sizeof(w));
-    const size_t pix = (size_t)C * L * L * kCh;
+    const size_t pix = (size_t)C * L * L * kCh;        // FP32 buffers
+    const size_t apx = (size_t)C * L * (L + 2) * kCh;  // activation buffers (halo columns)
     size_t o = 0;
     auto take = [&](size_t n) {
         char *p = base ? base + o : nullptr;
@@ -1208,15 +1223,15 @@ NetWork net_layout(int64_t L, int64_t C, int train, char *base)
     };
     if (train) {
         w.z1 = (float *)take(pix * 4); w.z2 = (float *)take(pix * 4); w.z3 = (float *)take(pix * 4);
-        w.a1 = (__nv_bfloat16 *)take(pix * 2); w.a2 = (__nv_bfloat16 *)take(pix * 2);
-        w.a3 = (__nv_bfloat16 *)take(pix * 2);
+        w.a1 = (__nv_bfloat16 *)take(apx * 2); w.a2 = (__nv_bfloat16 *)take(apx * 2);
+        w.a3 = (__nv_bfloat16 *)take(apx * 2);
         w.da = (float *)take(pix * 4); w.db = (float *)take(pix * 4);
         DeviceInfo info{152};
         device_info(&info);
         w.n_cta = (int64_t)info.sm_count * kWgradCtasPerSm;
         w.partial = (float *)take((size_t)w.n_cta * (kN2 + kCh) * sizeof(float));
     } else {
-        w.a1 = (__nv_bfloat16 *)take(pix * 2); w.a2 = (__nv_bfloat16 *)take(pix * 2);
+        w.a1 = (__nv_bfloat16 *)take(apx * 2); w.a2 = (__nv_bfloat16 *)take(apx * 2);
         w.a3 = w.a1;
     }
     w.P = (float *)take((size_t)C * L * L * 9 * sizeof(float));
@@ -1234,6 +1249,47 @@ constexpr int kBandRows[4] = {30, 28, 26, 3};  // a1, a2, a3 rows; logit block r
 constexpr int kBandLead[3] = {11, 10, 9};
 
 bool band_supported(int64_t L) { return L % kTileM == 0 && L >= 128; }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the library
+// does not link libcuda).
+EncodeTiledFn encode_tiled_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// The ring kernel's view of an activation buffer, one tensor map per channel
+// group g: (8 channels at 8g, L + 2 pixels of 64 bytes, L rows, C chains),
+// boxes of 8 x 130 x 1 x 1.
+bool encode_rows(CUtensorMap (&m)[kGroups], const __nv_bfloat16 *a, int L, int64_t C)
+{
+    EncodeTiledFn fn = encode_tiled_fn();
+    if (fn == nullptr) return false;
+    const cuuint64_t dims[4] = {8, (cuuint64_t)L + 2, (cuuint64_t)L, (cuuint64_t)C};
+    const cuuint64_t strides[3] = {(cuuint64_t)kCh * 2, (cuuint64_t)(L + 2) * kCh * 2,
+                                   (cuuint64_t)L * (L + 2) * kCh * 2};
+    const cuuint32_t box[4] = {8, kTileM + 2, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int g = 0; g < kGroups; ++g)
+        if (fn(&m[g], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)(a + 8 * g), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    return true;
+}
 
 int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, const float *params,
                    float *logits, const NetWork &w, int train, cudaStream_t s)
@@ -1267,6 +1323,7 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
         __nv_bfloat16 *outs[2] = {w.a2, train ? w.a3 : nullptr};
         for (int l = 0; l < 2; ++l) {
             RingConv p;
+            if (!encode_rows(p.tmap, ins[l], L, C)) return nfail(ISING_ECUDA, "cuTensorMapEncodeTiled failed");
             p.a_in = ins[l];
             p.a_out = outs[l];
             p.z_out = zs[l];

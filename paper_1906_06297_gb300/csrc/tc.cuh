@@ -95,6 +95,26 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Arrive on `bar` and raise its expected transaction count by `bytes` (the
+// bytes of the bulk copies that will complete on it).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Tiled bulk tensor copy (TMA) of one box of a 4-D tensor map into shared
+// memory (128-byte aligned destination), completing `bar`'s transactions.
+// tmap is the address of a CUtensorMap in the kernel's parameter space.
+__device__ __forceinline__ void tma_load_4d(void *smem_dst, const void *tmap, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // 16-byte asynchronous copy global -> shared (cached in L2 only), grouped by
 // commit_group and waited for by wait_group.
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
