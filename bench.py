@@ -53,13 +53,14 @@ def parse_args(argv=None):
     p.add_argument("--slabs", type=int, default=4, help="slabs on one GPU for the slab leg / workload")
     p.add_argument("--no-binder", action="store_true", help="skip the Binder-crossing leg")
     p.add_argument("--binder-sweeps", type=int, default=100000)
-    p.add_argument("--workload", choices=["sweep", "pt", "learned", "slabs", "binder"], default="sweep",
+    p.add_argument("--workload", choices=["sweep", "pt", "learned", "network", "slabs", "binder"], default="sweep",
                    help="sweep: the 65536^2 lattice (default); pt / learned: only that leg")
     p.add_argument("--no-learned", action="store_true", help="skip the learned block-proposal leg")
     p.add_argument("--learned-steps", type=int, default=1000, help="training steps of the proposal network")
     p.add_argument("--learned-cycles", type=int, default=400, help="measured sweep + move cycles")
     p.add_argument("--learned-configs", type=int, default=100000, help="training configurations")
     p.add_argument("--learned-chains", type=int, default=1024, help="chains of the measured learned cycles")
+    p.add_argument("--net-reps", type=int, default=10, help="timed network evaluations (--workload network)")
     return p.parse_args(argv)
 
 
@@ -628,7 +629,7 @@ def run_pt_only(args, world, rank, local):
             "pt_batch": pt}
 
 
-def time_network(ising, torch, L, C, params, beta, seed, device, stream, reps=10):
+def time_network(ising, torch, L, C, params, beta, seed, device, stream, reps=10, warmup=3):
     """CUDA-event times of one network evaluation of C chains of side L: the
     full forward (the state before a move) and the flipped-band forward (the
     proposed state), with the tensor-core FLOPs of the two 32 -> 32 layers."""
@@ -646,7 +647,7 @@ def time_network(ising, torch, L, C, params, beta, seed, device, stream, reps=10
                      ("flipped_band_forward", lambda: ising.ising_net_forward_flipped(
                          L, C, mv.black, mv.white, flips, params, mv.lx, mv.lxp, mv.work, stream))):
         with torch.cuda.stream(stream):
-            for _ in range(3):
+            for _ in range(warmup):
                 fn()
             torch.cuda.synchronize()
             e0.record(stream)
@@ -804,6 +805,24 @@ def main(argv=None):
         bl = run_binder_leg(args, device, torch.cuda.Stream(device=device))
         res = {"metric": METRIC, "value": bl["flips_per_ns"], "unit": UNIT, "impl": "ours",
                "config": {"workload": bl["workload"]}, "binder": bl}
+    elif args.workload == "network":
+        # the network's forward passes alone (random weights): full and flipped band
+        import numpy as np
+        import torch
+
+        import paper_1906_06297_gb300 as ising
+
+        ising.build()
+        torch.cuda.set_device(local)
+        device = torch.device("cuda", local)
+        rng = np.random.default_rng(args.seed)
+        params = torch.from_numpy(rng.normal(0.0, 0.1, ising.ising_net_param_count()).astype(np.float32)).to(device)
+        C = args.learned_chains
+        net = time_network(ising, torch, 128, C, params, BETA_C_CONFIG, args.seed, device,
+                           torch.cuda.Stream(device=device), reps=args.net_reps, warmup=min(3, args.warmup))
+        res = {"metric": "network forward pixels/s", "value": round(C * 128 * 128 / net["full_forward_ms"] / 1e6, 3),
+               "unit": "Gpixel/s", "impl": "ours", "higher_is_better": True,
+               "config": {"workload": f"{C} chains of 128x128, random bfloat16 weights"}, "network": net}
     elif args.workload == "learned":
         import torch
 
