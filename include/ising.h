@@ -347,6 +347,16 @@ ISING_API int ising_net_forward_flipped(int64_t L, int64_t C, const void *black_
  * last check (each such wait is bounded at about 2 s), else ISING_OK. */
 ISING_API int ising_net_check(ising_stream_t stream);
 
+/* Failure-path self-test of the tensor-core kernels' bounded waits: runs one
+ * forward (L a multiple of 128) in which the first 32-channel layer never
+ * signals the completion of its first accumulator.  The waits that depend on
+ * it give up after about 2 s, every CTA frees its tensor memory and returns,
+ * and the next ising_net_check reports ISING_ETIMEOUT; the device stays usable.
+ * logits_dev receives meaningless values.  Not part of the method. */
+ISING_API int ising_net_wait_selftest(int64_t L, int64_t C, const void *black_dev, const void *white_dev,
+                                     const float *params_dev, float *logits_dev, void *work_dev, size_t work_bytes,
+                                     ising_stream_t stream);
+
 /* grad_dev = d(sum dlogits * logits)/d(params) for the last training forward
  * on the same chains and parameters (straight-through the bfloat16 rounding). */
 ISING_API int ising_net_backward(int64_t L, int64_t C, const void *black_dev, const void *white_dev,

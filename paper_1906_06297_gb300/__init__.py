@@ -116,6 +116,7 @@ def _load():
             "ising_net_forward": [i64, i64, P, P, P, P, P, P, ctypes.c_size_t, i32, P],
             "ising_net_forward_flipped": [i64, i64, P, P, P, P, P, P, P, ctypes.c_size_t, P],
             "ising_net_check": [P],
+            "ising_net_wait_selftest": [i64, i64, P, P, P, P, P, ctypes.c_size_t, P],
             "ising_net_backward": [i64, i64, P, P, P, P, P, P, ctypes.c_size_t, P],
             "ising_net_targets_loss": [i64, i64, P, P, dbl, P, P, P, P, P],
             "ising_net_adam": [P, P, P, P, i64, ctypes.c_float, P],
@@ -590,6 +591,12 @@ def ising_net_forward_flipped(L, C, black, white, flip_block, params, logits_x, 
 
 def ising_net_check(stream=None):
     _check(_load().ising_net_check(_stream(stream)), "ising_net_check")
+
+
+def ising_net_wait_selftest(L, C, black, white, params, logits, work, stream=None):
+    _check(_load().ising_net_wait_selftest(L, C, _addr(black), _addr(white), _addr(params), _addr(logits),
+                                           _addr(work), work.numel() * work.element_size(), _stream(stream)),
+           "ising_net_wait_selftest")
 
 
 def ising_net_backward(L, C, black, white, params, dlogits, grad, work, stream=None):

@@ -505,6 +505,7 @@ struct RingConv {
     int segs;           // L / 128
     int units_per_col;  // ceil(bd.rows / kUnitRows)
     int64_t units;      // C segs units_per_col
+    int withhold;       // self-test: never signal the first accumulator, so its wait runs out
 };
 
 struct RingUnit {
@@ -619,6 +620,11 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
                         tc::tma_load_4d(dst + g * kRingPlane, &p.tmap[g], 0, w.x0, y, (int)w.c, &full[s]);
                 }
             }
+            // on a failure no copy may still be writing into shared memory when the CTA exits:
+            // wait (bounded) for the last rows issued
+            if (!ok)
+                for (uint32_t m = n > kRing ? n - kRing : 0; m < n; ++m)
+                    tc::mbar_wait(&full[m & (kRing - 1)], (m / kRing) & 1, kWaitCycles);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -665,7 +671,7 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
                         const uint64_t bd = tc::smem_desc(b_u32 + (k * kGroups + 2 * h) * kCh * 16, kCh * 16, 128);
                         tc::mma_bf16(tmem + (uint32_t)(a * kCh), ad, bd, idesc, st > 0 ? 1u : 0u);
                     }
-                    tc::mma_commit(&accf[a]);
+                    if (!(p.withhold && t == 0)) tc::mma_commit(&accf[a]);
                     tc::mma_commit(&empty[(n0 + j) % kRing]);
                     if (j == w.nrows - 1) {
                         tc::mma_commit(&empty[(n0 + j + 1) % kRing]);
@@ -1292,7 +1298,7 @@ bool encode_rows(CUtensorMap (&m)[kGroups], const __nv_bfloat16 *a, int L, int64
 }
 
 int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, const float *params,
-                   float *logits, const NetWork &w, int train, cudaStream_t s)
+                   float *logits, const NetWork &w, int train, cudaStream_t s, bool withhold = false)
 {
     const int L = ch.L;
     DeviceInfo info{152};
@@ -1335,6 +1341,7 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
             p.segs = L / kTileM;
             p.units_per_col = (bd[l + 1].rows + kUnitRows - 1) / kUnitRows;
             p.units = C * p.segs * p.units_per_col;
+            p.withhold = withhold && l == 0;
             const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.units, 2 * info.sm_count));
             if (l == 0)
                 conv32_ring_kernel<false><<<grid, kRingThreads, kRingSmem, s>>>(p);
@@ -1429,6 +1436,25 @@ ISING_API int ising_net_forward_flipped(int64_t L, int64_t C, const void *black_
     cudaError_t e = cudaMemcpyAsync(logits_dev, logits_x_dev, lbytes, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return nfail(ISING_ECUDA, cudaGetErrorString(e));
     return launch_forward(ch, C, flip_block_dev, true, params_dev, logits_dev, w, 0, s);
+}
+
+ISING_API int ising_net_wait_selftest(int64_t L, int64_t C, const void *black_dev, const void *white_dev,
+                                     const float *params_dev, float *logits_dev, void *work_dev, size_t work_bytes,
+                                     ising_stream_t stream)
+{
+    int rc = check_chains(L, C);
+    if (rc) return rc;
+    if (L % kTileM != 0) return nfail(ISING_EINVAL, "the self-test runs the row-ring kernel: L must be a multiple of 128");
+    NetWork w = net_layout(L, C, 0, (char *)work_dev);
+    if (work_dev == nullptr || work_bytes < w.bytes) return nfail(ISING_EINVAL, "work buffer too small");
+    const size_t plane = (size_t)C * L * L / 32 * 8;
+    if (check_device_range(black_dev, plane, "black") || check_device_range(white_dev, plane, "white") ||
+        check_device_range(params_dev, kParams * 4, "params") ||
+        check_device_range(logits_dev, (size_t)C * (L / 8) * (L / 8) * 4, "logits") ||
+        check_device_range(work_dev, w.bytes, "work"))
+        return nfail(ISING_EINVAL, "planes, params, logits and work must be device memory of their sizes");
+    Chains ch{(const uint64_t *)black_dev, (const uint64_t *)white_dev, (int)L, (int)(L / 32)};
+    return launch_forward(ch, C, nullptr, false, params_dev, logits_dev, w, 0, (cudaStream_t)stream, true);
 }
 
 ISING_API int ising_net_check(ising_stream_t stream)

@@ -131,6 +131,28 @@ def test_flipped_band_pass_rejects_bad_arguments():
                                         mv.work[:1024])
 
 
+def test_bounded_wait_reports_timeout_and_device_stays_usable():
+    """The first conv layer withholds one accumulator signal: its waits give up
+    (about 2 s), ising_net_check reports ISING_ETIMEOUT, and a normal forward
+    afterwards gives the same logits as before."""
+    L, C = 128, 2
+    mv = chains(L, C, 7)
+    params = torch.from_numpy(theta32(3)).cuda()
+    want = torch.zeros((C, (L // 8) ** 2), dtype=torch.float32, device="cuda")
+    ising.ising_net_forward(L, C, mv.black, mv.white, None, params, want, mv.work)
+    ising.ising_net_check()
+    junk = torch.zeros_like(want)
+    ising.ising_net_wait_selftest(L, C, mv.black, mv.white, params, junk, mv.work)
+    with pytest.raises(ising.IsingError) as e:
+        ising.ising_net_check()
+    assert e.value.status == ising.ISING_ETIMEOUT
+    ising.ising_net_check()  # the flag was cleared
+    again = torch.zeros_like(want)
+    ising.ising_net_forward(L, C, mv.black, mv.white, None, params, again, mv.work)
+    ising.ising_net_check()
+    assert torch.equal(again, want)
+
+
 @pytest.mark.parametrize("L,C", [(32, 2), (128, 2)])
 def test_backward_and_loss_match_oracle(L, C):
     mv = chains(L, C, 5)
