@@ -1,7 +1,8 @@
 // tc.cuh -- inline-PTX wrappers for the fifth-generation tensor cores of
 // sm_100-family GPUs (tcgen05): tensor-memory (TMEM) allocation, the
 // single-thread MMA issue with shared-memory operand descriptors, completion
-// through an mbarrier, and the warp-wide TMEM loads of the epilogue.
+// through an mbarrier, the warp-wide TMEM loads of the epilogue, and the
+// tensor copies (TMA) that stage operands in shared memory.
 //
 // Operand layout used here: K-major, no swizzle.  A "core matrix" is 8 rows x
 // 16 bytes (8 bf16 along K) stored as 128 contiguous bytes, row r at +16 r.
@@ -113,22 +114,6 @@ __device__ __forceinline__ void tma_load_4d(void *smem_dst, const void *tmap, in
         "%5}], [%6];" ::"r"(smem_u32(smem_dst)),
         "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
         : "memory");
-}
-
-// 16-byte asynchronous copy global -> shared (cached in L2 only), grouped by
-// commit_group and waited for by wait_group.
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gmem_src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-// Waits until at most N of this thread's committed groups are still pending.
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
