@@ -192,18 +192,52 @@ __device__ __forceinline__ void store_act(__nv_bfloat16 *a, int L, int64_t c, in
     if (x == L - 1) *reinterpret_cast<uint4 *>(a + apix(L, c, y, -1) * kCh + off) = v;
 }
 
-// Layer 1 (1 -> 32 channels, from the spins): thread per pixel of the band;
-// blockIdx.y walks the chains and blockIdx.x the 128-pixel tiles of a chain's
-// band, so all index arithmetic is 32-bit.  Writes a1 (bfloat16) and, when
-// z_out != nullptr, z1 (FP32).
+// Layer 1 (1 -> 32 channels) sees only the 3 x 3 spins around a pixel, so its
+// output is a function of a 9-bit pattern (bit k set when the spin at tap k =
+// 3 (dy + 1) + (dx + 1) is +1).  l1_table_kernel evaluates z1 and
+// bf16(gelu(z1)) for all 512 patterns, with the arithmetic a direct evaluation
+// would use (bias first, then the taps in order by fmaf); l1_kernel then reads
+// each pixel's pattern and copies its row of the table.
+constexpr int kPatterns = 512;
 constexpr int kL1Threads = 128;
 
-__global__ void __launch_bounds__(kL1Threads, 6) l1_kernel(Chains ch, Band bd, const int32_t *flip, const float *params,
-                                                        float *z_out, __nv_bfloat16 *a_out)
+__global__ void l1_table_kernel(const float *params, float *tz, __nv_bfloat16 *ta)
 {
-    __shared__ float W[kN1], Bs[kCh];
-    for (int i = threadIdx.x; i < kN1; i += blockDim.x) W[i] = bf16r(params[kOffW1 + i]);
-    for (int i = threadIdx.x; i < kCh; i += blockDim.x) Bs[i] = bf16r(params[kOffB1 + i]);
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;  // pattern * 32 + output channel
+    if (e >= kPatterns * kCh) return;
+    const int pat = e / kCh, o = e - pat * kCh;
+    float v = bf16r(params[kOffB1 + o]);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v = fmaf(bf16r(params[kOffW1 + o * 9 + k]), ((pat >> k) & 1) ? 1.0f : -1.0f, v);
+    tz[e] = v;
+    ta[e] = __float2bfloat16_rn(gelu(v));
+}
+
+// 1 if the spin at row y, column x of chain c is +1 (block `flip`, or -1 for
+// none, negated).
+__device__ __forceinline__ uint32_t spin_up(const Chains &ch, int64_t c, int y, int x, int flip)
+{
+    const int j = x >> 1;
+    const uint64_t *plane = ((y + x) & 1) ? ch.white : ch.black;
+    uint32_t u = (uint32_t)(plane[c * (int64_t)ch.L * ch.wpr + (int64_t)y * ch.wpr + (j >> 4)] >> (4 * (j & 15))) & 1u;
+    if (flip >= 0) {
+        const int nb = ch.L / kBlk;
+        const int by = flip / nb, bx = flip - by * nb;
+        if ((y >> 3) == by && (x >> 3) == bx) u ^= 1u;
+    }
+    return u;
+}
+
+// Thread per pixel of the band; blockIdx.y walks the chains and blockIdx.x
+// the 128-pixel tiles of a chain's band, so all index arithmetic is 32-bit.
+// Writes a1 (bfloat16, from the table in shared memory) and, when z_out !=
+// nullptr, z1 (FP32).
+__global__ void __launch_bounds__(kL1Threads) l1_kernel(Chains ch, Band bd, const int32_t *flip,
+                                                        const __nv_bfloat16 *ta, const float *tz, float *z_out,
+                                                        __nv_bfloat16 *a_out)
+{
+    __shared__ uint4 T[kPatterns * kCh * 2 / 16];  // ta, 32 KiB
+    for (int i = threadIdx.x; i < kPatterns * kCh * 2 / 16; i += blockDim.x) T[i] = reinterpret_cast<const uint4 *>(ta)[i];
     __syncthreads();
     const int L = ch.L;
     const int per = bd.rows * L;  // band pixels per chain, a multiple of 128
@@ -214,29 +248,17 @@ __global__ void __launch_bounds__(kL1Threads, 6) l1_kernel(Chains ch, Band bd, c
             const int ry = r / L, x = r - ry * L;
             int y = row0 + ry;
             y = y >= L ? y - L : y;
-            float sp[9];
+            uint32_t pat = 0;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) sp[k] = spin_at(ch, c, wrap(y + k / 3 - 1, L), wrap(x + k % 3 - 1, L), fb);
-            const int64_t q = (c * L + y) * (int64_t)L + x;
-            float4 *zo = z_out ? reinterpret_cast<float4 *>(z_out + q * kCh) : nullptr;
-#pragma unroll 1
-            for (int g = 0; g < kCh / 8; ++g) {
-                float z[8];
+            for (int k = 0; k < 9; ++k) pat |= spin_up(ch, c, wrap(y + k / 3 - 1, L), wrap(x + k % 3 - 1, L), fb) << k;
+            const uint4 *row = T + pat * 4;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int o = 8 * g + j;
-                    float v = Bs[o];
+            for (int g = 0; g < 4; ++g) store_act(a_out, L, c, y, x, 8 * g, row[g]);
+            if (z_out) {
+                const float4 *zr = reinterpret_cast<const float4 *>(tz + pat * kCh);
+                float4 *zo = reinterpret_cast<float4 *>(z_out + ((c * L + y) * (int64_t)L + x) * kCh);
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) v = fmaf(W[o * 9 + k], sp[k], v);
-                    z[j] = v;
-                }
-                if (zo) {
-                    zo[2 * g] = make_float4(z[0], z[1], z[2], z[3]);
-                    zo[2 * g + 1] = make_float4(z[4], z[5], z[6], z[7]);
-                }
-                store_act(a_out, L, c, y, x, 8 * g,
-                          make_uint4(pack_bf16x2(gelu(z[0]), gelu(z[1])), pack_bf16x2(gelu(z[2]), gelu(z[3])),
-                                     pack_bf16x2(gelu(z[4]), gelu(z[5])), pack_bf16x2(gelu(z[6]), gelu(z[7]))));
+                for (int i = 0; i < 8; ++i) zo[i] = __ldg(zr + i);
             }
         }
     }
@@ -1207,8 +1229,8 @@ int check_chains(int64_t L, int64_t C)
 // a1 and a2 (bfloat16; where a3 is written at all it reuses a1's buffer).
 // Both end with the 9 FP32 planes P of layer 4's tap projections.
 struct NetWork {
-    float *z1, *z2, *z3, *da, *db, *partial, *P;
-    __nv_bfloat16 *a1, *a2, *a3;
+    float *z1, *z2, *z3, *da, *db, *partial, *P, *tz;
+    __nv_bfloat16 *a1, *a2, *a3, *ta;
     int64_t n_cta;
     size_t bytes;
 };
@@ -1241,6 +1263,8 @@ NetWork net_layout(int64_t L, int64_t C, int train, char *base)
         w.a3 = w.a1;
     }
     w.P = (float *)take((size_t)C * L * L * 9 * sizeof(float));
+    w.tz = (float *)take((size_t)kPatterns * kCh * sizeof(float));
+    w.ta = (__nv_bfloat16 *)take((size_t)kPatterns * kCh * 2);
     w.bytes = o;
     return w;
 }
@@ -1317,7 +1341,8 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
         const int64_t want = (int64_t)info.sm_count * 16;
         const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, want));
         const unsigned gy = (unsigned)std::max<int64_t>(1, std::min<int64_t>({C, 65535, (want + gx - 1) / gx}));
-        l1_kernel<<<dim3(gx, gy), kL1Threads, 0, s>>>(ch, bd[0], flip, params, train ? w.z1 : nullptr, w.a1);
+        l1_table_kernel<<<kPatterns * kCh / 256, 256, 0, s>>>(params, w.tz, w.ta);
+        l1_kernel<<<dim3(gx, gy), kL1Threads, 0, s>>>(ch, bd[0], flip, w.ta, w.tz, train ? w.z1 : nullptr, w.a1);
     }
     const int off[2][2] = {{kOffW2, kOffB2}, {kOffW3, kOffB3}};
     const __nv_bfloat16 *ins[2] = {w.a1, w.a2};
