@@ -20,9 +20,15 @@
 // pixels: column 0 repeats pixel L - 1 and column L + 1 pixel 0 (the periodic
 // halo, written by the producer), so that one rectangular copy fetches a row
 // segment with both neighbours.  The pre-activations z kept for training and
-// the gradients are NHWC FP32 without halo.  The two 32 -> 32 layers
-// run on the tensor cores (tcgen05, see conv32_tc_kernel); every reduction has
-// a fixed order, so a forward pass is a deterministic function of the state.
+// the gradients are NHWC FP32 without halo.
+//
+// Forward kernels: layer 1 by table lookup (l1_table_kernel, l1_kernel); the
+// two 32 -> 32 layers on the tensor cores (tcgen05; conv32_ring_kernel for L
+// a multiple of 128, conv32_tc_kernel otherwise), the second one also
+// contracting layer 4's input channels (P, the 9 tap projections); the tap
+// sums and block means (pool_kernel).  Every reduction has a fixed order, so
+// a forward pass is a deterministic function of the state.  Backward kernels:
+// FP32 on the CUDA cores, straight through the bfloat16 roundings.
 //
 // Move.  Block b is drawn by inverse CDF of q_x (purpose-3 draw, site 0, in
 // the chain's stream) or uniformly; x' = x with block b flipped; the flip is
