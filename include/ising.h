@@ -113,7 +113,11 @@ ISING_API int ising_sweep(const ising_lattice_t *lat, double beta, int64_t n_swe
  * caller's device lattice `dev`, runs the sweeps, and copies the planes and
  * the trace (if trace_host is not NULL; trace_dev is then required as device
  * staging of n_sweeps x 2 int64) back.  Pinned host memory makes the copies
- * asynchronous; the call does not synchronise the stream. */
+ * asynchronous; the call does not synchronise the stream.  One sweep of an
+ * MSC4 lattice runs in row bands on two more streams of the library's own so
+ * that the copies overlap the half-sweeps; the work is still ordered on
+ * `stream` (it starts after the work queued on it and the stream waits for
+ * all of it), and the result is that of ising_sweep. */
 ISING_API int ising_sweep_host(const ising_lattice_t *dev, void *black_host, void *white_host, double beta,
                                int64_t n_sweeps, uint64_t seed, uint64_t sweep_offset, int64_t *trace_dev,
                                int64_t *trace_host, ising_stream_t stream);

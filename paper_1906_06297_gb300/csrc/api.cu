@@ -9,6 +9,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -43,6 +44,7 @@ int cuda_fail(cudaError_t e, const char *what)
 struct DeviceCache {
     std::mutex mu;
     int sm_count[64] = {};
+    cudaStream_t aux[64][2] = {};  // compute and copy-out streams of ising_sweep_host, made on first use
 };
 DeviceCache g_dev;
 
@@ -207,6 +209,57 @@ int check_slab_set(const ising_slab_t *slabs, int32_t n)
                     if (pa[i] < pb[j] + nb && pb[j] < pa[i] + na)
                         return fail(ISING_EINVAL, "planes of slabs %d and %d overlap", (int)a, (int)b);
         }
+    return ISING_OK;
+}
+
+// Half-sweep of rows row0 .. row0 + rows - 1 of a periodic MSC4 lattice, in
+// place: local row r is global row row0 + r; the source walk reaches global
+// rows row0 - 1 .. row0 + rows + 1 (mod L), so the row above local row 0 is
+// local L - 1 for the first band and local -1 otherwise, and global row L
+// (local L - row0) continues at global row 0 (local -row0).  Keys, thresholds
+// and observables are those of the whole-lattice half-sweep restricted to the
+// band, so the bands of a partition give the whole-lattice result bit for bit.
+int band_half_sweep_impl(const ising_lattice_t *lat, const Accept &acc, const RoundKeys &rk, int colour, uint64_t t,
+                         int64_t row0, int64_t rows, int64_t *obs, cudaStream_t s)
+{
+    const int64_t stride = lat->row_stride_bytes / 8;
+    Msc4SweepParams p;
+    p.tgt = (uint64_t *)(colour == 0 ? lat->black : lat->white) + row0 * stride;
+    p.src = (const uint64_t *)(colour == 0 ? lat->white : lat->black) + row0 * stride;
+    p.L = lat->L;
+    p.rows = rows;
+    p.row0 = row0;
+    p.wrap_row = lat->L - row0;
+    p.wrap_to = -row0;
+    p.first_up = row0 == 0 ? lat->L - 1 : -1;
+    p.wpr = lat->L / 32;
+    p.stride = stride;
+    p.qrow = lat->L / 8;
+    p.total = ((p.wpr + 63) / 64) * rows;
+    p.c2 = (uint32_t)t;
+    p.c3 = counter_word3(colour, kPurposeMetropolis, t);
+    p.acc = acc;
+    p.rk = rk;
+    p.obs = (long long *)obs;
+    cudaError_t e = msc4_half_sweep(p, colour, s);
+    return e == cudaSuccess ? ISING_OK : cuda_fail(e, "band half-sweep launch");
+}
+
+// The compute and copy-out streams of the banded host path, per device.
+int aux_streams(cudaStream_t *cmp, cudaStream_t *out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(ISING_ECUDA, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_dev.mu);
+    for (int i = 0; i < 2; ++i)
+        if (g_dev.aux[dev][i] == nullptr) {
+            e = cudaStreamCreateWithFlags(&g_dev.aux[dev][i], cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(e, "stream create");
+        }
+    *cmp = g_dev.aux[dev][0];
+    *out = g_dev.aux[dev][1];
     return ISING_OK;
 }
 
@@ -512,6 +565,106 @@ ISING_API int ising_slab_sweep(const ising_slab_t *slabs, int32_t n, double beta
     return ISING_OK;
 }
 
+namespace {
+
+// One sweep of an MSC4 lattice held in host memory, in K row bands so that
+// the copies overlap the half-sweeps and each other.  Stream `s` copies the
+// bands in (the last band first, then 0 .. K-2), the compute stream runs
+// black band 0, black 1, then black k+1 before white k for k = 1 .. K-2, then
+// white K-1 and white 0, and the copy-out stream returns band k as soon as
+// white k is done.  Black band k needs the white rows next to it unchanged
+// (bands k-1 and k+1 are whited only after black k+1 resp. at the end: white
+// 0 comes last because black K-1 reads white row 0), white band k needs black
+// bands k-1 .. k+1 done; events carry these orders across the streams, and
+// `s` finally waits for the copy-out stream.
+int sweep_host_banded(const ising_lattice_t *dev, char *host[2], size_t row, const Accept &acc, const RoundKeys &rk,
+                      uint64_t t, int64_t *trace_dev, int64_t *trace_host, cudaStream_t s)
+{
+    const int64_t L = dev->L;
+    const int K = (int)std::min<int64_t>(16, L / 8);
+    const int64_t per = (L + K - 1) / K;
+    int64_t b0[16], br[16];
+    for (int k = 0; k < K; ++k) {
+        b0[k] = k * per;
+        br[k] = std::min<int64_t>(per, L - b0[k]);
+    }
+    cudaStream_t cmp, out;
+    int rc = aux_streams(&cmp, &out);
+    if (rc) return rc;
+    cudaEvent_t start, end, ev_in[16], ev_w[16];
+    cudaEvent_t *all[2] = {&start, &end};
+    auto make = [](cudaEvent_t *e) { return cudaEventCreateWithFlags(e, cudaEventDisableTiming); };
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = make(all[i]);
+    for (int k = 0; k < K && e == cudaSuccess; ++k) {
+        e = make(&ev_in[k]);
+        if (e == cudaSuccess) e = make(&ev_w[k]);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "event create");
+    void *devp[2] = {dev->black, dev->white};
+    const size_t pitch = (size_t)dev->row_stride_bytes;
+    auto copy = [&](int k, bool in, cudaStream_t st) {
+        cudaError_t r = cudaSuccess;
+        for (int c = 0; c < 2 && r == cudaSuccess; ++c) {
+            char *d = (char *)devp[c] + b0[k] * pitch;
+            char *h = host[c] + b0[k] * row;
+            r = in ? cudaMemcpy2DAsync(d, pitch, h, row, row, (size_t)br[k], cudaMemcpyHostToDevice, st)
+                   : cudaMemcpy2DAsync(h, row, d, pitch, row, (size_t)br[k], cudaMemcpyDeviceToHost, st);
+        }
+        return r;
+    };
+    e = cudaEventRecord(start, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cmp, start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(out, start, 0);
+    for (int i = 0; i < K && e == cudaSuccess; ++i) {
+        const int k = (i + K - 1) % K;  // K-1, 0, 1, .., K-2
+        e = copy(k, true, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in[k], s);
+    }
+    if (e == cudaSuccess && trace_dev) e = cudaMemsetAsync(trace_dev, 0, 2 * sizeof(int64_t), cmp);
+    if (e != cudaSuccess) return cuda_fail(e, "host sweep: copy in");
+    auto black = [&](int k) {
+        for (int d = -1; d <= 1; ++d) {
+            cudaError_t r = cudaStreamWaitEvent(cmp, ev_in[(k + d + K) % K], 0);
+            if (r != cudaSuccess) return cuda_fail(r, "host sweep: wait");
+        }
+        return band_half_sweep_impl(dev, acc, rk, 0, t, b0[k], br[k], nullptr, cmp);
+    };
+    auto white = [&](int k) {
+        int r = band_half_sweep_impl(dev, acc, rk, 1, t, b0[k], br[k], trace_dev, cmp);
+        if (r) return r;
+        cudaError_t x = cudaEventRecord(ev_w[k], cmp);
+        return x == cudaSuccess ? ISING_OK : cuda_fail(x, "host sweep: event");
+    };
+    rc = black(0);
+    if (!rc) rc = black(1);
+    for (int k = 2; k < K && !rc; ++k) {
+        rc = black(k);
+        if (!rc) rc = white(k - 1);
+    }
+    if (!rc) rc = white(K - 1);
+    if (!rc) rc = white(0);
+    if (rc) return rc;
+    for (int i = 0; i < K && e == cudaSuccess; ++i) {
+        const int k = (i + 1) % K;  // 1, .., K-1, 0
+        e = cudaStreamWaitEvent(out, ev_w[k], 0);
+        if (e == cudaSuccess) e = copy(k, false, out);
+    }
+    if (e == cudaSuccess && trace_host != nullptr)
+        e = cudaMemcpyAsync(trace_host, trace_dev, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, out);
+    if (e == cudaSuccess) e = cudaEventRecord(end, out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, end, 0);
+    cudaEventDestroy(start);
+    cudaEventDestroy(end);
+    for (int k = 0; k < K; ++k) {
+        cudaEventDestroy(ev_in[k]);
+        cudaEventDestroy(ev_w[k]);
+    }
+    return e == cudaSuccess ? ISING_OK : cuda_fail(e, "host sweep: copy out");
+}
+
+}  // namespace
+
 ISING_API int ising_sweep_host(const ising_lattice_t *dev, void *black_host, void *white_host, double beta,
                                int64_t n_sweeps, uint64_t seed, uint64_t sweep_offset, int64_t *trace_dev,
                                int64_t *trace_host, ising_stream_t stream)
@@ -524,6 +677,18 @@ ISING_API int ising_sweep_host(const ising_lattice_t *dev, void *black_host, voi
     size_t row = 0;
     row_bytes_of(dev->L, dev->layout, &row);
     cudaStream_t s = (cudaStream_t)stream;
+    if (n_sweeps == 1 && dev->layout == ISING_MSC4) {
+        Accept acc;
+        uint64_t T[5];
+        rc = build_accept(beta, &acc, T);
+        if (rc) return rc;
+        if (trace_dev != nullptr) {
+            rc = check_device_range(trace_dev, 2 * sizeof(int64_t), "trace");
+            if (rc) return rc;
+        }
+        char *host[2] = {(char *)black_host, (char *)white_host};
+        return sweep_host_banded(dev, host, row, acc, make_round_keys(seed), sweep_offset, trace_dev, trace_host, s);
+    }
     void *host[2] = {black_host, white_host};
     void *devp[2] = {dev->black, dev->white};
     for (int c = 0; c < 2; ++c) {

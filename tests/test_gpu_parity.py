@@ -241,6 +241,33 @@ def test_host_buffer_entry_point():
     np.testing.assert_array_equal(tr_host.numpy(), tr_o)
 
 
+@pytest.mark.parametrize("L,beta,stride", [(64, 0.4406868, None), (192, 0.3, None), (256, 0.0, None),
+                                           (640, 50.0, None), (2112, 0.4406868, 2112 // 4 + 64),
+                                           (4224, 0.6, None)])
+def test_host_buffer_single_sweep_in_bands(L, beta, stride):
+    """One sweep through host memory runs in row bands that overlap the copies
+    (8 to 16 bands, ragged, padded device rows): each step of 3 sweeps equals
+    the oracle bit for bit, planes and trace, and the host planes feed the
+    next call."""
+    seed, n = 9, 3
+    init = ising.Lattice(L, "msc4")
+    ising.ising_init_lattice(init, ising.ISING_INIT_RANDOM, seed)
+    torch.cuda.synchronize()
+    hb = init.black.cpu().pin_memory()
+    hw = init.white.cpu().pin_memory()
+    dev = ising.Lattice(L, "msc4", row_stride_bytes=stride)
+    tr_dev = torch.zeros((1, 2), dtype=torch.int64, device="cuda")
+    tr_host = torch.zeros((1, 2), dtype=torch.int64).pin_memory()
+    s = oracle.init(L, oracle.MODE_RANDOM, seed)
+    for k in range(n):
+        ising.ising_sweep_host(dev, hb.data_ptr(), hw.data_ptr(), beta, 1, seed, k, tr_dev, tr_host.data_ptr())
+        torch.cuda.synchronize()
+        tr_o = oracle.run(s, beta, 1, seed, off=k)
+        got = oracle.from_planes_msc4(L, hb.numpy().view(np.uint64), hw.numpy().view(np.uint64))
+        np.testing.assert_array_equal(got, s)
+        np.testing.assert_array_equal(tr_host.numpy(), tr_o)
+
+
 def test_undersized_buffers_are_rejected():
     """The library checks each plane against the extent of its CUDA allocation
     (the caching allocator's segment, so only overruns past the segment can be
