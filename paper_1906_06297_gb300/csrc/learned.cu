@@ -1136,72 +1136,134 @@ __device__ __forceinline__ uint32_t move_draw(const RoundKeys &rk, uint32_t stre
     return w == 0 ? u.x : w == 1 ? u.y : w == 2 ? u.z : u.w;
 }
 
-// log of the softmax normaliser, summed in block order in FP64
-__device__ double log_norm(const float *l, int nb)
+// The move kernels run one warp per chain.  FP64 arithmetic is slow on this
+// GPU, so the lanes compute the exponentials of a chunk of 256 blocks in
+// parallel into shared memory and lane 0 adds them up in block order: every
+// FP64 operation, and so every decision, is the one of a sequential loop.
+constexpr int kMoveWarps = 4;   // chains per 128-thread CTA
+constexpr int kChunk = 256;     // blocks per chunk
+
+__device__ __forceinline__ double warp_max_logit(const float *l, int nb)
 {
-    double m = l[0];
-    for (int b = 1; b < nb; ++b) m = fmax(m, (double)l[b]);
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += exp((double)l[b] - m);
-    return m + log(s);
+    double m = -INFINITY;
+    for (int b = (threadIdx.x & 31); b < nb; b += 32) m = fmax(m, (double)l[b]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    return m;
 }
 
-__global__ void propose_kernel(int64_t C, int nb, const float *logits, const __grid_constant__ RoundKeys rk,
-                               uint64_t t, int32_t *block)
+// exp(l[b] - m) of the blocks base .. base + n - 1 into e[0 .. n-1]
+__device__ __forceinline__ void chunk_exp(const float *l, double m, int base, int n, double *e)
 {
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+    for (int j = (threadIdx.x & 31); j < n; j += 32) e[j] = exp((double)l[base + j] - m);
+    __syncwarp();
+}
+
+// sum over b of exp(l[b] - m) in block order (the value is lane 0's)
+__device__ double warp_exp_sum(const float *l, int nb, double m, double *e)
+{
+    double total = 0.0;
+    for (int base = 0; base < nb; base += kChunk) {
+        const int n = min(kChunk, nb - base);
+        chunk_exp(l, m, base, n, e);
+        if ((threadIdx.x & 31) == 0)
+            for (int j = 0; j < n; ++j) total += e[j];
+        __syncwarp();
+    }
+    return total;
+}
+
+__global__ void __launch_bounds__(32 * kMoveWarps) propose_kernel(int64_t C, int nb, const float *logits,
+                                                                   const __grid_constant__ RoundKeys rk, uint64_t t,
+                                                                   int32_t *block)
+{
+    __shared__ double ebuf[kMoveWarps][kChunk];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    double *e = ebuf[wl];
+    const int64_t nwarps = (int64_t)gridDim.x * kMoveWarps;
+    for (int64_t c = (int64_t)blockIdx.x * kMoveWarps + wl; c < C; c += nwarps) {
         const uint32_t u = move_draw(rk, (uint32_t)c, 0, t);
         int b = nb - 1;
         if (logits == nullptr) {
             b = (int)(((uint64_t)u * (uint64_t)nb) >> 32);
         } else {
+            // inverse CDF: the first block whose cumulative weight exceeds u / 2^32 of the total
             const float *l = logits + c * nb;
-            double m = l[0];
-            for (int k = 1; k < nb; ++k) m = fmax(m, (double)l[k]);
-            double total = 0.0;
-            for (int k = 0; k < nb; ++k) total += exp((double)l[k] - m);
-            const double target = ((double)u / 4294967296.0) * total;
+            const double m = warp_max_logit(l, nb);
+            const double target = ((double)u / 4294967296.0) * warp_exp_sum(l, nb, m, e);
             double acc = 0.0;
-            for (int k = 0; k < nb; ++k) {
-                acc += exp((double)l[k] - m);
-                if (acc > target) {
-                    b = k;
-                    break;
-                }
+            int found = -1;
+            for (int base = 0; base < nb && found < 0; base += kChunk) {
+                const int n = min(kChunk, nb - base);
+                chunk_exp(l, m, base, n, e);
+                if (lane == 0)
+                    for (int j = 0; j < n; ++j) {
+                        acc += e[j];
+                        if (acc > target) {
+                            found = base + j;
+                            break;
+                        }
+                    }
+                found = __shfl_sync(0xffffffffu, found, 0);
             }
+            if (found >= 0) b = found;
         }
-        block[c] = b;
+        if (lane == 0) block[c] = b;
     }
 }
 
-__global__ void accept_kernel(Chains ch, uint64_t *black, uint64_t *white, int64_t C, double beta, const float *lx,
-                              const float *lxp, const int32_t *block, const __grid_constant__ RoundKeys rk, uint64_t t,
-                              int32_t *accepted, int64_t *dE_out)
+__global__ void __launch_bounds__(32 * kMoveWarps) accept_kernel(Chains ch, uint64_t *black, uint64_t *white,
+                                                                  int64_t C, double beta, const float *lx,
+                                                                  const float *lxp, const int32_t *block,
+                                                                  const __grid_constant__ RoundKeys rk, uint64_t t,
+                                                                  int32_t *accepted, int64_t *dE_out)
 {
+    __shared__ double ebuf[kMoveWarps][kChunk];
     const int L = ch.L, nb1 = L / kBlk, nb = nb1 * nb1;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    double *e = ebuf[wl];
+    const int64_t nwarps = (int64_t)gridDim.x * kMoveWarps;
+    for (int64_t c = (int64_t)blockIdx.x * kMoveWarps + wl; c < C; c += nwarps) {
         const int b = block[c];
-        const int dE = block_delta_E(ch, c, b);
+        const int by = b / nb1, bx = b - by * nb1, y0 = by * kBlk, x0 = bx * kBlk;
+        // twice the boundary bond sum: lane = (edge, position along it)
+        const int pos = lane & 7, edge = lane >> 3;
+        int yi, xi, yo, xo;
+        if (edge == 0) { yi = y0; xi = x0 + pos; yo = (y0 - 1 + L) % L; xo = xi; }
+        else if (edge == 1) { yi = y0 + kBlk - 1; xi = x0 + pos; yo = (y0 + kBlk) % L; xo = xi; }
+        else if (edge == 2) { yi = y0 + pos; xi = x0; yo = yi; xo = (x0 - 1 + L) % L; }
+        else { yi = y0 + pos; xi = x0 + kBlk - 1; yo = yi; xo = (x0 + kBlk) % L; }
+        int d = (int)spin_at(ch, c, yi, xi, -1) * (int)spin_at(ch, c, yo, xo, -1);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+        const int dE = 2 * d;
         double x = -beta * (double)dE;
         if (lx != nullptr) {
-            const double logp_rev = (double)lxp[c * nb + b] - log_norm(lxp + c * nb, nb);
-            const double logp_fwd = (double)lx[c * nb + b] - log_norm(lx + c * nb, nb);
+            // log q(b) = l_b - (max + log sum exp(l - max)), sums in block order
+            const float *lr = lxp + c * nb, *lf = lx + c * nb;
+            const double mr = warp_max_logit(lr, nb);
+            const double sr = warp_exp_sum(lr, nb, mr, e);
+            const double mf = warp_max_logit(lf, nb);
+            const double sf = warp_exp_sum(lf, nb, mf, e);
+            const double logp_rev = (double)lr[b] - (mr + log(sr));
+            const double logp_fwd = (double)lf[b] - (mf + log(sf));
             x = (x + logp_rev) - logp_fwd;
         }
-        const uint64_t T = x >= 0.0 ? (uint64_t(1) << 32) : (uint64_t)floor(ldexp(exp(x), 32));
-        const uint32_t u = move_draw(rk, (uint32_t)c, 1, t);
-        const bool acc = (uint64_t)u < T;
-        accepted[c] = acc ? 1 : 0;
-        if (dE_out) dE_out[c] = dE;
-        if (acc) {
-            const int by = b / nb1, bx = b - by * nb1;
-            // the block's 4 sites of each colour per row sit in nibbles 4 bx .. 4 bx + 3
-            const int j0 = 4 * bx;
-            const uint64_t mask = 0x1111ull << (4 * (j0 & 15));
-            for (int r = 0; r < kBlk; ++r) {
-                const int64_t w = c * (int64_t)L * ch.wpr + (int64_t)(by * kBlk + r) * ch.wpr + (j0 >> 4);
-                black[w] ^= mask;
-                white[w] ^= mask;
+        if (lane == 0) {
+            const uint64_t T = x >= 0.0 ? (uint64_t(1) << 32) : (uint64_t)floor(ldexp(exp(x), 32));
+            const uint32_t u = move_draw(rk, (uint32_t)c, 1, t);
+            const bool acc = (uint64_t)u < T;
+            accepted[c] = acc ? 1 : 0;
+            if (dE_out) dE_out[c] = dE;
+            if (acc) {
+                // the block's 4 sites of each colour per row sit in nibbles 4 bx .. 4 bx + 3
+                const int j0 = 4 * bx;
+                const uint64_t mask = 0x1111ull << (4 * (j0 & 15));
+                for (int r = 0; r < kBlk; ++r) {
+                    const int64_t w = c * (int64_t)L * ch.wpr + (int64_t)(y0 + r) * ch.wpr + (j0 >> 4);
+                    black[w] ^= mask;
+                    white[w] ^= mask;
+                }
             }
         }
     }
@@ -1584,8 +1646,8 @@ ISING_API int ising_block_propose(int64_t L, int64_t C, const float *logits_dev,
     if (rc) return rc;
     if (check_device_range(block_dev, (size_t)C * 4, "block")) return nfail(ISING_EINVAL, "block must be device memory");
     const int nb = (int)((L / 8) * (L / 8));
-    propose_kernel<<<grid1d(C, 128), 128, 0, (cudaStream_t)stream>>>(C, nb, logits_dev, make_round_keys(seed), t,
-                                                                     block_dev);
+    propose_kernel<<<grid1d(C * 32, 32 * kMoveWarps), 32 * kMoveWarps, 0, (cudaStream_t)stream>>>(
+        C, nb, logits_dev, make_round_keys(seed), t, block_dev);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ISING_OK : nfail(ISING_ECUDA, cudaGetErrorString(e));
 }
@@ -1605,7 +1667,7 @@ ISING_API int ising_block_accept(int64_t L, int64_t C, void *black_dev, void *wh
         check_device_range(accepted_dev, (size_t)C * 4, "accepted"))
         return nfail(ISING_EINVAL, "planes and accepted must be device memory of their sizes");
     Chains ch{(const uint64_t *)black_dev, (const uint64_t *)white_dev, (int)L, (int)(L / 32)};
-    accept_kernel<<<grid1d(C, 128), 128, 0, (cudaStream_t)stream>>>(
+    accept_kernel<<<grid1d(C * 32, 32 * kMoveWarps), 32 * kMoveWarps, 0, (cudaStream_t)stream>>>(
         ch, (uint64_t *)black_dev, (uint64_t *)white_dev, C, beta, logits_x_dev, logits_xp_dev, block_dev,
         make_round_keys(seed), t, accepted_dev, dE_dev);
     cudaError_t e = cudaGetLastError();
