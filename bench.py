@@ -53,7 +53,8 @@ def parse_args(argv=None):
     p.add_argument("--slabs", type=int, default=4, help="slabs on one GPU for the slab leg / workload")
     p.add_argument("--no-binder", action="store_true", help="skip the Binder-crossing leg")
     p.add_argument("--binder-sweeps", type=int, default=100000)
-    p.add_argument("--workload", choices=["sweep", "pt", "learned", "network", "slabs", "binder"], default="sweep",
+    p.add_argument("--workload", choices=["sweep", "pt", "learned", "network", "train", "slabs", "binder"],
+                   default="sweep",
                    help="sweep: the 65536^2 lattice (default); pt / learned: only that leg")
     p.add_argument("--no-learned", action="store_true", help="skip the learned block-proposal leg")
     p.add_argument("--learned-steps", type=int, default=1000, help="training steps of the proposal network")
@@ -871,6 +872,30 @@ def main(argv=None):
         res = {"metric": "network forward pixels/s", "value": round(C * 128 * 128 / net["full_forward_ms"] / 1e6, 3),
                "unit": "Gpixel/s", "impl": "ours", "higher_is_better": True,
                "config": {"workload": f"{C} chains of 128x128, random bfloat16 weights"}, "network": net}
+    elif args.workload == "train":
+        # the proposal network's training alone: --learned-steps Adam steps of batch 64 on
+        # --learned-configs plain-sweep configurations of 128 x 128
+        import torch
+
+        import paper_1906_06297_gb300 as ising
+
+        ising.build()
+        torch.cuda.set_device(local)
+        device = torch.device("cuda", local)
+        stream = torch.cuda.Stream(device=device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tr = ising.train_block_proposer(128, BETA_C_CONFIG, n_configs=args.learned_configs, batch=64,
+                                        steps=args.learned_steps, lr=2e-3, seed=args.seed,
+                                        log_every=max(1, args.learned_steps // 10), device=device, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res = {"metric": "proposal-network training steps/s", "value": round(args.learned_steps / (ms * 1e-3), 2),
+               "unit": "steps/s", "impl": "ours", "higher_is_better": True,
+               "config": {"workload": f"{args.learned_steps} Adam steps, batch 64 chains of 128x128, "
+                                      f"{args.learned_configs} configurations"},
+               "train_ms": round(ms, 1), "loss_first_last": [round(tr["loss"][0], 4), round(tr["loss"][-1], 4)]}
     elif args.workload == "learned":
         import torch
 

@@ -295,7 +295,7 @@ __device__ __forceinline__ uint32_t spin_up(const Chains &ch, int64_t c, int y, 
 // Thread per pixel of the band; blockIdx.y walks the chains and blockIdx.x
 // the 128-pixel tiles of a chain's band, so all index arithmetic is 32-bit.
 // Writes a1 (bfloat16, from the table in shared memory) and, when z_out !=
-// nullptr, z1 (FP32).
+// nullptr, z1 (FP32), each store instruction covering whole pixels.
 __global__ void __launch_bounds__(kL1Threads) l1_kernel(Chains ch, Band bd, const int32_t *flip,
                                                         const __nv_bfloat16 *ta, const float *tz, float *z_out,
                                                         __nv_bfloat16 *a_out)
@@ -315,14 +315,24 @@ __global__ void __launch_bounds__(kL1Threads) l1_kernel(Chains ch, Band bd, cons
             uint32_t pat = 0;
 #pragma unroll
             for (int k = 0; k < 9; ++k) pat |= spin_up(ch, c, wrap(y + k / 3 - 1, L), wrap(x + k % 3 - 1, L), fb) << k;
-            const uint4 *row = T + pat * 4;
+            // the warp's 32 pixels are consecutive in one row: store round j
+            // writes pixels 8j .. 8j+7 whole (512 contiguous bytes), lane l
+            // the 16-byte part l % 4 of pixel 8j + l / 4
+            const int lane = threadIdx.x & 31, x_first = x - lane;
 #pragma unroll
-            for (int g = 0; g < 4; ++g) store_act(a_out, L, c, y, x, 8 * g, row[g]);
+            for (int j = 0; j < 4; ++j) {
+                const int pp = 8 * j + (lane >> 2), g = lane & 3;
+                const uint32_t pt = __shfl_sync(0xffffffffu, pat, pp);
+                store_act(a_out, L, c, y, x_first + pp, 8 * g, T[pt * 4 + g]);
+            }
             if (z_out) {
-                const float4 *zr = reinterpret_cast<const float4 *>(tz + pat * kCh);
-                float4 *zo = reinterpret_cast<float4 *>(z_out + ((c * L + y) * (int64_t)L + x) * kCh);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) zo[i] = __ldg(zr + i);
+                for (int j = 0; j < 8; ++j) {
+                    const int pp = 4 * j + (lane >> 3), g = lane & 7;
+                    const uint32_t pt = __shfl_sync(0xffffffffu, pat, pp);
+                    reinterpret_cast<float4 *>(z_out + ((c * L + y) * (int64_t)L + x_first + pp) * kCh)[g] =
+                        __ldg(reinterpret_cast<const float4 *>(tz + pt * kCh) + g);
+                }
             }
         }
     }
@@ -900,41 +910,43 @@ __global__ void __launch_bounds__(kThreads) l4_project_kernel(Band bd, const flo
 }
 
 // Layer 4 and the block mean from the projections: z4(y, x) = b4 + sum over
-// taps k of P[k](y + dy_k, x + dx_k).  Warp per (chain, block) over `brows`
-// block rows per chain (all of them in a full pass; in a band pass the
-// flipped block's row and its two neighbours), two pixels per lane, taps in
-// order, then a fixed shuffle tree.
+// taps k of P[k](y + dy_k, x + dx_k).  Warp per (chain, block row, group of 4
+// blocks) over `brows` block rows per chain (all of them in a full pass; in a
+// band pass the flipped block's row and its two neighbours): lane l owns
+// pixel column 8 b + l of the group and walks the block's 8 rows (taps in
+// order, rows in order), so every load of a tap plane is 32 consecutive
+// floats; the 8 lanes of a block then add up in a fixed shuffle tree.
 __global__ void __launch_bounds__(kThreads) pool_kernel(int L, int64_t C, int brows, const int32_t *flip,
                                                         const float *params, const float *P, float *logits)
 {
     const float b4 = bf16r(params[kOffB4]);
-    const int nb1 = L / kBlk, nb = nb1 * nb1;
+    const int nb1 = L / kBlk, nb = nb1 * nb1, groups = nb1 / 4;
     const int lane = threadIdx.x & 31;
     const int64_t npix = C * (int64_t)L * L;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int per = brows * nb1;
+    const int per = brows * groups;
     for (int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < C * per; wi += nw) {
         const int64_t c = wi / per;
-        const int r = (int)(wi - c * per), rb = r / nb1, bx = r - rb * nb1;
+        const int r = (int)(wi - c * per), rb = r / groups, bg = r - rb * groups;
         int by = rb;
         if (flip) {
             const int f = flip[c];
             by = wrap((f < 0 ? 0 : f / nb1) - 1 + rb, nb1);
         }
         const float *Pc = P + c * (int64_t)L * L;
+        const int x = bg * 32 + lane;
+        const int xs[3] = {wrap(x - 1, L), x, wrap(x + 1, L)};
         float part = 0.0f;
-        for (int e = 0; e < 2; ++e) {
-            const int pix = lane + 32 * e;  // 0..63 within the block
-            const int y = by * kBlk + pix / kBlk, x = bx * kBlk + pix % kBlk;
+        for (int yy = by * kBlk; yy < by * kBlk + kBlk; ++yy) {
+            const int ys[3] = {wrap(yy - 1, L), yy, wrap(yy + 1, L)};
             float z = b4;
 #pragma unroll
-            for (int k = 0; k < 9; ++k)
-                z += __ldg(Pc + k * npix + wrap(y + k / 3 - 1, L) * (int64_t)L + wrap(x + k % 3 - 1, L));
+            for (int k = 0; k < 9; ++k) z += __ldg(Pc + k * npix + ys[k / 3] * (int64_t)L + xs[k % 3]);
             part += z;
         }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-        if (lane == 0) logits[c * nb + by * nb1 + bx] = part * (1.0f / (kBlk * kBlk));
+        for (int off = 4; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+        if ((lane & 7) == 0) logits[c * nb + by * nb1 + 4 * bg + (lane >> 3)] = part * (1.0f / (kBlk * kBlk));
     }
 }
 
@@ -1527,7 +1539,7 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
                                                                                              w.P);
     }
     const int brows = band ? kBandRows[3] : L / kBlk;
-    const int64_t warps = C * brows * (L / kBlk);
+    const int64_t warps = C * brows * (L / kBlk / 4);
     pool_kernel<<<grid1d(warps * 32, kThreads), kThreads, 0, s>>>(L, C, brows, band ? flip : nullptr, params, w.P,
                                                                   logits);
     cudaError_t e = cudaGetLastError();
