@@ -16,7 +16,9 @@ gelu(z) = z Phi(z) (Phi the standard normal CDF).  It is a BF16 network: the
 caller passes bfloat16-valued weights, and r rounds each activation to the
 nearest bfloat16 (via float32, ties to even); everything else is float64 here.
 Gradients pass straight through r (the rounded activations enter the weight
-gradients).  The proposal picks block b
+gradients); in the same way the gradient entering each 32 -> 32 layer's data
+gradient (dz3, dz2) is rounded to bfloat16 there, while the weight gradients
+take it unrounded.  The proposal picks block b
 with probability q_x(b) = softmax(l)_b; x' is x with block b flipped.
 
 Move (exact Metropolis-Hastings): accept with min(1, exp(-beta dE) q_x'(b) /
@@ -82,15 +84,17 @@ def conv(a, W, b):
     return z + b[None, :, None, None]
 
 
-def conv_backward(a, W, dz):
-    """Gradients of sum(dz * conv(a, W, b)) w.r.t. a, W and b."""
+def conv_backward(a, W, dz, dz_data=None):
+    """Gradients of sum(dz * conv(a, W, b)) w.r.t. a, W and b; the gradient
+    w.r.t. a uses dz_data in place of dz when it is given."""
     dW = np.zeros_like(W)
     da = np.zeros_like(a)
+    dd = dz if dz_data is None else dz_data
     for k, (dy, dx) in enumerate(OFFSETS):
         shifted = np.roll(a, shift=(-dy, -dx), axis=(2, 3))
         dW[:, :, k] = np.einsum("coyx,ciyx->oi", dz, shifted)
         # z[y, x] uses a[y+dy, x+dx]: push dz back to those inputs
-        back = np.einsum("oi,coyx->ciyx", W[:, :, k], dz)
+        back = np.einsum("oi,coyx->ciyx", W[:, :, k], dd)
         da += np.roll(back, shift=(dy, dx), axis=(2, 3))
     db = dz.sum(axis=(0, 2, 3))
     return da, dW, db
@@ -131,7 +135,7 @@ def forward(theta, spins, B=8, flip=None, keep=False, round_act=True):
     z4 = conv(a3, p["W4"], p["b4"])
     logits = block_pool(z4, B)
     if keep:
-        return logits, dict(a0=a0, z1=z1, a1=a1, z2=z2, a2=a2, z3=z3, a3=a3, B=B)
+        return logits, dict(a0=a0, z1=z1, a1=a1, z2=z2, a2=a2, z3=z3, a3=a3, B=B, round=round_act)
     return logits
 
 
@@ -144,11 +148,12 @@ def backward(theta, cache, dlogits):
     n = int(round(math.sqrt(nb)))
     L = n * B
     dz4 = np.repeat(np.repeat(dlogits.reshape(C, n, n), B, axis=1), B, axis=2)[:, None] / (B * B)
+    r = bf16_round if cache.get("round", True) else (lambda v: v)
     da3, dW4, db4 = conv_backward(cache["a3"], p["W4"], dz4)
     dz3 = da3 * gelu_grad(cache["z3"])
-    da2, dW3, db3 = conv_backward(cache["a2"], p["W3"], dz3)
+    da2, dW3, db3 = conv_backward(cache["a2"], p["W3"], dz3, dz_data=r(dz3))
     dz2 = da2 * gelu_grad(cache["z2"])
-    da1, dW2, db2 = conv_backward(cache["a1"], p["W2"], dz2)
+    da1, dW2, db2 = conv_backward(cache["a1"], p["W2"], dz2, dz_data=r(dz2))
     dz1 = da1 * gelu_grad(cache["z1"])
     _, dW1, db1 = conv_backward(cache["a0"], p["W1"], dz1)
     assert L == cache["a0"].shape[2]

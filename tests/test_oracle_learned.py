@@ -4,7 +4,9 @@
   network without activation rounding, which is smooth; the rounded network
   uses the same formulas straight through the rounding).
 - The bfloat16 activations: exactly representable, within half a bfloat16
-  step of the unrounded values, and the logits close to the unrounded ones.
+  step of the unrounded values, and the logits close to the unrounded ones;
+  the gradient of the rounded network (bfloat16 gradients into the 32-channel
+  data gradients) close to the exact one, its layer-4 part equal to it.
 - The block energy change against the full Hamiltonian (Eq. 1) before and
   after the flip.
 - The Metropolis-Hastings block move, interleaved with checkerboard sweeps,
@@ -110,6 +112,24 @@ def test_activations_are_bf16_and_close_to_unrounded():
     # the logits move by a small fraction of their spread, not by a different network
     d = np.abs(lr - lu).max()
     assert 0 < d < 0.05 * (np.abs(lu).max() + 1e-12), (d, np.abs(lu).max())
+
+
+def test_rounded_backward_is_close_to_the_exact_gradient():
+    rng = np.random.default_rng(8)
+    theta = ln.bf16_round(random_theta(9, 0.2).astype(np.float32))
+    spins = rng.choice([-1.0, 1.0], size=(2, 16, 16))
+    dl = rng.normal(size=(2, 4))
+    _, cr = ln.forward(theta, spins, B=8, keep=True)
+    gr = ln.backward(theta, cr, dl)
+    cu = dict(cr, round=False)  # same rounded activations, unrounded gradients
+    gu = ln.backward(theta, cu, dl)
+    parts = ln.unflatten(np.arange(ln.N_PARAMS))
+    w4 = np.concatenate([parts["W4"].ravel(), parts["b4"].ravel(), parts["W3"].ravel(), parts["b3"].ravel()])
+    # W4, b4 and W3 see dz3 unrounded: identical
+    np.testing.assert_array_equal(gr[w4.astype(int)], gu[w4.astype(int)])
+    # W2 and W1 see gradients that went through bfloat16 (2^-8 relative per value)
+    d = np.abs(gr - gu).max() / np.abs(gu).max()
+    assert 0 < d < 1e-2, d
 
 
 def _chain_bond_sums(logits_fn, beta, n_cycles, seed, L=4, B=2):
