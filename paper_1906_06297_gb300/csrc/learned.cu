@@ -567,6 +567,13 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv32_tc_kernel(const __grid
 // (pfull, a3empty), and the epilogue warps of the first channel half store P
 // one tile later (pempty), as 9 FP32 planes P[k][pixel].  Then a3 itself need not reach global memory
 // (it still does when training, for the backward pass).
+// BWD (the data gradient of a 32 -> 32 layer in the training backward pass):
+// the same contraction with the incoming gradient dz (bfloat16, halo columns)
+// as the staged rows and the weights transposed and tap-flipped, B_k[i][o] =
+// W[o][i][8 - k], since dz_prev(p)[i] = gelu'(z_prev(p)[i]) sum_k sum_o
+// W[o][i][k] dz(p - off_k)[o] and -off_k = off_{8-k}; the epilogue multiplies
+// by gelu'(z_prev) and writes dz_prev in FP32 (and in bfloat16 with halo
+// columns when a_out is set, for the next data gradient).
 // Dependencies: MMA step t waits on epilogue steps < t only, epilogue step t
 // on MMA steps <= t only, so no wait can close a cycle.
 constexpr int kRing = 8;        // staged rows (a power of two)
@@ -599,6 +606,8 @@ struct RingConv {
     __nv_bfloat16 *a_out;  // nullable when PROJ
     float *z_out;          // nullable
     float *P;              // PROJ: 9 planes of C L^2
+    const float *zg;       // BWD: z of the layer below (FP32, NHWC) for gelu'
+    float *d_out;          // BWD: dz of the layer below (FP32, NHWC)
     const float *params;
     int w_off, b_off;
     Band bd;
@@ -634,7 +643,7 @@ __device__ __forceinline__ int ring_row(const RingConv &p, int64_t c, int r)
     return y >= L ? y - L : y;
 }
 
-template <bool PROJ>
+template <bool PROJ, bool BWD>
 __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __grid_constant__ RingConv p)
 {
     extern __shared__ __align__(1024) uint8_t ring_smem[];
@@ -672,11 +681,14 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
         tc::fence_mbar_init();
     }
     for (int e = tid; e < kTaps * kGroups * kCh; e += blockDim.x) {
-        const int k = e / (kGroups * kCh), r = e - k * (kGroups * kCh), g = r / kCh, o = r - g * kCh;
-        const float *w = p.params + p.w_off + (o * kCh + 8 * g) * 9 + k;
+        const int k = e / (kGroups * kCh), r = e - k * (kGroups * kCh), g = r / kCh, n = r - g * kCh;
+        // forward: row n = output channel o, K = input channels 8g .. 8g+7 of tap k;
+        // BWD: row n = input channel i, K = output channels 8g .. 8g+7 of tap 8 - k
+        const int st = BWD ? kCh * 9 : 9;
+        const float *w = p.params + p.w_off + (BWD ? ((8 * g) * kCh + n) * 9 + (8 - k) : (n * kCh + 8 * g) * 9 + k);
         *reinterpret_cast<uint4 *>(sB + e * 16) =
-            make_uint4(pack_bf16x2(w[0], w[9]), pack_bf16x2(w[18], w[27]), pack_bf16x2(w[36], w[45]),
-                       pack_bf16x2(w[54], w[63]));
+            make_uint4(pack_bf16x2(w[0], w[st]), pack_bf16x2(w[2 * st], w[3 * st]),
+                       pack_bf16x2(w[4 * st], w[5 * st]), pack_bf16x2(w[6 * st], w[7 * st]));
     }
     if (PROJ) {
         // W4^T as an N = 16 x K = 32 operand: row n = tap n (zero for n >= 9),
@@ -691,7 +703,7 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
             *reinterpret_cast<uint4 *>(sW4 + e * 16) = make_uint4(u[0], u[1], u[2], u[3]);
         }
     }
-    if (tid < kCh) sBias[tid] = bf16r(p.params[p.b_off + tid]);
+    if (tid < kCh) sBias[tid] = BWD ? 0.0f : bf16r(p.params[p.b_off + tid]);
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -821,42 +833,63 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
                 if (lane == 0) tc::mbar_arrive(&acce[a]);
                 const int y = ring_row(p, w.c, w.r0 + j);
                 const int64_t q = (w.c * L + y) * (int64_t)L + w.x0 + m;
+                if constexpr (BWD) {
+                    const float4 *zq = reinterpret_cast<const float4 *>(p.zg + q * kCh + 16 * half);
+                    float4 *dq = reinterpret_cast<float4 *>(p.d_out + q * kCh + 16 * half);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] += sBias[16 * half + i];
-                if (p.z_out) {
-                    float4 *zo = reinterpret_cast<float4 *>(p.z_out + q * kCh + 16 * half);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) zo[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                }
-                uint32_t pk[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    float g0 = v[2 * i], g1 = v[2 * i + 1];
-                    gelu2(g0, g1);
-                    pk[i] = pack_bf16x2(g0, g1);
-                }
-                if (p.a_out) {
-                    store_act(p.a_out, L, w.c, y, w.x0 + m, 16 * half, make_uint4(pk[0], pk[1], pk[2], pk[3]));
-                    store_act(p.a_out, L, w.c, y, w.x0 + m, 16 * half + 8, make_uint4(pk[4], pk[5], pk[6], pk[7]));
-                }
-                if (PROJ) {
-                    const int b = (int)(t & 1);
-                    if (t >= 2 && !__all_sync(0xffffffffu, tc::mbar_wait(&a3empty[b], (uint32_t)(((t >> 1) + 1) & 1),
-                                                                          kWaitCycles))) {
-                        ok = false;
-                        break;
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 zz = __ldg(zq + i);
+                        v[4 * i] *= gelu_grad(zz.x);
+                        v[4 * i + 1] *= gelu_grad(zz.y);
+                        v[4 * i + 2] *= gelu_grad(zz.z);
+                        v[4 * i + 3] *= gelu_grad(zz.w);
+                        dq[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
                     }
-                    uint8_t *dst = a3s + b * kRowBytes + 2 * half * kRingPlane + m * 16;
-                    *reinterpret_cast<uint4 *>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                    *reinterpret_cast<uint4 *>(dst + kRingPlane) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                    tc::fence_async_smem();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&a3full[b]);
-                    if (half == 0 && t >= 1 && !read_proj(t - 1, q_prev)) {
-                        ok = false;
-                        break;
+                    if (p.a_out) {
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) pk[i] = pack_bf16x2(v[2 * i], v[2 * i + 1]);
+                        store_act(p.a_out, L, w.c, y, w.x0 + m, 16 * half, make_uint4(pk[0], pk[1], pk[2], pk[3]));
+                        store_act(p.a_out, L, w.c, y, w.x0 + m, 16 * half + 8, make_uint4(pk[4], pk[5], pk[6], pk[7]));
                     }
-                    q_prev = q;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += sBias[16 * half + i];
+                    if (p.z_out) {
+                        float4 *zo = reinterpret_cast<float4 *>(p.z_out + q * kCh + 16 * half);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) zo[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    }
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        float g0 = v[2 * i], g1 = v[2 * i + 1];
+                        gelu2(g0, g1);
+                        pk[i] = pack_bf16x2(g0, g1);
+                    }
+                    if (p.a_out) {
+                        store_act(p.a_out, L, w.c, y, w.x0 + m, 16 * half, make_uint4(pk[0], pk[1], pk[2], pk[3]));
+                        store_act(p.a_out, L, w.c, y, w.x0 + m, 16 * half + 8, make_uint4(pk[4], pk[5], pk[6], pk[7]));
+                    }
+                    if (PROJ) {
+                        const int b = (int)(t & 1);
+                        if (t >= 2 && !__all_sync(0xffffffffu, tc::mbar_wait(&a3empty[b], (uint32_t)(((t >> 1) + 1) & 1),
+                                                                              kWaitCycles))) {
+                            ok = false;
+                            break;
+                        }
+                        uint8_t *dst = a3s + b * kRowBytes + 2 * half * kRingPlane + m * 16;
+                        *reinterpret_cast<uint4 *>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        *reinterpret_cast<uint4 *>(dst + kRingPlane) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                        tc::fence_async_smem();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&a3full[b]);
+                        if (half == 0 && t >= 1 && !read_proj(t - 1, q_prev)) {
+                            ok = false;
+                            break;
+                        }
+                        q_prev = q;
+                    }
                 }
             }
         }
@@ -955,7 +988,8 @@ __global__ void __launch_bounds__(kThreads) pool_kernel(int L, int64_t C, int br
 // ---------------------------------------------------------------------------
 // dz3 = gelu'(z3) * sum_k W4[i][k] * d4(p - off_k),  d4(p) = dlogit(block of p) / 64.
 __global__ void __launch_bounds__(kThreads) l4_bwd_data_kernel(int L, int64_t C, const float *params,
-                                                               const float *dlogits, const float *z3, float *dz3)
+                                                               const float *dlogits, const float *z3, float *dz3,
+                                                               __nv_bfloat16 *dz3b)
 {
     __shared__ float W[kN1];
     for (int i = threadIdx.x; i < kN1; i += blockDim.x) W[i] = bf16r(params[kOffW4 + i]);
@@ -973,17 +1007,29 @@ __global__ void __launch_bounds__(kThreads) l4_bwd_data_kernel(int L, int64_t C,
             const int yy = (y - (k / 3 - 1) + L) % L, xx = (x - (k % 3 - 1) + L) % L;
             d[k] = dlogits[c * nb1 * nb1 + (yy / kBlk) * nb1 + xx / kBlk] * (1.0f / (kBlk * kBlk));
         }
-        for (int i = 0; i < kCh; ++i) {
-            float g = 0.0f;
+#pragma unroll 1
+        for (int i8 = 0; i8 < kCh; i8 += 8) {
+            float v[8];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) g = fmaf(W[i * 9 + k], d[k], g);
-            dz3[p * kCh + i] = g * gelu_grad(z3[p * kCh + i]);
+            for (int i = 0; i < 8; ++i) {
+                float g = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) g = fmaf(W[(i8 + i) * 9 + k], d[k], g);
+                v[i] = g * gelu_grad(z3[p * kCh + i8 + i]);
+                dz3[p * kCh + i8 + i] = v[i];
+            }
+            // bfloat16 copy with halo columns: the operand of the next data gradient on the tensor cores
+            if (dz3b)
+                store_act(dz3b, L, c, y, x, i8,
+                          make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                                     pack_bf16x2(v[6], v[7])));
         }
     }
 }
 
-// dz_prev = gelu'(z_prev) * sum_{k, o} W[o][i][k] * dz(p - off_k)[o]; weights
-// as Wt[k][o][i] (32 contiguous inputs per tap and output).
+// dz_prev = gelu'(z_prev) * sum_{k, o} W[o][i][k] * bf16(dz(p - off_k)[o]);
+// weights as Wt[k][o][i] (32 contiguous inputs per tap and output).  The
+// incoming gradient is rounded to bfloat16, as on the tensor-core path.
 __global__ void __launch_bounds__(kThreads) conv32_bwd_data_kernel(int L, int64_t C, const float *params, int w_off,
                                                                    const float *dz, const float *z_prev, float *dz_prev)
 {
@@ -1007,7 +1053,7 @@ __global__ void __launch_bounds__(kThreads) conv32_bwd_data_kernel(int L, int64_
 #pragma unroll
             for (int q = 0; q < kCh / 4; ++q) {
                 const float4 v = src[q];
-                const float g4[4] = {v.x, v.y, v.z, v.w};
+                const float g4[4] = {bf16r(v.x), bf16r(v.y), bf16r(v.z), bf16r(v.w)};
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     const float *w = Wt + (k * kCh + 4 * q + r) * kCh;
@@ -1376,7 +1422,7 @@ int check_chains(int64_t L, int64_t C)
 // Both end with the 9 FP32 planes P of layer 4's tap projections.
 struct NetWork {
     float *z1, *z2, *z3, *da, *db, *partial, *P, *tz;
-    __nv_bfloat16 *a1, *a2, *a3, *ta;
+    __nv_bfloat16 *a1, *a2, *a3, *ta, *gb1, *gb2;  // gb: bfloat16 gradients with halo columns (training)
     int64_t n_cta;
     size_t bytes;
 };
@@ -1400,6 +1446,7 @@ NetWork net_layout(int64_t L, int64_t C, int train, char *base)
         w.a1 = (__nv_bfloat16 *)take(apx * 2); w.a2 = (__nv_bfloat16 *)take(apx * 2);
         w.a3 = (__nv_bfloat16 *)take(apx * 2);
         w.da = (float *)take(pix * 4); w.db = (float *)take(pix * 4);
+        w.gb1 = (__nv_bfloat16 *)take(apx * 2); w.gb2 = (__nv_bfloat16 *)take(apx * 2);
         DeviceInfo info{152};
         device_info(&info);
         w.n_cta = (int64_t)info.sm_count * kWgradCtasPerSm;
@@ -1467,6 +1514,38 @@ bool encode_rows(CUtensorMap (&m)[kGroups], const __nv_bfloat16 *a, int L, int64
     return true;
 }
 
+// The data gradient of a 32 -> 32 layer (weights at w_off) on the tensor
+// cores: dz_prev = gelu'(zg) * conv^T(in), in the bfloat16 gradient with halo
+// columns; writes d_out (FP32) and, if given, a_out (bfloat16, halo columns).
+int launch_ring_bwd(int L, int64_t C, const float *params, int w_off, const __nv_bfloat16 *in, const float *zg,
+                    float *d_out, __nv_bfloat16 *a_out, cudaStream_t s)
+{
+    DeviceInfo info{152};
+    device_info(&info);
+    RingConv p{};
+    if (!encode_rows(p.tmap, in, L, C)) return nfail(ISING_ECUDA, "cuTensorMapEncodeTiled failed");
+    p.a_in = in;
+    p.a_out = a_out;
+    p.zg = zg;
+    p.d_out = d_out;
+    p.params = params;
+    p.w_off = w_off;
+    p.b_off = 0;
+    p.bd.L = L;
+    p.bd.C = C;
+    p.bd.rows = L;
+    p.bd.lead = 0;
+    p.bd.flip = nullptr;
+    p.segs = L / kTileM;
+    p.units_per_col = (L + kUnitRows - 1) / kUnitRows;
+    p.units = C * p.segs * p.units_per_col;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.units, 2 * info.sm_count));
+    cudaFuncSetAttribute(conv32_ring_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmem);
+    conv32_ring_kernel<false, true><<<grid, kRingThreads, kRingSmem, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ISING_OK : nfail(ISING_ECUDA, cudaGetErrorString(e));
+}
+
 int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, const float *params,
                    float *logits, const NetWork &w, int train, cudaStream_t s, bool withhold = false)
 {
@@ -1495,11 +1574,13 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
     float *zs[2] = {train ? w.z2 : nullptr, train ? w.z3 : nullptr};
     if (L % kTileM == 0) {
         // row-ring kernels; the second one also projects onto layer 4's taps
-        cudaFuncSetAttribute(conv32_ring_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmem);
-        cudaFuncSetAttribute(conv32_ring_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmem);
+        cudaFuncSetAttribute(conv32_ring_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kRingSmem);
+        cudaFuncSetAttribute(conv32_ring_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kRingSmem);
         __nv_bfloat16 *outs[2] = {w.a2, train ? w.a3 : nullptr};
         for (int l = 0; l < 2; ++l) {
-            RingConv p;
+            RingConv p{};
             if (!encode_rows(p.tmap, ins[l], L, C)) return nfail(ISING_ECUDA, "cuTensorMapEncodeTiled failed");
             p.a_in = ins[l];
             p.a_out = outs[l];
@@ -1515,9 +1596,9 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
             p.withhold = withhold && l == 0;
             const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.units, 2 * info.sm_count));
             if (l == 0)
-                conv32_ring_kernel<false><<<grid, kRingThreads, kRingSmem, s>>>(p);
+                conv32_ring_kernel<false, false><<<grid, kRingThreads, kRingSmem, s>>>(p);
             else
-                conv32_ring_kernel<true><<<grid, kRingThreads, kRingSmem, s>>>(p);
+                conv32_ring_kernel<true, false><<<grid, kRingThreads, kRingSmem, s>>>(p);
         }
     } else {
         cudaFuncSetAttribute(conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
@@ -1671,15 +1752,28 @@ ISING_API int ising_net_backward(int64_t L, int64_t C, const void *black_dev, co
     // layer 4
     wgrad_kernel<kCh, 1><<<gw, 256, sm4, s>>>(ch, C, w.a3, nullptr, dlogits_dev, w.partial);
     reduce_partials_kernel<<<4, 256, 0, s>>>(w.partial, w.n_cta, kN1 + 1, kN1, grad_dev, kOffW4, kOffB4);
-    l4_bwd_data_kernel<<<g, kThreads, 0, s>>>((int)L, C, params_dev, dlogits_dev, w.z3, w.da);  // dz3
+    // the data gradients of the 32 -> 32 layers run on the tensor cores for L a multiple of 128
+    const bool ring = L % kTileM == 0;
+    l4_bwd_data_kernel<<<g, kThreads, 0, s>>>((int)L, C, params_dev, dlogits_dev, w.z3, w.da,
+                                              ring ? w.gb1 : nullptr);  // dz3
     // layer 3
     wgrad_kernel<kCh, kCh><<<gw, 256, sm32, s>>>(ch, C, w.a2, w.da, nullptr, w.partial);
     reduce_partials_kernel<<<40, 256, 0, s>>>(w.partial, w.n_cta, kN2 + kCh, kN2, grad_dev, kOffW3, kOffB3);
-    conv32_bwd_data_kernel<<<g, kThreads, smem, s>>>((int)L, C, params_dev, kOffW3, w.da, w.z2, w.db);  // dz2
+    if (ring) {
+        rc = launch_ring_bwd((int)L, C, params_dev, kOffW3, w.gb1, w.z2, w.db, w.gb2, s);  // dz2
+        if (rc) return rc;
+    } else {
+        conv32_bwd_data_kernel<<<g, kThreads, smem, s>>>((int)L, C, params_dev, kOffW3, w.da, w.z2, w.db);  // dz2
+    }
     // layer 2
     wgrad_kernel<kCh, kCh><<<gw, 256, sm32, s>>>(ch, C, w.a1, w.db, nullptr, w.partial);
     reduce_partials_kernel<<<40, 256, 0, s>>>(w.partial, w.n_cta, kN2 + kCh, kN2, grad_dev, kOffW2, kOffB2);
-    conv32_bwd_data_kernel<<<g, kThreads, smem, s>>>((int)L, C, params_dev, kOffW2, w.db, w.z1, w.da);  // dz1
+    if (ring) {
+        rc = launch_ring_bwd((int)L, C, params_dev, kOffW2, w.gb2, w.z1, w.da, nullptr, s);  // dz1
+        if (rc) return rc;
+    } else {
+        conv32_bwd_data_kernel<<<g, kThreads, smem, s>>>((int)L, C, params_dev, kOffW2, w.db, w.z1, w.da);  // dz1
+    }
     // layer 1
     wgrad_kernel<1, kCh><<<gw, 256, sm1, s>>>(ch, C, nullptr, w.da, nullptr, w.partial);
     reduce_partials_kernel<<<4, 256, 0, s>>>(w.partial, w.n_cta, kN1 + kCh, kN1, grad_dev, kOffW1, kOffB1);
