@@ -551,6 +551,15 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv32_tc_kernel(const __grid
 //   warp 0: loader -- lane 0 fetches each row with four tensor copies (TMA),
 //           one per channel group: a box of 8 channels x 130 pixels of the
 //           padded row (its halo columns included), completing on full[slot];
+//           or, in the first layer of an inference pass (FUSED), the warp
+//           builds the row of a1 itself: 18 lanes turn 3 spin rows x 6
+//           32-column chunks around the segment into bit vectors (a chunk is
+//           one black and one white MSC4 word, nibbles compressed and
+//           interleaved by the row's colour parity), each pixel's 3 x 3
+//           pattern comes from them by shuffles, and its layer-1 output is
+//           the pattern's row of the table (l1_table_kernel); the lanes then
+//           fence the async proxy and lane 0 arrives on full[slot]: a1 never
+//           goes through global memory;
 //   warp 1: lane 0 issues the 18 MMAs of each tile into one of kAcc
 //           accumulators, then commits to accf[acc] and to empty[slot] of
 //           the row no later tile of the unit reads;
@@ -608,6 +617,9 @@ struct RingConv {
     float *P;              // PROJ: 9 planes of C L^2
     const float *zg;       // BWD: z of the layer below (FP32, NHWC) for gelu'
     float *d_out;          // BWD: dz of the layer below (FP32, NHWC)
+    Chains ch;             // FUSED: the spins (flip[c], or -1, negated)
+    const int32_t *flip;
+    const __nv_bfloat16 *ta;  // FUSED: layer 1's table, 512 patterns x 32 channels
     const float *params;
     int w_off, b_off;
     Band bd;
@@ -643,7 +655,41 @@ __device__ __forceinline__ int ring_row(const RingConv &p, int64_t c, int r)
     return y >= L ? y - L : y;
 }
 
-template <bool PROJ, bool BWD>
+// Bit t of the result is the lowest bit of nibble t of w.
+__device__ __forceinline__ uint32_t nibble_compress(uint64_t w)
+{
+    uint64_t v = w & 0x1111111111111111ull;
+    v = (v | (v >> 3)) & 0x0303030303030303ull;
+    v = (v | (v >> 6)) & 0x000F000F000F000Full;
+    v = (v | (v >> 12)) & 0x000000FF000000FFull;
+    return (uint32_t)((v | (v >> 24)) & 0xFFFFull);
+}
+
+// Bit t of x (16 bits) moved to bit 2t.
+__device__ __forceinline__ uint32_t bit_spread(uint32_t x)
+{
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    return (x | (x << 1)) & 0x55555555u;
+}
+
+// Columns 32 b .. 32 b + 31 of spin row r of chain c as bits (1 = up), with
+// block `flip` (or -1) negated.  Both planes' word b covers these columns:
+// in row r the black spins sit at the columns of r's parity.
+__device__ __forceinline__ uint32_t spin_chunk(const Chains &ch, int64_t c, int r, int b, int flip)
+{
+    const int64_t at = (c * ch.L + r) * (int64_t)ch.wpr + b;
+    const uint32_t kb = bit_spread(nibble_compress(ch.black[at])), kw = bit_spread(nibble_compress(ch.white[at]));
+    uint32_t v = (r & 1) ? (kw | (kb << 1)) : (kb | (kw << 1));
+    if (flip >= 0) {
+        const int nb = ch.L / kBlk, by = flip / nb, bx = flip - by * nb;
+        if ((r >> 3) == by && ((bx * kBlk) >> 5) == b) v ^= 0xFFu << ((bx * kBlk) & 31);
+    }
+    return v;
+}
+
+template <bool PROJ, bool BWD, bool FUSED>
 __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __grid_constant__ RingConv p)
 {
     extern __shared__ __align__(1024) uint8_t ring_smem[];
@@ -712,7 +758,56 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
     const uint32_t tproj = tmem + (uint32_t)(kAcc * kCh);
     bool ok = true;
 
-    if (warp == 0) {
+    if (warp == 0 && FUSED) {
+        // loader building the rows of a1 from the spins
+        uint32_t n = 0;
+        const uint4 *ta = reinterpret_cast<const uint4 *>(p.ta);
+        const int nw = L / 32;
+        for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+            const RingUnit w = ring_unit(p, u);
+            const int fb = p.flip ? p.flip[w.c] : -1;
+            for (int j = -1; j <= w.nrows; ++j, ++n) {
+                const uint32_t s = n & (kRing - 1);
+                if (n >= kRing &&
+                    !__all_sync(0xffffffffu, tc::mbar_wait(&empty[s], ((n / kRing) + 1) & 1, kWaitCycles))) {
+                    ok = false;
+                    break;
+                }
+                const int y = ring_row(p, w.c, w.r0 + j);
+                // lane 6 d + q (d < 3, q < 6): chunk x0 / 32 - 1 + q (periodic) of spin row y - 1 + d
+                uint32_t bits = 0;
+                if (lane < 18) {
+                    const int d = lane / 6, q = lane - 6 * d;
+                    const int r = wrap(y - 1 + d, L);
+                    const int b = (w.x0 / 32 - 1 + q + nw) % nw;
+                    bits = spin_chunk(p.ch, w.c, r, b, fb);
+                }
+                uint8_t *dst = ring + s * kRowBytes;
+#pragma unroll
+                for (int i = 0; i < 5; ++i) {
+                    const int e = lane + 32 * i;   // entry e is column x0 - 1 + e
+                    const int o = e + 30;          // column x0 - 2 + e relative to the window start x0 - 32
+                    const int wi = o >> 5, sh = o & 31;
+                    uint32_t pat = 0;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const uint32_t lo = __shfl_sync(0xffffffffu, bits, 6 * d + min(wi, 5));
+                        const uint32_t hi = __shfl_sync(0xffffffffu, bits, 6 * d + min(wi + 1, 5));
+                        const uint32_t trip = (uint32_t)((((uint64_t)hi << 32) | lo) >> sh) & 7u;
+                        pat |= trip << (3 * d);
+                    }
+                    if (e < kTileM + 2) {
+#pragma unroll
+                        for (int g = 0; g < kGroups; ++g)
+                            *reinterpret_cast<uint4 *>(dst + g * kRingPlane + e * 16) = __ldg(ta + pat * kGroups + g);
+                    }
+                }
+                tc::fence_async_smem();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&full[s]);
+            }
+        }
+    } else if (warp == 0) {
         // loader
         if (lane == 0) {
             uint32_t n = 0;  // rows staged so far
@@ -1540,8 +1635,8 @@ int launch_ring_bwd(int L, int64_t C, const float *params, int w_off, const __nv
     p.units_per_col = (L + kUnitRows - 1) / kUnitRows;
     p.units = C * p.segs * p.units_per_col;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.units, 2 * info.sm_count));
-    cudaFuncSetAttribute(conv32_ring_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmem);
-    conv32_ring_kernel<false, true><<<grid, kRingThreads, kRingSmem, s>>>(p);
+    cudaFuncSetAttribute(conv32_ring_kernel<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmem);
+    conv32_ring_kernel<false, true, false><<<grid, kRingThreads, kRingSmem, s>>>(p);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ISING_OK : nfail(ISING_ECUDA, cudaGetErrorString(e));
 }
@@ -1567,21 +1662,30 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
         const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, want));
         const unsigned gy = (unsigned)std::max<int64_t>(1, std::min<int64_t>({C, 65535, (want + gx - 1) / gx}));
         l1_table_kernel<<<kPatterns * kCh / 256, 256, 0, s>>>(params, w.tz, w.ta);
-        l1_kernel<<<dim3(gx, gy), kL1Threads, 0, s>>>(ch, bd[0], flip, w.ta, w.tz, train ? w.z1 : nullptr, w.a1);
+        // an inference pass of the row-ring kernels forms layer 1 inside the first conv
+        if (train || L % kTileM != 0)
+            l1_kernel<<<dim3(gx, gy), kL1Threads, 0, s>>>(ch, bd[0], flip, w.ta, w.tz, train ? w.z1 : nullptr,
+                                                           w.a1);
     }
     const int off[2][2] = {{kOffW2, kOffB2}, {kOffW3, kOffB3}};
     const __nv_bfloat16 *ins[2] = {w.a1, w.a2};
     float *zs[2] = {train ? w.z2 : nullptr, train ? w.z3 : nullptr};
     if (L % kTileM == 0) {
         // row-ring kernels; the second one also projects onto layer 4's taps
-        cudaFuncSetAttribute(conv32_ring_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(conv32_ring_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kRingSmem);
-        cudaFuncSetAttribute(conv32_ring_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(conv32_ring_kernel<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kRingSmem);
+        cudaFuncSetAttribute(conv32_ring_kernel<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kRingSmem);
         __nv_bfloat16 *outs[2] = {w.a2, train ? w.a3 : nullptr};
         for (int l = 0; l < 2; ++l) {
             RingConv p{};
-            if (!encode_rows(p.tmap, ins[l], L, C)) return nfail(ISING_ECUDA, "cuTensorMapEncodeTiled failed");
+            const bool fused = l == 0 && !train;
+            if (!fused && !encode_rows(p.tmap, ins[l], L, C)) return nfail(ISING_ECUDA, "cuTensorMapEncodeTiled failed");
+            p.ch = ch;
+            p.flip = flip;
+            p.ta = w.ta;
             p.a_in = ins[l];
             p.a_out = outs[l];
             p.z_out = zs[l];
@@ -1595,10 +1699,12 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
             p.units = C * p.segs * p.units_per_col;
             p.withhold = withhold && l == 0;
             const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.units, 2 * info.sm_count));
-            if (l == 0)
-                conv32_ring_kernel<false, false><<<grid, kRingThreads, kRingSmem, s>>>(p);
+            if (fused)
+                conv32_ring_kernel<false, false, true><<<grid, kRingThreads, kRingSmem, s>>>(p);
+            else if (l == 0)
+                conv32_ring_kernel<false, false, false><<<grid, kRingThreads, kRingSmem, s>>>(p);
             else
-                conv32_ring_kernel<true, false><<<grid, kRingThreads, kRingSmem, s>>>(p);
+                conv32_ring_kernel<true, false, false><<<grid, kRingThreads, kRingSmem, s>>>(p);
         }
     } else {
         cudaFuncSetAttribute(conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
