@@ -717,7 +717,7 @@ def time_network(ising, torch, L, C, params, beta, seed, device, stream, reps=10
         "frac": round(alg_bytes / t / 1e9 / hbm_peak, 4), "peak_source": source,
         "tensor": {"achieved": round(conv_flops / t / 1e12, 2), "peak": tensor_peak, "unit": "TFLOP/s",
                    "frac": round(conv_flops / t / 1e12 / tensor_peak, 4), "peak_source": f"bf16 burst, {source}"},
-        "note": "whole forward (5 kernels): algorithmic bytes and tensor-core FLOPs over the CUDA-event time"}
+        "note": "whole inference forward (4 kernels at L a multiple of 128): algorithmic bytes and tensor-core FLOPs over the CUDA-event time"}
     del mv
     return out
 
