@@ -74,6 +74,10 @@ def _load():
         for name in ("oracle_to_planes_int8", "oracle_to_planes_msc4"):
             getattr(lib, name).argtypes = [i64, p, p, p, i64]
             getattr(lib, name).restype = None
+        lib.oracle_to_planes_bits.argtypes = [i64, p, p, p]
+        lib.oracle_from_planes_bits.argtypes = [i64, p, p, p]
+        lib.oracle_to_planes_bits.restype = None
+        lib.oracle_from_planes_bits.restype = None
         for name in ("oracle_from_planes_int8", "oracle_from_planes_msc4"):
             getattr(lib, name).argtypes = [i64, p, p, i64, p]
             getattr(lib, name).restype = None
@@ -198,6 +202,24 @@ def from_planes_msc4(L: int, black: np.ndarray, white: np.ndarray) -> np.ndarray
     w = np.ascontiguousarray(white, dtype=np.uint64)
     s = np.zeros((L, L), dtype=np.int8)
     _load().oracle_from_planes_msc4(L, _ptr(b), _ptr(w), b.shape[1], _ptr(s))
+    return s
+
+
+def to_planes_bits(s: np.ndarray):
+    """The two colour planes in the bit-packed format: (L, L/16) uint8 each."""
+    L = s.shape[0]
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    b = np.zeros((L, L // 16), dtype=np.uint8)
+    w = np.zeros((L, L // 16), dtype=np.uint8)
+    _load().oracle_to_planes_bits(L, _ptr(s), _ptr(b), _ptr(w))
+    return b, w
+
+
+def from_planes_bits(L: int, black: np.ndarray, white: np.ndarray) -> np.ndarray:
+    b = np.ascontiguousarray(black, dtype=np.uint8).reshape(L, L // 16)
+    w = np.ascontiguousarray(white, dtype=np.uint8).reshape(L, L // 16)
+    s = np.zeros((L, L), dtype=np.int8)
+    _load().oracle_from_planes_bits(L, _ptr(b), _ptr(w), _ptr(s))
     return s
 
 

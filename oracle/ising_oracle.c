@@ -335,6 +335,37 @@ void oracle_from_planes_msc4(int64_t L, const uint64_t *black, const uint64_t *w
         oracle_row_from_planes_msc4(L, i, black + i * stride, white + i * stride, s + i * L);
 }
 
+/* ------------------------------------------------------------------------- */
+/* The bit-packed format (an I/O format of the library, not of the paper): a  */
+/* colour plane row of L/2 spins as L/16 bytes, compacted column j at bit j%8 */
+/* of byte j/8, 1 for +1 and 0 for -1; rows dense.                            */
+/* ------------------------------------------------------------------------- */
+void oracle_to_planes_bits(int64_t L, const int8_t *s, uint8_t *black, uint8_t *white)
+{
+    int64_t rb = L / 16;
+    for (int64_t k = 0; k < L * rb; k++) {
+        black[k] = 0;
+        white[k] = 0;
+    }
+    for (int64_t i = 0; i < L; i++)
+        for (int64_t c = 0; c < L; c++) {
+            uint8_t *dst = (colour_of(i, c) == 0 ? black : white) + i * rb;
+            int64_t j = c / 2;
+            if (s[i * L + c] > 0) dst[j / 8] |= (uint8_t)(1u << (j % 8));
+        }
+}
+
+void oracle_from_planes_bits(int64_t L, const uint8_t *black, const uint8_t *white, int8_t *s)
+{
+    int64_t rb = L / 16;
+    for (int64_t i = 0; i < L; i++)
+        for (int64_t c = 0; c < L; c++) {
+            const uint8_t *src = (colour_of(i, c) == 0 ? black : white) + i * rb;
+            int64_t j = c / 2;
+            s[i * L + c] = ((src[j / 8] >> (j % 8)) & 1) ? 1 : -1;
+        }
+}
+
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP
