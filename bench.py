@@ -53,7 +53,7 @@ def parse_args(argv=None):
     p.add_argument("--slabs", type=int, default=4, help="slabs on one GPU for the slab leg / workload")
     p.add_argument("--no-binder", action="store_true", help="skip the Binder-crossing leg")
     p.add_argument("--binder-sweeps", type=int, default=100000)
-    p.add_argument("--workload", choices=["sweep", "pt", "learned", "network", "train", "slabs", "binder"],
+    p.add_argument("--workload", choices=["sweep", "pt", "learned", "network", "train", "slabs", "binder", "host"],
                    default="sweep",
                    help="sweep: the 65536^2 lattice (default); pt / learned: only that leg")
     p.add_argument("--no-learned", action="store_true", help="skip the learned block-proposal leg")
@@ -522,30 +522,55 @@ def rng_probe(ising, torch, L, seed, stream):
 
 
 def run_e2e(ising, torch, args, L, beta, seed, device, stream):
-    """Through the host-buffer entry point: every step copies both planes in
-    from pinned host memory, sweeps once, and copies planes and trace back."""
+    """Through the host-buffer entry points: every step copies the lattice in
+    from pinned host memory, sweeps once, and copies lattice and trace back.
+    The headline uses the bit-packed host format (ising_sweep_host_bits: one
+    bit per spin on the link, converted to and from MSC4 on the device); the
+    same sweep with MSC4 host planes (ising_sweep_host, four bits per spin on
+    the link) is reported beside it."""
     steps = max(1, args.e2e_steps)
     dev = ising.Lattice(L, "msc4", device=device)
     ising.ising_init_lattice(dev, ising.ISING_INIT_RANDOM, seed, stream)
+    nb = ising.ising_bits_bytes(L)
+    stage = torch.empty(2 * nb, dtype=torch.uint8, device=device)
+    ising.ising_msc4_to_bits(dev, stage[:nb], stage[nb:], stream)
     torch.cuda.synchronize()
+    bb = stage[:nb].cpu().pin_memory()
+    bw = stage[nb:].cpu().pin_memory()
     hb = dev.black.cpu().pin_memory()
     hw = dev.white.cpu().pin_memory()
     tr_dev = torch.zeros((1, 2), dtype=torch.int64, device=device)
     tr_host = torch.zeros((1, 2), dtype=torch.int64).pin_memory()
-    ising.ising_sweep_host(dev, hb.data_ptr(), hw.data_ptr(), beta, 1, seed, 0, tr_dev, tr_host.data_ptr(), stream)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        e0.record(stream)
-        for k in range(steps):
-            ising.ising_sweep_host(dev, hb.data_ptr(), hw.data_ptr(), beta, 1, seed, 1 + k, tr_dev,
-                                   tr_host.data_ptr(), stream)
-        e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+
+    def bits_step(k):
+        ising.ising_sweep_host_bits(dev, bb, bw, stage, beta, 1, seed, k, tr_dev, tr_host.data_ptr(), stream)
+
+    def msc4_step(k):
+        ising.ising_sweep_host(dev, hb.data_ptr(), hw.data_ptr(), beta, 1, seed, k, tr_dev, tr_host.data_ptr(),
+                               stream)
+
+    def timed(step):
+        step(0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for k in range(steps):
+                step(1 + k)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    ms = timed(bits_step)
+    ms4 = timed(msc4_step)
     plane = dev.row_bytes * L
-    return {"value": round(L * L * steps / (ms * 1e6), 3), "unit": UNIT, "h2d_bytes_per_step": 2 * plane,
-            "d2h_bytes_per_step": 2 * plane + 16, "steps": steps, "ms_per_step": round(ms / steps, 3)}
+    return {"value": round(L * L * steps / (ms * 1e6), 3), "unit": UNIT, "h2d_bytes_per_step": 2 * nb,
+            "d2h_bytes_per_step": 2 * nb + 16, "steps": steps, "ms_per_step": round(ms / steps, 3),
+            "host_format": "bit-packed planes, 1 bit per spin (ising_sweep_host_bits)",
+            "msc4_host": {"value": round(L * L * steps / (ms4 * 1e6), 3), "unit": UNIT,
+                          "h2d_bytes_per_step": 2 * plane, "d2h_bytes_per_step": 2 * plane + 16,
+                          "ms_per_step": round(ms4 / steps, 3),
+                          "host_format": "MSC4 planes, 4 bits per spin (ising_sweep_host)"}}
 
 
 def run_pt_batch(ising, torch, args, device, stream):
@@ -844,6 +869,20 @@ def main(argv=None):
         res = run_pt_only(args, world, rank, local)
     elif args.workload == "slabs":
         res = run_slabs(args, world, rank, local)
+    elif args.workload == "host":
+        # the host-buffer legs alone: one sweep per step of the L^2 lattice
+        # held in pinned host memory (bit-packed, and MSC4 beside it)
+        import torch
+
+        import paper_1906_06297_gb300 as ising
+
+        ising.build()
+        torch.cuda.set_device(local)
+        device = torch.device("cuda", local)
+        e2e = run_e2e(ising, torch, args, args.L, args.beta, args.seed, device, torch.cuda.Stream(device=device))
+        res = {"metric": METRIC, "value": e2e["value"], "unit": UNIT, "impl": "ours",
+               "config": {"workload": f"{args.L}x{args.L} MSC4 lattice in host memory, one sweep per step",
+                          "beta": args.beta}, "e2e": e2e}
     elif args.workload == "binder":
         import torch
 

@@ -114,13 +114,45 @@ ISING_API int ising_sweep(const ising_lattice_t *lat, double beta, int64_t n_swe
  * the trace (if trace_host is not NULL; trace_dev is then required as device
  * staging of n_sweeps x 2 int64) back.  Pinned host memory makes the copies
  * asynchronous; the call does not synchronise the stream.  One sweep of an
- * MSC4 lattice runs in row bands on two more streams of the library's own so
- * that the copies overlap the half-sweeps; the work is still ordered on
- * `stream` (it starts after the work queued on it and the stream waits for
- * all of it), and the result is that of ising_sweep. */
+ * MSC4 lattice runs in 16 to 64 row bands on two more streams of the
+ * library's own: plane bands are copied in in the order the half-sweeps need
+ * them and each is copied out as soon as it is final, so that both directions
+ * of the host link are busy while the bands are swept; the work is still
+ * ordered on `stream` (it starts after the work queued on it and the stream
+ * waits for all of it), and the result is that of ising_sweep. */
 ISING_API int ising_sweep_host(const ising_lattice_t *dev, void *black_host, void *white_host, double beta,
                                int64_t n_sweeps, uint64_t seed, uint64_t sweep_offset, int64_t *trace_dev,
                                int64_t *trace_host, ising_stream_t stream);
+
+/* Bit-packed format of an MSC4 lattice's colour planes (an I/O format, not
+ * in the paper): L rows of L/2 bits, L/16 bytes per row, rows dense;
+ * compacted column j of a row is bit j % 8 of the row's byte j / 8, 1 for an
+ * up spin and 0 for a down spin.  These are the MSC4 plane's spins in the
+ * same order at one bit each instead of four (Sec. 3.3 spends four bits per
+ * spin for the bit-parallel neighbour sums, which storage and transfers do not
+ * need), so a lattice crosses the host link in a quarter of the bytes.
+ * L % 64 == 0.  *bytes_per_plane = L * L / 16. */
+ISING_API int ising_bits_bytes(int64_t L, size_t *bytes_per_plane);
+
+/* MSC4 device lattice -> bit planes in device memory (ising_bits_bytes each,
+ * 4-byte aligned), and back.  Asynchronous on `stream`. */
+ISING_API int ising_msc4_to_bits(const ising_lattice_t *msc4, void *black_bits, void *white_bits,
+                                 ising_stream_t stream);
+ISING_API int ising_bits_to_msc4(const void *black_bits, const void *white_bits, const ising_lattice_t *msc4,
+                                 ising_stream_t stream);
+
+/* ising_sweep_host for a lattice held in host memory in the bit-packed
+ * format: black_host / white_host are bit planes (4-byte aligned; pinned for
+ * asynchronous copies), `dev` an MSC4 device lattice of the same L that holds
+ * the state during the call, stage_dev caller-owned device scratch of
+ * 2 x ising_bits_bytes (16-byte aligned).  One sweep runs in row bands as in
+ * ising_sweep_host, each band converted on the device after its copy in and
+ * before its copy out; n_sweeps != 1 copies and converts whole planes.  The
+ * result equals ising_sweep on the unpacked lattice, converted back. */
+ISING_API int ising_sweep_host_bits(const ising_lattice_t *dev, void *black_host, void *white_host,
+                                    void *stage_dev, double beta, int64_t n_sweeps, uint64_t seed,
+                                    uint64_t sweep_offset, int64_t *trace_dev, int64_t *trace_host,
+                                    ising_stream_t stream);
 
 /* out_dev[0..1] = {sum of spins, sum over bonds s_i s_j}: magnetisation
  * M = out[0], energy E = -out[1] (Eq. 1 with J = 1). */

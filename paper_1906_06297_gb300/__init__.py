@@ -83,6 +83,10 @@ def _load():
             "ising_half_sweep": [LP, dbl, i32, u64, u64, P, P],
             "ising_sweep": [LP, dbl, i64, u64, u64, P, P],
             "ising_sweep_host": [LP, P, P, dbl, i64, u64, u64, P, P, P],
+            "ising_bits_bytes": [i64, P],
+            "ising_msc4_to_bits": [LP, P, P, P],
+            "ising_bits_to_msc4": [P, P, LP, P],
+            "ising_sweep_host_bits": [LP, P, P, P, dbl, i64, u64, u64, P, P, P],
             "ising_observables": [LP, P, P],
             "ising_pack": [LP, LP, P],
             "ising_unpack": [LP, LP, P],
@@ -211,6 +215,30 @@ def ising_sweep_host(dev_lat, black_host, white_host, beta: float, n_sweeps: int
     _check(_load().ising_sweep_host(ctypes.byref(_struct(dev_lat)), _addr(black_host), _addr(white_host),
                                     float(beta), n_sweeps, seed, sweep_offset, _addr(trace_dev), _addr(trace_host),
                                     _stream(stream)), "ising_sweep_host")
+
+
+def ising_bits_bytes(L: int) -> int:
+    n = ctypes.c_size_t()
+    _check(_load().ising_bits_bytes(L, ctypes.byref(n)), "ising_bits_bytes")
+    return n.value
+
+
+def ising_msc4_to_bits(msc4, black_bits, white_bits, stream=None):
+    _check(_load().ising_msc4_to_bits(ctypes.byref(_struct(msc4)), _addr(black_bits), _addr(white_bits),
+                                      _stream(stream)), "ising_msc4_to_bits")
+
+
+def ising_bits_to_msc4(black_bits, white_bits, msc4, stream=None):
+    _check(_load().ising_bits_to_msc4(_addr(black_bits), _addr(white_bits), ctypes.byref(_struct(msc4)),
+                                      _stream(stream)), "ising_bits_to_msc4")
+
+
+def ising_sweep_host_bits(dev_lat, black_host, white_host, stage_dev, beta: float, n_sweeps: int, seed: int,
+                          sweep_offset: int = 0, trace_dev=None, trace_host=None, stream=None):
+    _check(_load().ising_sweep_host_bits(ctypes.byref(_struct(dev_lat)), _addr(black_host), _addr(white_host),
+                                         _addr(stage_dev), float(beta), n_sweeps, seed, sweep_offset,
+                                         _addr(trace_dev), _addr(trace_host), _stream(stream)),
+           "ising_sweep_host_bits")
 
 
 def ising_observables(lat, out, stream=None):

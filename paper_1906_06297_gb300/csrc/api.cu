@@ -43,8 +43,10 @@ int cuda_fail(cudaError_t e, const char *what)
 
 struct DeviceCache {
     std::mutex mu;
+    std::mutex host_mu;  // held while ising_sweep_host enqueues its bands
     int sm_count[64] = {};
     cudaStream_t aux[64][2] = {};  // compute and copy-out streams of ising_sweep_host, made on first use
+    cudaEvent_t *host_ev[64] = {};  // the events of ising_sweep_host's bands, made on first use
 };
 DeviceCache g_dev;
 
@@ -568,22 +570,64 @@ ISING_API int ising_slab_sweep(const ising_slab_t *slabs, int32_t n, double beta
 namespace {
 
 // One sweep of an MSC4 lattice held in host memory, in K row bands so that
-// the copies overlap the half-sweeps and each other.  Stream `s` copies the
-// bands in (the last band first, then 0 .. K-2), the compute stream runs
-// black band 0, black 1, then black k+1 before white k for k = 1 .. K-2, then
-// white K-1 and white 0, and the copy-out stream returns band k as soon as
-// white k is done.  Black band k needs the white rows next to it unchanged
-// (bands k-1 and k+1 are whited only after black k+1 resp. at the end: white
-// 0 comes last because black K-1 reads white row 0), white band k needs black
-// bands k-1 .. k+1 done; events carry these orders across the streams, and
-// `s` finally waits for the copy-out stream.
-int sweep_host_banded(const ising_lattice_t *dev, char *host[2], size_t row, const Accept &acc, const RoundKeys &rk,
-                      uint64_t t, int64_t *trace_dev, int64_t *trace_host, cudaStream_t s)
+// the copies overlap the half-sweeps and each other (the host link, not the
+// sweep, bounds this path).  The compute stream runs black band 0, black 1,
+// then black k before white k-1 for k = 2 .. K-1, then white K-1 and white 0:
+// black band k reads the white rows next to it unchanged (white k-1 runs after
+// black k, white 0 last because black K-1 reads white row 0) and white band k
+// needs black bands k-1 .. k+1 done.  Stream `s` copies plane bands in the
+// order black bands first need them (white K-1, 0, 1, black 0, then white k+1
+// and black k), so black k waits only for the copy of its own black band; the
+// copy-out stream returns each plane band in compute order as soon as it is
+// final -- a black band right after its black half-sweep -- so that both link
+// directions stay busy from the first band to the last.  `s` finally waits for
+// the copy-out stream.
+//
+// Host formats: with stage == nullptr the host planes are MSC4 rows of `hrow`
+// bytes copied straight into the lattice; otherwise they are bit-packed rows
+// of `hrow` = L/16 bytes, copied into `stage` (black's plane, then white's)
+// and converted to and from MSC4 on the compute stream around each band's
+// half-sweeps.
+constexpr int kMaxHostBands = 64;
+
+// Bands of about 16 MiB per host plane: 16 .. 64 bands, and at least 8 rows each.
+int host_band_count(int64_t L, size_t hrow)
+{
+    const int64_t by_bytes = (int64_t)(((size_t)L * hrow) >> 24);
+    const int64_t k = std::min<int64_t>(std::max<int64_t>(by_bytes, 16), kMaxHostBands);
+    return (int)std::min<int64_t>(k, L / 8);
+}
+
+// The events of the banded host path, per device, made on first use; the
+// caller holds g_dev.host_mu while it enqueues, so no two calls interleave their
+// records of them (a wait refers to the record made before it is enqueued).
+constexpr int kHostEvents = 3 * kMaxHostBands + 2;
+
+int host_events(int dev, cudaEvent_t **ev)
+{
+    if (g_dev.host_ev[dev] == nullptr) {
+        cudaEvent_t *e = new cudaEvent_t[kHostEvents];
+        for (int i = 0; i < kHostEvents; ++i) {
+            cudaError_t r = cudaEventCreateWithFlags(&e[i], cudaEventDisableTiming);
+            if (r != cudaSuccess) {
+                for (int j = 0; j < i; ++j) cudaEventDestroy(e[j]);
+                delete[] e;
+                return cuda_fail(r, "event create");
+            }
+        }
+        g_dev.host_ev[dev] = e;
+    }
+    *ev = g_dev.host_ev[dev];
+    return ISING_OK;
+}
+
+int sweep_host_banded(const ising_lattice_t *dev, char *host[2], char *stage, size_t hrow, const Accept &acc,
+                      const RoundKeys &rk, uint64_t t, int64_t *trace_dev, int64_t *trace_host, cudaStream_t s)
 {
     const int64_t L = dev->L;
-    const int K = (int)std::min<int64_t>(16, L / 8);
-    const int64_t per = (L + K - 1) / K;
-    int64_t b0[16], br[16];
+    const int64_t per = (L + host_band_count(L, hrow) - 1) / host_band_count(L, hrow);
+    const int K = (int)((L + per - 1) / per);  // no empty band
+    int64_t b0[kMaxHostBands], br[kMaxHostBands];
     for (int k = 0; k < K; ++k) {
         b0[k] = k * per;
         br[k] = std::min<int64_t>(per, L - b0[k]);
@@ -591,50 +635,87 @@ int sweep_host_banded(const ising_lattice_t *dev, char *host[2], size_t row, con
     cudaStream_t cmp, out;
     int rc = aux_streams(&cmp, &out);
     if (rc) return rc;
-    cudaEvent_t start, end, ev_in[16], ev_w[16];
-    cudaEvent_t *all[2] = {&start, &end};
-    auto make = [](cudaEvent_t *e) { return cudaEventCreateWithFlags(e, cudaEventDisableTiming); };
-    cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = make(all[i]);
-    for (int k = 0; k < K && e == cudaSuccess; ++k) {
-        e = make(&ev_in[k]);
-        if (e == cudaSuccess) e = make(&ev_w[k]);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "event create");
-    void *devp[2] = {dev->black, dev->white};
+    int devi = 0;
+    cudaError_t e = cudaGetDevice(&devi);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lock(g_dev.host_mu);
+    cudaEvent_t *ev = nullptr;
+    rc = host_events(devi, &ev);
+    if (rc) return rc;
+    cudaEvent_t start = ev[0], end = ev[1], *ev_in = ev + 2, *ev_b = ev_in + K, *ev_w = ev_b + K;
+    const bool bits = stage != nullptr;
+    char *devp[2] = {(char *)dev->black, (char *)dev->white};
+    char *stg[2] = {stage, bits ? stage + (size_t)L * hrow : nullptr};
     const size_t pitch = (size_t)dev->row_stride_bytes;
-    auto copy = [&](int k, bool in, cudaStream_t st) {
-        cudaError_t r = cudaSuccess;
-        for (int c = 0; c < 2 && r == cudaSuccess; ++c) {
-            char *d = (char *)devp[c] + b0[k] * pitch;
-            char *h = host[c] + b0[k] * row;
-            r = in ? cudaMemcpy2DAsync(d, pitch, h, row, row, (size_t)br[k], cudaMemcpyHostToDevice, st)
-                   : cudaMemcpy2DAsync(h, row, d, pitch, row, (size_t)br[k], cudaMemcpyDeviceToHost, st);
+    const int64_t stride_words = dev->row_stride_bytes / 8;
+    auto copy = [&](int c, int k, bool in, cudaStream_t st) {
+        char *d = devp[c] + b0[k] * pitch, *h = host[c] + b0[k] * hrow;
+        if (bits) {
+            char *g = stg[c] + b0[k] * hrow;
+            return in ? cudaMemcpyAsync(g, h, (size_t)br[k] * hrow, cudaMemcpyHostToDevice, st)
+                      : cudaMemcpyAsync(h, g, (size_t)br[k] * hrow, cudaMemcpyDeviceToHost, st);
         }
-        return r;
+        return in ? cudaMemcpy2DAsync(d, pitch, h, hrow, hrow, (size_t)br[k], cudaMemcpyHostToDevice, st)
+                  : cudaMemcpy2DAsync(h, hrow, d, pitch, hrow, (size_t)br[k], cudaMemcpyDeviceToHost, st);
+    };
+    // bits mode: staged band -> MSC4 band (after its copy in) and back (before its copy out)
+    auto unpack = [&](int c, int k) {
+        if (!bits) return cudaSuccess;
+        return bits_to_msc4((const uint32_t *)(stg[c] + b0[k] * hrow), (uint64_t *)(devp[c] + b0[k] * pitch),
+                            stride_words, L, br[k], cmp);
+    };
+    auto pack = [&](int c, int k) {
+        if (!bits) return cudaSuccess;
+        return msc4_to_bits((const uint64_t *)(devp[c] + b0[k] * pitch), stride_words,
+                            (uint32_t *)(stg[c] + b0[k] * hrow), L, br[k], cmp);
     };
     e = cudaEventRecord(start, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cmp, start, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(out, start, 0);
-    for (int i = 0; i < K && e == cudaSuccess; ++i) {
-        const int k = (i + K - 1) % K;  // K-1, 0, 1, .., K-2
-        e = copy(k, true, s);
-        if (e == cudaSuccess) e = cudaEventRecord(ev_in[k], s);
+    // copy-in order: white K-1, 0, 1, black 0, then white k+1 and black k
+    // (k = 1 .. K-2), black K-1; ev_in[k] follows black band k, after which
+    // every plane band that black k reads is in
+    auto in_black = [&](int k) {
+        cudaError_t r = copy(0, k, true, s);
+        return r == cudaSuccess ? cudaEventRecord(ev_in[k], s) : r;
+    };
+    if (e == cudaSuccess) e = copy(1, K - 1, true, s);
+    if (e == cudaSuccess) e = copy(1, 0, true, s);
+    if (e == cudaSuccess) e = copy(1, 1, true, s);
+    if (e == cudaSuccess) e = in_black(0);
+    for (int k = 1; k + 1 < K && e == cudaSuccess; ++k) {
+        if (k + 1 < K - 1) e = copy(1, k + 1, true, s);
+        if (e == cudaSuccess) e = in_black(k);
     }
+    if (e == cudaSuccess) e = in_black(K - 1);
     if (e == cudaSuccess && trace_dev) e = cudaMemsetAsync(trace_dev, 0, 2 * sizeof(int64_t), cmp);
     if (e != cudaSuccess) return cuda_fail(e, "host sweep: copy in");
+    // compute, each band followed by its copy-out on `out`; in bits mode the
+    // white bands are unpacked in their copy-in order (K-1, 0, 1, .., K-2) as
+    // far as black k needs them: the first min(k + 3, K) of that order
+    int unpacked = 0;
     auto black = [&](int k) {
-        for (int d = -1; d <= 1; ++d) {
-            cudaError_t r = cudaStreamWaitEvent(cmp, ev_in[(k + d + K) % K], 0);
-            if (r != cudaSuccess) return cuda_fail(r, "host sweep: wait");
-        }
-        return band_half_sweep_impl(dev, acc, rk, 0, t, b0[k], br[k], nullptr, cmp);
+        cudaError_t r = cudaStreamWaitEvent(cmp, ev_in[k], 0);
+        for (; r == cudaSuccess && unpacked < std::min(k + 3, K); ++unpacked)
+            r = unpack(1, unpacked == 0 ? K - 1 : unpacked - 1);
+        if (r == cudaSuccess) r = unpack(0, k);
+        if (r != cudaSuccess) return cuda_fail(r, "host sweep: unpack");
+        int x = band_half_sweep_impl(dev, acc, rk, 0, t, b0[k], br[k], nullptr, cmp);
+        if (x) return x;
+        r = pack(0, k);
+        if (r == cudaSuccess) r = cudaEventRecord(ev_b[k], cmp);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(out, ev_b[k], 0);
+        if (r == cudaSuccess) r = copy(0, k, false, out);
+        return r == cudaSuccess ? ISING_OK : cuda_fail(r, "host sweep: copy out");
     };
     auto white = [&](int k) {
-        int r = band_half_sweep_impl(dev, acc, rk, 1, t, b0[k], br[k], trace_dev, cmp);
-        if (r) return r;
-        cudaError_t x = cudaEventRecord(ev_w[k], cmp);
-        return x == cudaSuccess ? ISING_OK : cuda_fail(x, "host sweep: event");
+        int x = band_half_sweep_impl(dev, acc, rk, 1, t, b0[k], br[k], trace_dev, cmp);
+        if (x) return x;
+        cudaError_t r = pack(1, k);
+        if (r == cudaSuccess) r = cudaEventRecord(ev_w[k], cmp);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(out, ev_w[k], 0);
+        if (r == cudaSuccess) r = copy(1, k, false, out);
+        return r == cudaSuccess ? ISING_OK : cuda_fail(r, "host sweep: copy out");
     };
     rc = black(0);
     if (!rc) rc = black(1);
@@ -645,21 +726,10 @@ int sweep_host_banded(const ising_lattice_t *dev, char *host[2], size_t row, con
     if (!rc) rc = white(K - 1);
     if (!rc) rc = white(0);
     if (rc) return rc;
-    for (int i = 0; i < K && e == cudaSuccess; ++i) {
-        const int k = (i + 1) % K;  // 1, .., K-1, 0
-        e = cudaStreamWaitEvent(out, ev_w[k], 0);
-        if (e == cudaSuccess) e = copy(k, false, out);
-    }
-    if (e == cudaSuccess && trace_host != nullptr)
+    if (trace_host != nullptr)
         e = cudaMemcpyAsync(trace_host, trace_dev, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, out);
     if (e == cudaSuccess) e = cudaEventRecord(end, out);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, end, 0);
-    cudaEventDestroy(start);
-    cudaEventDestroy(end);
-    for (int k = 0; k < K; ++k) {
-        cudaEventDestroy(ev_in[k]);
-        cudaEventDestroy(ev_w[k]);
-    }
     return e == cudaSuccess ? ISING_OK : cuda_fail(e, "host sweep: copy out");
 }
 
@@ -687,7 +757,8 @@ ISING_API int ising_sweep_host(const ising_lattice_t *dev, void *black_host, voi
             if (rc) return rc;
         }
         char *host[2] = {(char *)black_host, (char *)white_host};
-        return sweep_host_banded(dev, host, row, acc, make_round_keys(seed), sweep_offset, trace_dev, trace_host, s);
+        return sweep_host_banded(dev, host, nullptr, row, acc, make_round_keys(seed), sweep_offset, trace_dev,
+                                 trace_host, s);
     }
     void *host[2] = {black_host, white_host};
     void *devp[2] = {dev->black, dev->white};
@@ -701,6 +772,118 @@ ISING_API int ising_sweep_host(const ising_lattice_t *dev, void *black_host, voi
     for (int c = 0; c < 2; ++c) {
         cudaError_t e = cudaMemcpy2DAsync(host[c], row, devp[c], (size_t)dev->row_stride_bytes, row, (size_t)dev->L,
                                           cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    }
+    if (trace_host != nullptr && n_sweeps > 0) {
+        cudaError_t e = cudaMemcpyAsync(trace_host, trace_dev, (size_t)n_sweeps * 2 * sizeof(int64_t),
+                                        cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "trace copy");
+    }
+    return ISING_OK;
+}
+
+namespace {
+
+int check_msc4_bits(const ising_lattice_t *lat, const void *black_bits, const void *white_bits, size_t *plane_bits)
+{
+    int rc = check_lattice(lat);
+    if (rc) return rc;
+    if (lat->layout != ISING_MSC4) return fail(ISING_EINVAL, "the bit-packed format converts MSC4 lattices");
+    rc = ising_bits_bytes(lat->L, plane_bits);
+    if (rc) return rc;
+    if (black_bits == nullptr || white_bits == nullptr) return fail(ISING_EINVAL, "bit planes are NULL");
+    if (((uintptr_t)black_bits | (uintptr_t)white_bits) % 4 != 0)
+        return fail(ISING_EINVAL, "bit planes must be 4-byte aligned");
+    return ISING_OK;
+}
+
+}  // namespace
+
+ISING_API int ising_bits_bytes(int64_t L, size_t *bytes_per_plane)
+{
+    if (bytes_per_plane == nullptr) return fail(ISING_EINVAL, "bytes_per_plane is NULL");
+    size_t row = 0;
+    int rc = row_bytes_of(L, ISING_MSC4, &row);  // L even, L % 64 == 0
+    if (rc) return rc;
+    *bytes_per_plane = (size_t)L * (size_t)(L / 16);
+    return ISING_OK;
+}
+
+ISING_API int ising_msc4_to_bits(const ising_lattice_t *msc4, void *black_bits, void *white_bits,
+                                 ising_stream_t stream)
+{
+    size_t nb = 0;
+    int rc = check_msc4_bits(msc4, black_bits, white_bits, &nb);
+    if (rc) return rc;
+    rc = check_device_range(black_bits, nb, "black bits");
+    if (!rc) rc = check_device_range(white_bits, nb, "white bits");
+    if (rc) return rc;
+    const int64_t sw = msc4->row_stride_bytes / 8;
+    cudaError_t e = msc4_to_bits((const uint64_t *)msc4->black, sw, (uint32_t *)black_bits, msc4->L, msc4->L,
+                                 (cudaStream_t)stream);
+    if (e == cudaSuccess)
+        e = msc4_to_bits((const uint64_t *)msc4->white, sw, (uint32_t *)white_bits, msc4->L, msc4->L,
+                         (cudaStream_t)stream);
+    return e == cudaSuccess ? ISING_OK : cuda_fail(e, "to-bits launch");
+}
+
+ISING_API int ising_bits_to_msc4(const void *black_bits, const void *white_bits, const ising_lattice_t *msc4,
+                                 ising_stream_t stream)
+{
+    size_t nb = 0;
+    int rc = check_msc4_bits(msc4, black_bits, white_bits, &nb);
+    if (rc) return rc;
+    rc = check_device_range(black_bits, nb, "black bits");
+    if (!rc) rc = check_device_range(white_bits, nb, "white bits");
+    if (rc) return rc;
+    const int64_t sw = msc4->row_stride_bytes / 8;
+    cudaError_t e = bits_to_msc4((const uint32_t *)black_bits, (uint64_t *)msc4->black, sw, msc4->L, msc4->L,
+                                 (cudaStream_t)stream);
+    if (e == cudaSuccess)
+        e = bits_to_msc4((const uint32_t *)white_bits, (uint64_t *)msc4->white, sw, msc4->L, msc4->L,
+                         (cudaStream_t)stream);
+    return e == cudaSuccess ? ISING_OK : cuda_fail(e, "from-bits launch");
+}
+
+ISING_API int ising_sweep_host_bits(const ising_lattice_t *dev, void *black_host, void *white_host, void *stage_dev,
+                                    double beta, int64_t n_sweeps, uint64_t seed, uint64_t sweep_offset,
+                                    int64_t *trace_dev, int64_t *trace_host, ising_stream_t stream)
+{
+    size_t nb = 0;
+    int rc = check_msc4_bits(dev, black_host, white_host, &nb);
+    if (rc) return rc;
+    if (stage_dev == nullptr || (uintptr_t)stage_dev % 16 != 0)
+        return fail(ISING_EINVAL, "stage_dev must be a 16-byte aligned device buffer");
+    rc = check_device_range(stage_dev, 2 * nb, "stage");
+    if (rc) return rc;
+    if (n_sweeps < 0) return fail(ISING_EINVAL, "n_sweeps = %lld < 0", (long long)n_sweeps);
+    if (trace_host != nullptr && trace_dev == nullptr)
+        return fail(ISING_EINVAL, "trace_host needs trace_dev as device staging");
+    if (trace_dev != nullptr && n_sweeps > 0) {
+        rc = check_device_range(trace_dev, (size_t)n_sweeps * 2 * sizeof(int64_t), "trace");
+        if (rc) return rc;
+    }
+    Accept acc;
+    uint64_t T[5];
+    rc = build_accept(beta, &acc, T);
+    if (rc) return rc;
+    const size_t hrow = (size_t)(dev->L / 16);
+    cudaStream_t s = (cudaStream_t)stream;
+    char *host[2] = {(char *)black_host, (char *)white_host};
+    char *stg[2] = {(char *)stage_dev, (char *)stage_dev + nb};
+    if (n_sweeps == 1)
+        return sweep_host_banded(dev, host, (char *)stage_dev, hrow, acc, make_round_keys(seed), sweep_offset,
+                                 trace_dev, trace_host, s);
+    for (int c = 0; c < 2; ++c) {
+        cudaError_t e = cudaMemcpyAsync(stg[c], host[c], nb, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    }
+    rc = ising_bits_to_msc4(stg[0], stg[1], dev, stream);
+    if (!rc) rc = ising_sweep(dev, beta, n_sweeps, seed, sweep_offset, trace_dev, stream);
+    if (!rc) rc = ising_msc4_to_bits(dev, stg[0], stg[1], stream);
+    if (rc) return rc;
+    for (int c = 0; c < 2; ++c) {
+        cudaError_t e = cudaMemcpyAsync(host[c], stg[c], nb, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
     }
     if (trace_host != nullptr && n_sweeps > 0) {

@@ -119,6 +119,27 @@ struct Int8SweepParams {
 
 constexpr uint32_t kNibbleLsb = 0x11111111u;
 
+// The 16 spins of an MSC4 word as 16 bits (bit k = the low bit of nibble k,
+// 1 for an up spin) and back: the bit-packed format holds a plane row's spins
+// in the same order at one bit each.
+__device__ __forceinline__ uint32_t msc4_word_to_bits(uint64_t w)
+{
+    uint64_t v = w & 0x1111111111111111ull;
+    v = (v | (v >> 3)) & 0x0303030303030303ull;
+    v = (v | (v >> 6)) & 0x000F000F000F000Full;
+    v = (v | (v >> 12)) & 0x000000FF000000FFull;
+    return (uint32_t)((v | (v >> 24)) & 0xFFFFull);
+}
+
+__device__ __forceinline__ uint64_t bits_to_msc4_word(uint32_t x)
+{
+    uint64_t v = x & 0xFFFFull;
+    v = (v | (v << 24)) & 0x000000FF000000FFull;
+    v = (v | (v << 12)) & 0x000F000F000F000Full;
+    v = (v | (v << 6)) & 0x0303030303030303ull;
+    return (v | (v << 3)) & 0x1111111111111111ull;
+}
+
 // ---------------------------------------------------------------------------
 // Block-wide reduction of two int64 partial sums and one atomic per block.
 // ---------------------------------------------------------------------------

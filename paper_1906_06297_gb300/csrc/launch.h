@@ -33,6 +33,12 @@ cudaError_t msc4_pack(const int8_t *src, int64_t src_stride, uint64_t *dst, int6
                       int64_t L, cudaStream_t s);
 cudaError_t msc4_unpack(const uint64_t *src, int64_t src_stride_words, int8_t *dst, int64_t dst_stride,
                         int64_t L, cudaStream_t s);
+// `rows` rows of an MSC4 plane (row stride in words) <-> the same rows in the
+// bit-packed format (L/16 bytes per row, dense); L % 64 == 0.
+cudaError_t msc4_to_bits(const uint64_t *plane, int64_t stride_words, uint32_t *bits, int64_t L, int64_t rows,
+                         cudaStream_t s);
+cudaError_t bits_to_msc4(const uint32_t *bits, uint64_t *plane, int64_t stride_words, int64_t L, int64_t rows,
+                         cudaStream_t s);
 
 // One int8 per spin.
 cudaError_t int8_init(int8_t *plane, int colour, int64_t L, int64_t stride, int mode, uint64_t seed,

@@ -655,16 +655,6 @@ __device__ __forceinline__ int ring_row(const RingConv &p, int64_t c, int r)
     return y >= L ? y - L : y;
 }
 
-// Bit t of the result is the lowest bit of nibble t of w.
-__device__ __forceinline__ uint32_t nibble_compress(uint64_t w)
-{
-    uint64_t v = w & 0x1111111111111111ull;
-    v = (v | (v >> 3)) & 0x0303030303030303ull;
-    v = (v | (v >> 6)) & 0x000F000F000F000Full;
-    v = (v | (v >> 12)) & 0x000000FF000000FFull;
-    return (uint32_t)((v | (v >> 24)) & 0xFFFFull);
-}
-
 // Bit t of x (16 bits) moved to bit 2t.
 __device__ __forceinline__ uint32_t bit_spread(uint32_t x)
 {
@@ -680,7 +670,7 @@ __device__ __forceinline__ uint32_t bit_spread(uint32_t x)
 __device__ __forceinline__ uint32_t spin_chunk(const Chains &ch, int64_t c, int r, int b, int flip)
 {
     const int64_t at = (c * ch.L + r) * (int64_t)ch.wpr + b;
-    const uint32_t kb = bit_spread(nibble_compress(ch.black[at])), kw = bit_spread(nibble_compress(ch.white[at]));
+    const uint32_t kb = bit_spread(msc4_word_to_bits(ch.black[at])), kw = bit_spread(msc4_word_to_bits(ch.white[at]));
     uint32_t v = (r & 1) ? (kw | (kb << 1)) : (kb | (kw << 1));
     if (flip >= 0) {
         const int nb = ch.L / kBlk, by = flip / nb, bx = flip - by * nb;

@@ -32,6 +32,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
+#include <cstdint>
 #include <mutex>
 
 #include "common.cuh"
@@ -419,6 +421,55 @@ cudaError_t msc4_unpack(const uint64_t *src, int64_t src_stride_words, int8_t *d
 {
     const int64_t n = L * (L / 32);
     msc4_unpack_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, src_stride_words, dst, dst_stride, L);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// MSC4 plane rows <-> the bit-packed format (one bit per spin, L/16 bytes per
+// row, dense rows): a thread converts two words (32 spins) <-> one uint32;
+// blockIdx.x covers (row, 256-pair chunk of the row).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) msc4_to_bits_kernel(const uint64_t *__restrict__ plane,
+                                                           int64_t stride_words, uint32_t *__restrict__ bits,
+                                                           int64_t pairs, unsigned chunks)
+{
+    const unsigned r = blockIdx.x / chunks;
+    const int64_t p = (int64_t)(blockIdx.x - r * chunks) * 256 + threadIdx.x;
+    if (p >= pairs) return;
+    const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(plane + (int64_t)r * stride_words + 2 * p);
+    bits[(int64_t)r * pairs + p] = msc4_word_to_bits(w.x) | (msc4_word_to_bits(w.y) << 16);
+}
+
+__global__ void __launch_bounds__(256) bits_to_msc4_kernel(const uint32_t *__restrict__ bits, uint64_t *__restrict__ plane,
+                                                           int64_t stride_words, int64_t pairs, unsigned chunks)
+{
+    const unsigned r = blockIdx.x / chunks;
+    const int64_t p = (int64_t)(blockIdx.x - r * chunks) * 256 + threadIdx.x;
+    if (p >= pairs) return;
+    const uint32_t b = bits[(int64_t)r * pairs + p];
+    *reinterpret_cast<ulonglong2 *>(plane + (int64_t)r * stride_words + 2 * p) =
+        make_ulonglong2(bits_to_msc4_word(b & 0xFFFFu), bits_to_msc4_word(b >> 16));
+}
+
+cudaError_t msc4_to_bits(const uint64_t *plane, int64_t stride_words, uint32_t *bits, int64_t L, int64_t rows,
+                         cudaStream_t s)
+{
+    if (rows <= 0) return cudaSuccess;
+    const int64_t pairs = L / 64;
+    const unsigned chunks = (unsigned)((pairs + 255) / 256);
+    if (rows * (int64_t)chunks > INT32_MAX) return cudaErrorInvalidConfiguration;
+    msc4_to_bits_kernel<<<(unsigned)(rows * chunks), 256, 0, s>>>(plane, stride_words, bits, pairs, chunks);
+    return cudaGetLastError();
+}
+
+cudaError_t bits_to_msc4(const uint32_t *bits, uint64_t *plane, int64_t stride_words, int64_t L, int64_t rows,
+                         cudaStream_t s)
+{
+    if (rows <= 0) return cudaSuccess;
+    const int64_t pairs = L / 64;
+    const unsigned chunks = (unsigned)((pairs + 255) / 256);
+    if (rows * (int64_t)chunks > INT32_MAX) return cudaErrorInvalidConfiguration;
+    bits_to_msc4_kernel<<<(unsigned)(rows * chunks), 256, 0, s>>>(bits, plane, stride_words, pairs, chunks);
     return cudaGetLastError();
 }
 

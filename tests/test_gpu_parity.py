@@ -246,7 +246,7 @@ def test_host_buffer_entry_point():
                                            (4224, 0.6, None)])
 def test_host_buffer_single_sweep_in_bands(L, beta, stride):
     """One sweep through host memory runs in row bands that overlap the copies
-    (8 to 16 bands, ragged, padded device rows): each step of 3 sweeps equals
+    (8 or 16 bands, padded device rows): each step of 3 sweeps equals
     the oracle bit for bit, planes and trace, and the host planes feed the
     next call."""
     seed, n = 9, 3
@@ -266,6 +266,131 @@ def test_host_buffer_single_sweep_in_bands(L, beta, stride):
         got = oracle.from_planes_msc4(L, hb.numpy().view(np.uint64), hw.numpy().view(np.uint64))
         np.testing.assert_array_equal(got, s)
         np.testing.assert_array_equal(tr_host.numpy(), tr_o)
+
+
+def test_host_buffer_sweep_in_many_ragged_bands_equals_device_sweep():
+    """At 36864^2 (two 340 MB planes) the host path uses 20 bands of 1844
+    rows, the last one ragged: two calls equal two sweeps of the device path
+    (itself bit-exact against the oracle above), planes and trace."""
+    L, beta, seed = 36864, 0.4406868, 17
+    ref = ising.Lattice(L, "msc4")
+    ising.ising_init_lattice(ref, ising.ISING_INIT_RANDOM, seed)
+    torch.cuda.synchronize()
+    hb = ref.black.cpu().pin_memory()
+    hw = ref.white.cpu().pin_memory()
+    dev = ising.Lattice(L, "msc4")
+    tr_dev = torch.zeros((1, 2), dtype=torch.int64, device="cuda")
+    tr_host = torch.zeros((1, 2), dtype=torch.int64).pin_memory()
+    tr_ref = torch.zeros((1, 2), dtype=torch.int64, device="cuda")
+    for k in range(2):
+        ising.ising_sweep_host(dev, hb.data_ptr(), hw.data_ptr(), beta, 1, seed, k, tr_dev, tr_host.data_ptr())
+        ising.ising_sweep(ref, beta, 1, seed, k, tr_ref)
+        torch.cuda.synchronize()
+        assert torch.equal(hb, ref.black.cpu()) and torch.equal(hw, ref.white.cpu())
+        assert torch.equal(tr_host, tr_ref.cpu())
+    del ref, dev
+    torch.cuda.empty_cache()
+
+
+def pinned_bits(b, w):
+    return torch.from_numpy(b.copy()).pin_memory(), torch.from_numpy(w.copy()).pin_memory()
+
+
+@pytest.mark.parametrize("L,stride", [(64, None), (192, None), (320, 320 // 4 + 32), (2112, None)])
+def test_bit_planes_convert_both_ways_like_the_oracle(L, stride):
+    """MSC4 device planes -> bit planes equals the oracle's encoding of the
+    same lattice, and the oracle's bit planes -> MSC4 give back the lattice
+    (padded device rows included)."""
+    seed = 21
+    lat = ising.Lattice(L, "msc4", row_stride_bytes=stride)
+    ising.ising_init_lattice(lat, ising.ISING_INIT_RANDOM, seed)
+    nb = ising.ising_bits_bytes(L)
+    bits = torch.zeros(2 * nb, dtype=torch.uint8, device="cuda")
+    ising.ising_msc4_to_bits(lat, bits[:nb], bits[nb:])
+    torch.cuda.synchronize()
+    s = oracle.init(L, oracle.MODE_RANDOM, seed)
+    eb, ew = oracle.to_planes_bits(s)
+    got = bits.cpu().numpy()
+    np.testing.assert_array_equal(got[:nb].reshape(L, L // 16), eb)
+    np.testing.assert_array_equal(got[nb:].reshape(L, L // 16), ew)
+    back = ising.Lattice(L, "msc4", row_stride_bytes=stride)
+    up = torch.from_numpy(np.concatenate([eb.ravel(), ew.ravel()])).cuda()
+    ising.ising_bits_to_msc4(up[:nb], up[nb:], back)
+    torch.cuda.synchronize()
+    words = (back.row_stride_bytes // 8)
+    pb = back.black.cpu().numpy().view(np.uint64).reshape(L, words)[:, :L // 32]
+    pw = back.white.cpu().numpy().view(np.uint64).reshape(L, words)[:, :L // 32]
+    np.testing.assert_array_equal(oracle.from_planes_msc4(L, pb, pw), s)
+
+
+@pytest.mark.parametrize("L,beta,stride", [(64, 0.4406868, None), (256, 0.0, None), (640, 50.0, None),
+                                           (2112, 0.4406868, 2112 // 4 + 64), (4224, 0.6, None)])
+def test_host_bits_single_sweep_in_bands(L, beta, stride):
+    """One sweep of a bit-packed host lattice (bands converted on the device
+    after their copy in and before their copy out): each of 3 calls equals
+    the oracle bit for bit, planes and trace."""
+    seed, n = 9, 3
+    s = oracle.init(L, oracle.MODE_RANDOM, seed)
+    hb, hw = pinned_bits(*oracle.to_planes_bits(s))
+    dev = ising.Lattice(L, "msc4", row_stride_bytes=stride)
+    nb = ising.ising_bits_bytes(L)
+    stage = torch.empty(2 * nb, dtype=torch.uint8, device="cuda")
+    tr_dev = torch.zeros((1, 2), dtype=torch.int64, device="cuda")
+    tr_host = torch.zeros((1, 2), dtype=torch.int64).pin_memory()
+    for k in range(n):
+        ising.ising_sweep_host_bits(dev, hb, hw, stage, beta, 1, seed, k, tr_dev, tr_host.data_ptr())
+        torch.cuda.synchronize()
+        tr_o = oracle.run(s, beta, 1, seed, off=k)
+        np.testing.assert_array_equal(oracle.from_planes_bits(L, hb.numpy(), hw.numpy()), s)
+        np.testing.assert_array_equal(tr_host.numpy(), tr_o)
+
+
+def test_host_bits_several_sweeps_per_call():
+    """n_sweeps != 1 converts whole planes around ising_sweep: 2 calls of 4
+    sweeps equal the oracle's 8, planes and trace."""
+    L, beta, seed = 256, 0.4406868, 5
+    s = oracle.init(L, oracle.MODE_RANDOM, seed)
+    hb, hw = pinned_bits(*oracle.to_planes_bits(s))
+    dev = ising.Lattice(L, "msc4")
+    nb = ising.ising_bits_bytes(L)
+    stage = torch.empty(2 * nb, dtype=torch.uint8, device="cuda")
+    tr_dev = torch.zeros((4, 2), dtype=torch.int64, device="cuda")
+    tr_host = torch.zeros((4, 2), dtype=torch.int64).pin_memory()
+    for k in range(2):
+        ising.ising_sweep_host_bits(dev, hb, hw, stage, beta, 4, seed, 4 * k, tr_dev, tr_host.data_ptr())
+        torch.cuda.synchronize()
+        tr_o = oracle.run(s, beta, 4, seed, off=4 * k)
+        np.testing.assert_array_equal(oracle.from_planes_bits(L, hb.numpy(), hw.numpy()), s)
+        np.testing.assert_array_equal(tr_host.numpy(), tr_o)
+
+
+def test_host_bits_sweep_in_many_ragged_bands_equals_device_sweep():
+    """At 69632^2 (bit planes of 303 MB) the bit path uses 18 bands of 3869
+    rows, the last one ragged: two calls equal two sweeps of the device path,
+    converted to bits on the device (conversion checked above), and the trace."""
+    L, beta, seed = 69632, 0.4406868, 23
+    ref = ising.Lattice(L, "msc4")
+    ising.ising_init_lattice(ref, ising.ISING_INIT_RANDOM, seed)
+    nb = ising.ising_bits_bytes(L)
+    refbits = torch.empty(2 * nb, dtype=torch.uint8, device="cuda")
+    ising.ising_msc4_to_bits(ref, refbits[:nb], refbits[nb:])
+    torch.cuda.synchronize()
+    hb = refbits[:nb].cpu().pin_memory()
+    hw = refbits[nb:].cpu().pin_memory()
+    dev = ising.Lattice(L, "msc4")
+    stage = torch.empty(2 * nb, dtype=torch.uint8, device="cuda")
+    tr_dev = torch.zeros((1, 2), dtype=torch.int64, device="cuda")
+    tr_host = torch.zeros((1, 2), dtype=torch.int64).pin_memory()
+    tr_ref = torch.zeros((1, 2), dtype=torch.int64, device="cuda")
+    for k in range(2):
+        ising.ising_sweep_host_bits(dev, hb, hw, stage, beta, 1, seed, k, tr_dev, tr_host.data_ptr())
+        ising.ising_sweep(ref, beta, 1, seed, k, tr_ref)
+        ising.ising_msc4_to_bits(ref, refbits[:nb], refbits[nb:])
+        torch.cuda.synchronize()
+        assert torch.equal(hb, refbits[:nb].cpu()) and torch.equal(hw, refbits[nb:].cpu())
+        assert torch.equal(tr_host, tr_ref.cpu())
+    del ref, dev, refbits, stage
+    torch.cuda.empty_cache()
 
 
 def test_undersized_buffers_are_rejected():
