@@ -1185,6 +1185,20 @@ __device__ __forceinline__ void wgrad_stage(const Chains &ch, const __nv_bfloat1
     }
 }
 
+// N (1 or 2) consecutive floats of shared memory; a pair is one 8-byte load
+// (the address is even).
+template <int N>
+__device__ __forceinline__ void load_pair(const float *p, float (&v)[N])
+{
+    if constexpr (N == 2) {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        v[0] = t.x;
+        v[1] = t.y;
+    } else {
+        v[0] = p[0];
+    }
+}
+
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(256) wgrad_kernel(Chains ch, int64_t C, const __nv_bfloat16 *a_prev, const float *dz,
                                                     const float *dlogits, float *partial)
@@ -1221,22 +1235,39 @@ __global__ void __launch_bounds__(256) wgrad_kernel(Chains ch, int64_t C, const 
         wgrad_stage<CIN, COUT>(ch, a_prev, dz, dlogits, c, y0, x0, sa, sd);
         __syncthreads();
         if (active) {
-            for (int pix = 0; pix < kTy * kTx; ++pix) {
-                const int ty = pix / kTx, tx = pix - ty * kTx;
-                float g[OPT];
+            // pixels in row order; along a tile row the 3 x 3 input window
+            // slides in registers, so each pixel loads one new column per dy
+            // (channel pairs as float2 where there are two)
+            for (int ty = 0; ty < kTy; ++ty) {
+                float win[3][3][IPT];  // [dy][dx][input channel]
 #pragma unroll
-                for (int a = 0; a < OPT; ++a) g[a] = sd[pix * COUT + OPT * oq + a];
+                for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-                for (int a = 0; a < OPT; ++a) bacc[a] += g[a];
+                    for (int dx = 0; dx < 2; ++dx) load_pair<IPT>(sa + ((ty + dy) * (kTx + 2) + dx) * CIN + IPT * iq,
+                                                              win[dy][dx]);
 #pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    const int hp = (ty + k / 3) * (kTx + 2) + (tx + k % 3);
+                for (int tx = 0; tx < kTx; ++tx) {
 #pragma unroll
-                    for (int b = 0; b < IPT; ++b) {
-                        const float av = sa[hp * CIN + IPT * iq + b];
+                    for (int dy = 0; dy < 3; ++dy)
+                        load_pair<IPT>(sa + ((ty + dy) * (kTx + 2) + tx + 2) * CIN + IPT * iq, win[dy][2]);
+                    float g[OPT];
+                    load_pair<OPT>(sd + (ty * kTx + tx) * COUT + OPT * oq, g);
 #pragma unroll
-                        for (int a = 0; a < OPT; ++a) acc[a][b][k] = fmaf(g[a], av, acc[a][b][k]);
-                    }
+                    for (int a = 0; a < OPT; ++a) bacc[a] += g[a];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k)
+#pragma unroll
+                        for (int b = 0; b < IPT; ++b)
+#pragma unroll
+                            for (int a = 0; a < OPT; ++a)
+                                acc[a][b][k] = fmaf(g[a], win[k / 3][k % 3][b], acc[a][b][k]);
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                        for (int b = 0; b < IPT; ++b) {
+                            win[dy][0][b] = win[dy][1][b];
+                            win[dy][1][b] = win[dy][2][b];
+                        }
                 }
             }
         }

@@ -393,6 +393,33 @@ def test_host_bits_sweep_in_many_ragged_bands_equals_device_sweep():
     torch.cuda.empty_cache()
 
 
+def test_bit_format_arguments_are_checked_before_any_work():
+    """Wrong layout, unaligned host planes, a missing stage or trace staging
+    buffer and a negative beta are rejected with ISING_EINVAL, and nothing is
+    written."""
+    L = 128
+    nb = ising.ising_bits_bytes(L)
+    dev = ising.Lattice(L, "msc4")
+    stage = torch.zeros(2 * nb, dtype=torch.uint8, device="cuda")
+    hb = torch.zeros(nb + 4, dtype=torch.uint8).pin_memory()
+    hw = torch.zeros(nb + 4, dtype=torch.uint8).pin_memory()
+    i8 = ising.Lattice(L, "int8")
+    bad = [
+        lambda: ising.ising_sweep_host_bits(i8, hb, hw, stage, 0.4, 1, 1),
+        lambda: ising.ising_sweep_host_bits(dev, hb.data_ptr() + 2, hw, stage, 0.4, 1, 1),
+        lambda: ising.ising_sweep_host_bits(dev, hb, hw, None, 0.4, 1, 1),
+        lambda: ising.ising_sweep_host_bits(dev, hb, hw, stage, 0.4, 1, 1, 0, None, hb.data_ptr()),
+        lambda: ising.ising_sweep_host_bits(dev, hb, hw, stage, -0.1, 1, 1),
+        lambda: ising.ising_msc4_to_bits(i8, stage[:nb], stage[nb:]),
+    ]
+    for call in bad:
+        with pytest.raises(ising.IsingError) as e:
+            call()
+        assert e.value.status == ising.ISING_EINVAL
+    torch.cuda.synchronize()
+    assert int(stage.count_nonzero()) == 0
+
+
 def test_undersized_buffers_are_rejected():
     """The library checks each plane against the extent of its CUDA allocation
     (the caching allocator's segment, so only overruns past the segment can be
