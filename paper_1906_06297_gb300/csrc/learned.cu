@@ -1081,7 +1081,12 @@ __global__ void __launch_bounds__(kThreads) l4_bwd_data_kernel(int L, int64_t C,
     __syncthreads();
     const int nb1 = L / kBlk;
     const int64_t npix = C * (int64_t)L * L;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+    // four threads per pixel, 8 channels each: a warp reads and writes 8
+    // pixels' 1 KB of z3 / dz3 contiguously
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 4 * npix;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = e >> 2;
+        const int i8 = (int)(e & 3) * 8;
         const int64_t c = p / ((int64_t)L * L);
         const int yx = (int)(p - c * (int64_t)L * L);
         const int y = yx / L, x = yx - y * L;
@@ -1089,26 +1094,30 @@ __global__ void __launch_bounds__(kThreads) l4_bwd_data_kernel(int L, int64_t C,
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             // output pixel q = p - off_k used input p through tap k
-            const int yy = (y - (k / 3 - 1) + L) % L, xx = (x - (k % 3 - 1) + L) % L;
+            int yy = y - (k / 3 - 1), xx = x - (k % 3 - 1);
+            yy = yy < 0 ? yy + L : (yy >= L ? yy - L : yy);
+            xx = xx < 0 ? xx + L : (xx >= L ? xx - L : xx);
             d[k] = dlogits[c * nb1 * nb1 + (yy / kBlk) * nb1 + xx / kBlk] * (1.0f / (kBlk * kBlk));
         }
-#pragma unroll 1
-        for (int i8 = 0; i8 < kCh; i8 += 8) {
-            float v[8];
+        const float4 *zp = reinterpret_cast<const float4 *>(z3 + p * kCh + i8);
+        const float4 za = zp[0], zb = zp[1];
+        const float z[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+        float v[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                float g = 0.0f;
+        for (int i = 0; i < 8; ++i) {
+            float g = 0.0f;
 #pragma unroll
-                for (int k = 0; k < 9; ++k) g = fmaf(W[(i8 + i) * 9 + k], d[k], g);
-                v[i] = g * gelu_grad(z3[p * kCh + i8 + i]);
-                dz3[p * kCh + i8 + i] = v[i];
-            }
-            // bfloat16 copy with halo columns: the operand of the next data gradient on the tensor cores
-            if (dz3b)
-                store_act(dz3b, L, c, y, x, i8,
-                          make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                                     pack_bf16x2(v[6], v[7])));
+            for (int k = 0; k < 9; ++k) g = fmaf(W[(i8 + i) * 9 + k], d[k], g);
+            v[i] = g * gelu_grad(z[i]);
         }
+        float4 *out = reinterpret_cast<float4 *>(dz3 + p * kCh + i8);
+        out[0] = make_float4(v[0], v[1], v[2], v[3]);
+        out[1] = make_float4(v[4], v[5], v[6], v[7]);
+        // bfloat16 copy with halo columns: the operand of the next data gradient on the tensor cores
+        if (dz3b)
+            store_act(dz3b, L, c, y, x, i8,
+                      make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                                 pack_bf16x2(v[6], v[7])));
     }
 }
 
@@ -1168,20 +1177,43 @@ __device__ __forceinline__ void wgrad_stage(const Chains &ch, const __nv_bfloat1
                                             const float *dlogits, int64_t c, int y0, int x0, float *sa, float *sd)
 {
     const int L = ch.L, nb1 = L / kBlk;
-    // input tile with halo: (kTy + 2) x (kTx + 2) pixels x CIN channels
-    for (int e = threadIdx.x; e < (kTy + 2) * (kTx + 2) * CIN; e += blockDim.x) {
-        const int pix = e / CIN, i = e - pix * CIN;
-        const int ty = pix / (kTx + 2), tx = pix - ty * (kTx + 2);
-        int y = y0 + ty - 1, x = x0 + tx - 1;
-        y = y < 0 ? y + L : (y >= L ? y - L : y);
-        x = x < 0 ? x + L : (x >= L ? x - L : x);
-        sa[e] = CIN == 1 ? spin_at(ch, c, y, x, -1) : __bfloat162float(a_prev[apix(L, c, y, x) * CIN + i]);
+    // input tile with halo: (kTy + 2) x (kTx + 2) pixels x CIN channels; 32
+    // channels come as four 16-byte loads of 8 bfloat16 per pixel
+    if constexpr (CIN == kCh) {
+        constexpr int kOct = CIN / 8;
+        for (int e = threadIdx.x; e < (kTy + 2) * (kTx + 2) * kOct; e += blockDim.x) {
+            const int pix = e / kOct, q = e - pix * kOct;
+            const int ty = pix / (kTx + 2), tx = pix - ty * (kTx + 2);
+            int y = y0 + ty - 1, x = x0 + tx - 1;
+            y = y < 0 ? y + L : (y >= L ? y - L : y);
+            x = x < 0 ? x + L : (x >= L ? x - L : x);
+            const uint4 v = *reinterpret_cast<const uint4 *>(a_prev + apix(L, c, y, x) * CIN + 8 * q);
+            float4 *dst = reinterpret_cast<float4 *>(sa + pix * CIN + 8 * q);
+            dst[0] = make_float4(bf16_lo(v.x), bf16_hi(v.x), bf16_lo(v.y), bf16_hi(v.y));
+            dst[1] = make_float4(bf16_lo(v.z), bf16_hi(v.z), bf16_lo(v.w), bf16_hi(v.w));
+        }
+    } else {
+        for (int e = threadIdx.x; e < (kTy + 2) * (kTx + 2); e += blockDim.x) {
+            const int ty = e / (kTx + 2), tx = e - ty * (kTx + 2);
+            int y = y0 + ty - 1, x = x0 + tx - 1;
+            y = y < 0 ? y + L : (y >= L ? y - L : y);
+            x = x < 0 ? x + L : (x >= L ? x - L : x);
+            sa[e] = spin_at(ch, c, y, x, -1);
+        }
     }
-    for (int e = threadIdx.x; e < kTy * kTx * COUT; e += blockDim.x) {
-        const int pix = e / COUT, o = e - pix * COUT;
-        const int y = y0 + pix / kTx, x = x0 + pix % kTx;
-        sd[e] = COUT == 1 ? dlogits[c * nb1 * nb1 + (y / kBlk) * nb1 + x / kBlk] * (1.0f / (kBlk * kBlk))
-                          : dz[((c * L + y) * (int64_t)L + x) * COUT + o];
+    // output gradients of the tile: a tile row of 32 pixels x 32 channels is
+    // contiguous, loaded as float4
+    if constexpr (COUT == kCh) {
+        for (int e = threadIdx.x; e < kTy * kTx * COUT / 4; e += blockDim.x) {
+            const int row = e / (kTx * COUT / 4), v = e - row * (kTx * COUT / 4);
+            const float4 *src = reinterpret_cast<const float4 *>(dz + ((c * L + y0 + row) * (int64_t)L + x0) * COUT);
+            reinterpret_cast<float4 *>(sd)[e] = src[v];
+        }
+    } else {
+        for (int e = threadIdx.x; e < kTy * kTx; e += blockDim.x) {
+            const int y = y0 + e / kTx, x = x0 + e % kTx;
+            sd[e] = dlogits[c * nb1 * nb1 + (y / kBlk) * nb1 + x / kBlk] * (1.0f / (kBlk * kBlk));
+        }
     }
 }
 
@@ -1286,18 +1318,34 @@ __global__ void __launch_bounds__(256) wgrad_kernel(Chains ch, int64_t C, const 
     }
 }
 
-// grad[off + e] = sum over ctas (in order) of partial[cta][e]; weights come
-// first (W[o][i][k] order), then the biases.
-__global__ void reduce_partials_kernel(const float *partial, int64_t n_cta, int ne, int nw, float *grad, int w_off,
-                                       int b_off)
+// grad[off + e] = sum over ctas of partial[cta][e] in a fixed order: warp w
+// of a block sums the w-th eighth of the CTA range (in order) for 32
+// consecutive e, then the eight warp sums are added in warp order.  Weights
+// come first (W[o][i][k] order), then the biases.  Launch: ceil(ne / 32)
+// blocks of 256 threads.
+constexpr int kReduceWarps = 8;
+
+__global__ void __launch_bounds__(32 * kReduceWarps) reduce_partials_kernel(const float *partial, int64_t n_cta,
+                                                                            int ne, int nw, float *grad, int w_off,
+                                                                            int b_off)
 {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
-        float s = 0.0f;
-        for (int64_t k = 0; k < n_cta; ++k) s += partial[k * ne + e];
+    __shared__ float part[kReduceWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    const int64_t k0 = n_cta * warp / kReduceWarps, k1 = n_cta * (warp + 1) / kReduceWarps;
+    float s = 0.0f;
+    if (e < ne)
+        for (int64_t k = k0; k < k1; ++k) s += partial[k * ne + e];
+    part[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && e < ne) {
+        float t = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kReduceWarps; ++w) t += part[w][lane];
         if (e < nw)
-            grad[w_off + e] = s;
+            grad[w_off + e] = t;
         else
-            grad[b_off + (e - nw)] = s;
+            grad[b_off + (e - nw)] = t;
     }
 }
 
@@ -1543,7 +1591,7 @@ struct NetWork {
     size_t bytes;
 };
 
-constexpr int64_t kWgradCtasPerSm = 2;  // persistent CTAs per SM in the weight-gradient kernels
+constexpr int64_t kWgradCtasPerSm = 3;  // persistent CTAs per SM in the weight-gradient kernels
 
 NetWork net_layout(int64_t L, int64_t C, int train, char *base)
 {
@@ -1876,16 +1924,20 @@ ISING_API int ising_net_backward(int64_t L, int64_t C, const void *black_dev, co
     cudaFuncSetAttribute(wgrad_kernel<kCh, kCh>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm32);
     cudaFuncSetAttribute(wgrad_kernel<kCh, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
     cudaFuncSetAttribute(wgrad_kernel<1, kCh>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    auto reduce = [&](int ne, int nw, int w_off, int b_off) {
+        reduce_partials_kernel<<<(unsigned)((ne + 31) / 32), 32 * kReduceWarps, 0, s>>>(w.partial, w.n_cta, ne, nw,
+                                                                                       grad_dev, w_off, b_off);
+    };
     // layer 4
     wgrad_kernel<kCh, 1><<<gw, 256, sm4, s>>>(ch, C, w.a3, nullptr, dlogits_dev, w.partial);
-    reduce_partials_kernel<<<4, 256, 0, s>>>(w.partial, w.n_cta, kN1 + 1, kN1, grad_dev, kOffW4, kOffB4);
+    reduce(kN1 + 1, kN1, kOffW4, kOffB4);
     // the data gradients of the 32 -> 32 layers run on the tensor cores for L a multiple of 128
     const bool ring = L % kTileM == 0;
-    l4_bwd_data_kernel<<<g, kThreads, 0, s>>>((int)L, C, params_dev, dlogits_dev, w.z3, w.da,
-                                              ring ? w.gb1 : nullptr);  // dz3
+    l4_bwd_data_kernel<<<grid1d(4 * npix, kThreads), kThreads, 0, s>>>((int)L, C, params_dev, dlogits_dev, w.z3,
+                                                                     w.da, ring ? w.gb1 : nullptr);  // dz3
     // layer 3
     wgrad_kernel<kCh, kCh><<<gw, 256, sm32, s>>>(ch, C, w.a2, w.da, nullptr, w.partial);
-    reduce_partials_kernel<<<40, 256, 0, s>>>(w.partial, w.n_cta, kN2 + kCh, kN2, grad_dev, kOffW3, kOffB3);
+    reduce(kN2 + kCh, kN2, kOffW3, kOffB3);
     if (ring) {
         rc = launch_ring_bwd((int)L, C, params_dev, kOffW3, w.gb1, w.z2, w.db, w.gb2, s);  // dz2
         if (rc) return rc;
@@ -1894,7 +1946,7 @@ ISING_API int ising_net_backward(int64_t L, int64_t C, const void *black_dev, co
     }
     // layer 2
     wgrad_kernel<kCh, kCh><<<gw, 256, sm32, s>>>(ch, C, w.a1, w.db, nullptr, w.partial);
-    reduce_partials_kernel<<<40, 256, 0, s>>>(w.partial, w.n_cta, kN2 + kCh, kN2, grad_dev, kOffW2, kOffB2);
+    reduce(kN2 + kCh, kN2, kOffW2, kOffB2);
     if (ring) {
         rc = launch_ring_bwd((int)L, C, params_dev, kOffW2, w.gb2, w.z1, w.da, nullptr, s);  // dz1
         if (rc) return rc;
@@ -1903,7 +1955,7 @@ ISING_API int ising_net_backward(int64_t L, int64_t C, const void *black_dev, co
     }
     // layer 1
     wgrad_kernel<1, kCh><<<gw, 256, sm1, s>>>(ch, C, nullptr, w.da, nullptr, w.partial);
-    reduce_partials_kernel<<<4, 256, 0, s>>>(w.partial, w.n_cta, kN1 + kCh, kN1, grad_dev, kOffW1, kOffB1);
+    reduce(kN1 + kCh, kN1, kOffW1, kOffB1);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ISING_OK : nfail(ISING_ECUDA, cudaGetErrorString(e));
 }
