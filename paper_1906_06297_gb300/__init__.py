@@ -166,6 +166,22 @@ def _stream(stream):
     return ctypes.c_void_p(int(stream))
 
 
+def _on_stream(stream):
+    """Context that makes `stream` PyTorch's current stream (a torch.cuda.Stream
+    or a raw int handle; None keeps the current one), so that the PyTorch ops
+    of a helper that sequences several calls (copies, fills, collectives) are
+    ordered with the library calls it queues on `stream`."""
+    import contextlib
+
+    import torch
+
+    if stream is None:
+        return contextlib.nullcontext()
+    if not hasattr(stream, "cuda_stream"):
+        stream = torch.cuda.ExternalStream(int(stream))
+    return torch.cuda.stream(stream)
+
+
 def _addr(t) -> ctypes.c_void_p:
     if t is None:
         return ctypes.c_void_p(0)
@@ -437,8 +453,9 @@ def exchange_halos(slab: Slab, colour: int, group=None, stream=None):
         dist.P2POp(dist.irecv, p[0], peer(up), group, tag=0),
         dist.P2POp(dist.irecv, p[slab.rows + 1], peer(down), group, tag=1),
     ]
-    for w in dist.batch_isend_irecv(ops):
-        w.wait()
+    with _on_stream(stream):  # messages ordered after the half-sweeps queued on `stream`
+        for w in dist.batch_isend_irecv(ops):
+            w.wait()
 
 
 def slab_sweep(slab: Slab, beta: float, n_sweeps: int, seed: int, sweep_offset: int = 0, trace=None, group=None,
@@ -457,16 +474,17 @@ def slab_sweep(slab: Slab, beta: float, n_sweeps: int, seed: int, sweep_offset: 
 
     hs = half_sweep or (lambda sl, b, c, sd, t, obs: ising_slab_half_sweep(sl, b, c, sd, t, obs, stream))
     _, world = _world(group)
-    if trace is not None:
-        trace.zero_()
-    for k in range(n_sweeps):
-        t = sweep_offset + k
-        exchange_halos(slab, 1, group, stream)
-        hs(slab, beta, 0, seed, t, None)
-        exchange_halos(slab, 0, group, stream)
-        hs(slab, beta, 1, seed, t, trace[k] if trace is not None else None)
-    if trace is not None and world > 1:
-        dist.all_reduce(trace, group=group)
+    with _on_stream(stream):  # the fill, the messages and the half-sweeps in one stream order
+        if trace is not None:
+            trace.zero_()
+        for k in range(n_sweeps):
+            t = sweep_offset + k
+            exchange_halos(slab, 1, group, stream)
+            hs(slab, beta, 0, seed, t, None)
+            exchange_halos(slab, 0, group, stream)
+            hs(slab, beta, 1, seed, t, trace[k] if trace is not None else None)
+        if trace is not None and world > 1:
+            dist.all_reduce(trace, group=group)
 
 
 # ---------------------------------------------------------------------------
@@ -677,6 +695,7 @@ class BlockMove:
         self.block = torch.zeros(self.C, dtype=torch.int32, device=device)
         self.accepted = torch.zeros(self.C, dtype=torch.int32, device=device)
         self.dE = torch.zeros(self.C, dtype=torch.int64, device=device)
+        torch.cuda.synchronize(device)  # the fills above precede moves queued on any stream
 
     def move(self, params, seed: int, t: int, stream=None):
         """One block move of every chain; params None proposes uniformly."""
@@ -708,51 +727,54 @@ def train_block_proposer(L: int, beta: float, n_configs: int = 100_000, batch: i
     import numpy as np
     import torch
 
-    n_chains = min(n_configs, 1024)
-    gen = Batch([L] * n_chains, 1, [beta], device=device)
-    gen.init(ISING_INIT_RANDOM, seed, stream)
-    gen.run(equilibrate, seed, 0, 0, False, None, True, stream)
-    words = L * L // 32
-    data_b = torch.empty((n_configs, words * 8), dtype=torch.uint8, device=device)
-    data_w = torch.empty_like(data_b)
-    t, got = equilibrate, 0
-    while got < n_configs:
-        take = min(n_chains, n_configs - got)
-        data_b[got:got + take].copy_(gen.ws[gen._black_off:gen._black_off + 8 * words * take].view(take, words * 8))
-        data_w[got:got + take].copy_(gen.ws[gen._white_off:gen._white_off + 8 * words * take].view(take, words * 8))
-        got += take
-        gen.run(sweeps_between, seed, t, 0, False, None, True, stream)
-        t += sweeps_between
-    del gen
-    rng = np.random.default_rng(seed)
-    n_par = ising_net_param_count()
-    theta = np.zeros(n_par, dtype=np.float32)
-    o = 0
-    for size, fan_in, is_w in ((32 * 9, 9, True), (32, 0, False), (32 * 32 * 9, 288, True), (32, 0, False),
-                               (32 * 32 * 9, 288, True), (32, 0, False), (32 * 9, 288, True), (1, 0, False)):
-        if is_w:
-            theta[o:o + size] = rng.normal(0.0, np.sqrt(2.0 / fan_in), size)
-        o += size
-    params = torch.from_numpy(theta).to(device)
-    m = torch.zeros_like(params)
-    v = torch.zeros_like(params)
-    grad = torch.zeros_like(params)
-    nb = (L // 8) ** 2
-    work = torch.empty(ising_net_workspace_bytes(L, batch, True), dtype=torch.uint8, device=device)
-    logits = torch.zeros((batch, nb), dtype=torch.float32, device=device)
-    dlogits = torch.zeros_like(logits)
-    chain_sq = torch.zeros(batch, dtype=torch.float32, device=device)
-    loss = torch.zeros(1, dtype=torch.float32, device=device)
-    n_mb = n_configs // batch
-    order = rng.permutation(n_mb)
-    history = []
-    for step in range(1, steps + 1):
-        i0 = int(order[(step - 1) % n_mb]) * batch
-        blk, wht = data_b[i0:i0 + batch], data_w[i0:i0 + batch]
-        ising_net_forward(L, batch, blk, wht, None, params, logits, work, True, stream)
-        ising_net_targets_loss(L, batch, blk, wht, beta, logits, dlogits, chain_sq, loss, stream)
-        ising_net_backward(L, batch, blk, wht, params, dlogits, grad, work, stream)
-        ising_net_adam(params, grad, m, v, step, lr, stream)
-        if step == 1 or step % log_every == 0 or step == steps:
-            history.append(float(loss.item()))
-    return {"params": params, "loss": history, "steps": steps}
+    # every copy, fill and read of this function in the stream order of the library calls
+    with _on_stream(stream):
+        n_chains = min(n_configs, 1024)
+        gen = Batch([L] * n_chains, 1, [beta], device=device)
+        gen.init(ISING_INIT_RANDOM, seed, stream)
+        gen.run(equilibrate, seed, 0, 0, False, None, True, stream)
+        words = L * L // 32
+        data_b = torch.empty((n_configs, words * 8), dtype=torch.uint8, device=device)
+        data_w = torch.empty_like(data_b)
+        t, got = equilibrate, 0
+        while got < n_configs:
+            take = min(n_chains, n_configs - got)
+            nbytes = 8 * words * take
+            data_b[got:got + take].copy_(gen.ws[gen._black_off:gen._black_off + nbytes].view(take, words * 8))
+            data_w[got:got + take].copy_(gen.ws[gen._white_off:gen._white_off + nbytes].view(take, words * 8))
+            got += take
+            gen.run(sweeps_between, seed, t, 0, False, None, True, stream)
+            t += sweeps_between
+        del gen
+        rng = np.random.default_rng(seed)
+        n_par = ising_net_param_count()
+        theta = np.zeros(n_par, dtype=np.float32)
+        o = 0
+        for size, fan_in, is_w in ((32 * 9, 9, True), (32, 0, False), (32 * 32 * 9, 288, True), (32, 0, False),
+                                   (32 * 32 * 9, 288, True), (32, 0, False), (32 * 9, 288, True), (1, 0, False)):
+            if is_w:
+                theta[o:o + size] = rng.normal(0.0, np.sqrt(2.0 / fan_in), size)
+            o += size
+        params = torch.from_numpy(theta).to(device)
+        m = torch.zeros_like(params)
+        v = torch.zeros_like(params)
+        grad = torch.zeros_like(params)
+        nb = (L // 8) ** 2
+        work = torch.empty(ising_net_workspace_bytes(L, batch, True), dtype=torch.uint8, device=device)
+        logits = torch.zeros((batch, nb), dtype=torch.float32, device=device)
+        dlogits = torch.zeros_like(logits)
+        chain_sq = torch.zeros(batch, dtype=torch.float32, device=device)
+        loss = torch.zeros(1, dtype=torch.float32, device=device)
+        n_mb = n_configs // batch
+        order = rng.permutation(n_mb)
+        history = []
+        for step in range(1, steps + 1):
+            i0 = int(order[(step - 1) % n_mb]) * batch
+            blk, wht = data_b[i0:i0 + batch], data_w[i0:i0 + batch]
+            ising_net_forward(L, batch, blk, wht, None, params, logits, work, True, stream)
+            ising_net_targets_loss(L, batch, blk, wht, beta, logits, dlogits, chain_sq, loss, stream)
+            ising_net_backward(L, batch, blk, wht, params, dlogits, grad, work, stream)
+            ising_net_adam(params, grad, m, v, step, lr, stream)
+            if step == 1 or step % log_every == 0 or step == steps:
+                history.append(float(loss.item()))
+        return {"params": params, "loss": history, "steps": steps}

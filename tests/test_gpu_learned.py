@@ -212,6 +212,22 @@ def test_proposals_acceptances_and_flips_match_oracle():
         s_before = s_after
 
 
+def test_training_on_a_side_stream_is_deterministic():
+    """Training data, parameters and every kernel of a training run are
+    ordered on the caller's stream: two runs on a side stream with the same
+    seed give the same loss history and bit-identical parameters (the step-1
+    loss comes before any update, so it depends on the data alone)."""
+    runs = []
+    for _ in range(2):
+        s = torch.cuda.Stream()
+        res = ising.train_block_proposer(32, BETA, n_configs=2048, batch=64, steps=6, lr=3e-3, seed=11,
+                                         sweeps_between=2, equilibrate=5, log_every=1, stream=s)
+        torch.cuda.synchronize()
+        runs.append((res["loss"], res["params"].cpu()))
+    assert runs[0][0] == runs[1][0]
+    assert torch.equal(runs[0][1], runs[1][1])
+
+
 def test_training_makes_proposals_accepted_more_often():
     """After a short GPU training run the network's proposals have a several
     times larger Metropolis-Hastings acceptance probability than uniform ones
