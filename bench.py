@@ -307,6 +307,7 @@ def run_ours(args, world, rank, local):
         # 200 sweeps each; GB/s counts the algorithmic 1.5 bytes per spin update
         per_beta, per_beta_gbs = {}, {}
         ptrace = torch.zeros((200, 2), dtype=torch.int64, device=device)
+        torch.cuda.synchronize()  # the fill precedes the sweeps on `stream`
         for b in (0.30, BETA_C_CONFIG, 0.60):
             tot, _, _ = time_sweeps(ising, torch, lat, b, seed, 200, 2, ptrace, stream, per_kernel=False)
             per_beta[str(b)] = round(n_sites * 200 / (tot * 1e6), 2)
@@ -393,6 +394,7 @@ def run_slab_leg(ising, torch, args, device, stream, whole_flips_per_ns):
         ising.ising_slab_init(sl, ising.ISING_INIT_RANDOM, seed, stream)
         slabs.append(sl)
     trace = torch.zeros((steps, 2), dtype=torch.int64, device=device)
+    torch.cuda.synchronize()  # the fill precedes the sweeps on `stream`
     ms = time_slab_sweeps(ising, torch, slabs, args.beta, seed, steps, 3, trace, stream)
     rate = L * L * steps / (ms * 1e6)
     del slabs
@@ -506,6 +508,7 @@ def rng_probe(ising, torch, L, seed, stream):
     n_blocks = L * L // 8
     T3 = ising.ising_thresholds(BETA_C_CONFIG)[3]
     cnt = torch.zeros(1, dtype=torch.int64, device=stream.device)
+    torch.cuda.synchronize()  # the fill precedes the counting on `stream`
     for _ in range(3):
         ising.ising_rng_probe(n_blocks, seed, 0, 0, T3, cnt, stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -596,6 +599,7 @@ def run_pt_batch(ising, torch, args, device, stream):
     sweeps = args.pt_sweeps
     n_ev = b.n_events(sweeps, warm, every)
     tr = torch.zeros((n_ev, len(L), 2), dtype=torch.int64, device=device)
+    torch.cuda.synchronize()  # the fill precedes the run on `stream`
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         e0.record(stream)
@@ -636,6 +640,7 @@ def run_pt_batch(ising, torch, args, device, stream):
         bb.run(2000, seed, 0, every, swaps, None, True, stream)  # equilibration
         nev = bb.n_events(sweeps, 2000, every)
         tr = torch.zeros((nev, n32, 2), dtype=torch.int64, device=device)
+        torch.cuda.synchronize()  # the fill precedes the run on `stream`
         with torch.cuda.stream(stream):
             e0.record(stream)
             bb.run(sweeps, seed, 2000, every, swaps, tr, True, stream)

@@ -55,28 +55,30 @@ def binder_study(sizes=(32, 64), ladders: int = 8, ladder_size: int = 16, beta_l
     for side in sizes:
         L += [int(side)] * (ladders * ladder_size)
     S = ladder_size
-    b = ising.Batch(L, S, betas, device=device)
-    b.init(ising.ISING_INIT_RANDOM, seed, stream)
-    b.run(thermalize, seed, 0, record_every, True, None, True, stream)
-    b.check(stream)
-    per_chunk = max(record_every, (sweeps // chunks) // record_every * record_every)
-    n_lat = len(L)
-    area = torch.tensor([float(x) * float(x) for x in L], dtype=torch.float64, device=device)
-    # sums over events per chunk and lattice column: m^2, m^4
-    m2 = np.zeros((chunks, n_lat))
-    m4 = np.zeros((chunks, n_lat))
-    off = thermalize
-    events = 0
-    for c in range(chunks):
-        n_ev = b.n_events(per_chunk, off, record_every)
-        tr = torch.zeros((n_ev, n_lat, 2), dtype=torch.int64, device=device)
-        b.run(per_chunk, seed, off, record_every, True, tr, True, stream)
+    # the trace fills and reads in the stream order of the batched runs
+    with ising._on_stream(stream):
+        b = ising.Batch(L, S, betas, device=device)
+        b.init(ising.ISING_INIT_RANDOM, seed, stream)
+        b.run(thermalize, seed, 0, record_every, True, None, True, stream)
         b.check(stream)
-        m = tr[:, :, 0].to(torch.float64) / area
-        m2[c] = (m * m).sum(dim=0).cpu().numpy()
-        m4[c] = (m * m * m * m).sum(dim=0).cpu().numpy()
-        events += n_ev
-        off += per_chunk
+        per_chunk = max(record_every, (sweeps // chunks) // record_every * record_every)
+        n_lat = len(L)
+        area = torch.tensor([float(x) * float(x) for x in L], dtype=torch.float64, device=device)
+        # sums over events per chunk and lattice column: m^2, m^4
+        m2 = np.zeros((chunks, n_lat))
+        m4 = np.zeros((chunks, n_lat))
+        off = thermalize
+        events = 0
+        for c in range(chunks):
+            n_ev = b.n_events(per_chunk, off, record_every)
+            tr = torch.zeros((n_ev, n_lat, 2), dtype=torch.int64, device=device)
+            b.run(per_chunk, seed, off, record_every, True, tr, True, stream)
+            b.check(stream)
+            m = tr[:, :, 0].to(torch.float64) / area
+            m2[c] = (m * m).sum(dim=0).cpu().numpy()
+            m4[c] = (m * m * m * m).sum(dim=0).cpu().numpy()
+            events += n_ev
+            off += per_chunk
     n_per_chunk = events / chunks
     # trace column l*S + k holds the lattice at slot k of ladder l: pool the
     # ladders of each size per slot
