@@ -296,7 +296,8 @@ def pinned_bits(b, w):
     return torch.from_numpy(b.copy()).pin_memory(), torch.from_numpy(w.copy()).pin_memory()
 
 
-@pytest.mark.parametrize("L,stride", [(64, None), (192, None), (320, 320 // 4 + 32), (2112, None)])
+@pytest.mark.parametrize("L,stride", [(64, None), (192, None), (256, None), (320, 320 // 4 + 32),
+                                      (1024, 1024 // 4 + 16), (2112, None)])
 def test_bit_planes_convert_both_ways_like_the_oracle(L, stride):
     """MSC4 device planes -> bit planes equals the oracle's encoding of the
     same lattice, and the oracle's bit planes -> MSC4 give back the lattice
