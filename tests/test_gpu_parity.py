@@ -222,21 +222,31 @@ def test_rng_probe_counts_match_oracle():
     assert int(cnt.item()) == expect
 
 
-def test_host_buffer_entry_point():
-    L, beta, seed, n = 256, 0.4406868, 4, 7
-    init = ising.Lattice(L, "msc4")
-    ising.ising_init_lattice(init, ising.ISING_INIT_RANDOM, seed)
-    torch.cuda.synchronize()
-    hb = init.black.cpu().pin_memory()
-    hw = init.white.cpu().pin_memory()
-    dev = ising.Lattice(L, "msc4")
+@pytest.mark.parametrize("layout,L,stride", [("msc4", 256, None), ("int8", 256, None), ("int8", 130, 80)])
+def test_host_buffer_entry_point(layout, L, stride):
+    """Several sweeps through host memory (whole planes copied in and out
+    around ising_sweep): planes and trace equal the oracle, in both layouts
+    and with padded device rows."""
+    beta, seed, n = 0.4406868, 4, 7
+    s = oracle.init(L, oracle.MODE_RANDOM, seed)
+    if layout == "msc4":
+        b, w = oracle.to_planes_msc4(s)
+    else:
+        b, w = oracle.to_planes_int8(s)
+    hb = torch.from_numpy(b.view(np.uint8).copy()).pin_memory()
+    hw = torch.from_numpy(w.view(np.uint8).copy()).pin_memory()
+    dev = ising.Lattice(L, layout, row_stride_bytes=stride)
     tr_dev = torch.zeros((n, 2), dtype=torch.int64, device="cuda")
     tr_host = torch.zeros((n, 2), dtype=torch.int64).pin_memory()
     ising.ising_sweep_host(dev, hb.data_ptr(), hw.data_ptr(), beta, n, seed, 0, tr_dev, tr_host.data_ptr())
     torch.cuda.synchronize()
-    s = oracle.init(L, oracle.MODE_RANDOM, seed)
     tr_o = oracle.run(s, beta, n, seed)
-    got = oracle.from_planes_msc4(L, hb.numpy().view(np.uint64), hw.numpy().view(np.uint64))
+    if layout == "msc4":
+        got = oracle.from_planes_msc4(L, hb.numpy().view(np.uint64).reshape(L, -1),
+                                      hw.numpy().view(np.uint64).reshape(L, -1))
+    else:
+        got = oracle.from_planes_int8(L, hb.numpy().view(np.int8).reshape(L, -1),
+                                      hw.numpy().view(np.int8).reshape(L, -1))
     np.testing.assert_array_equal(got, s)
     np.testing.assert_array_equal(tr_host.numpy(), tr_o)
 
