@@ -667,14 +667,26 @@ __device__ __forceinline__ uint32_t bit_spread(uint32_t x)
 // Columns 32 b .. 32 b + 31 of spin row r of chain c as bits (1 = up), with
 // block `flip` (or -1) negated.  Both planes' word b covers these columns:
 // in row r the black spins sit at the columns of r's parity.
-__device__ __forceinline__ uint32_t spin_chunk(const Chains &ch, int64_t c, int r, int b, int flip)
+// The raw words behind spin_chunk: loaded one row ahead of their decoding in
+// the fused loader, so that their latency overlaps the building of a row.
+struct ChunkWords {
+    uint64_t b, w;
+    int r, blk;
+};
+
+__device__ __forceinline__ ChunkWords chunk_words(const Chains &ch, int64_t c, int r, int b)
 {
     const int64_t at = (c * ch.L + r) * (int64_t)ch.wpr + b;
-    const uint32_t kb = bit_spread(msc4_word_to_bits(ch.black[at])), kw = bit_spread(msc4_word_to_bits(ch.white[at]));
-    uint32_t v = (r & 1) ? (kw | (kb << 1)) : (kb | (kw << 1));
+    return ChunkWords{ch.black[at], ch.white[at], r, b};
+}
+
+__device__ __forceinline__ uint32_t chunk_bits(const Chains &ch, const ChunkWords &k, int flip)
+{
+    const uint32_t kb = bit_spread(msc4_word_to_bits(k.b)), kw = bit_spread(msc4_word_to_bits(k.w));
+    uint32_t v = (k.r & 1) ? (kw | (kb << 1)) : (kb | (kw << 1));
     if (flip >= 0) {
         const int nb = ch.L / kBlk, by = flip / nb, bx = flip - by * nb;
-        if ((r >> 3) == by && ((bx * kBlk) >> 5) == b) v ^= 0xFFu << ((bx * kBlk) & 31);
+        if ((k.r >> 3) == by && ((bx * kBlk) >> 5) == k.blk) v ^= 0xFFu << ((bx * kBlk) & 31);
     }
     return v;
 }
@@ -756,22 +768,27 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
         for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
             const RingUnit w = ring_unit(p, u);
             const int fb = p.flip ? p.flip[w.c] : -1;
+            // lane 6 d + q (d < 3, q < 6): chunk x0 / 32 - 1 + q (periodic) of spin row y - 1 + d
+            auto fetch = [&](int j) {
+                ChunkWords k{0, 0, 0, 0};
+                if (lane < 18) {
+                    const int y = ring_row(p, w.c, w.r0 + j);
+                    const int d = lane / 6, q = lane - 6 * d;
+                    k = chunk_words(p.ch, w.c, wrap(y - 1 + d, L), (w.x0 / 32 - 1 + q + nw) % nw);
+                }
+                return k;
+            };
+            ChunkWords next = fetch(-1);
             for (int j = -1; j <= w.nrows; ++j, ++n) {
                 const uint32_t s = n & (kRing - 1);
+                const ChunkWords cur = next;
+                if (j < w.nrows) next = fetch(j + 1);  // in flight while row j is built
                 if (n >= kRing &&
                     !__all_sync(0xffffffffu, tc::mbar_wait(&empty[s], ((n / kRing) + 1) & 1, kWaitCycles))) {
                     ok = false;
                     break;
                 }
-                const int y = ring_row(p, w.c, w.r0 + j);
-                // lane 6 d + q (d < 3, q < 6): chunk x0 / 32 - 1 + q (periodic) of spin row y - 1 + d
-                uint32_t bits = 0;
-                if (lane < 18) {
-                    const int d = lane / 6, q = lane - 6 * d;
-                    const int r = wrap(y - 1 + d, L);
-                    const int b = (w.x0 / 32 - 1 + q + nw) % nw;
-                    bits = spin_chunk(p.ch, w.c, r, b, fb);
-                }
+                const uint32_t bits = lane < 18 ? chunk_bits(p.ch, cur, fb) : 0u;
                 uint8_t *dst = ring + s * kRowBytes;
 #pragma unroll
                 for (int i = 0; i < 5; ++i) {
