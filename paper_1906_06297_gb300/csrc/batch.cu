@@ -528,8 +528,7 @@ int blocks_for(int threads, int *blocks)
 
 cudaError_t launch_coop(const BatchParams &p, int blocks, int threads, cudaStream_t s)
 {
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)blocks);
     cfg.blockDim = dim3((unsigned)threads);
     cfg.stream = s;
@@ -744,8 +743,7 @@ static int run_impl(ising_batch_t *b, uint64_t *black, uint64_t *white, int64_t 
         b->graph_threads = b->threads;
         b->graph_blocks = blocks;
     }
-    cudaKernelNodeParams kp;
-    memset(&kp, 0, sizeof(kp));
+    cudaKernelNodeParams kp = {};
     void *args[1] = {&p};
     kp.func = (void *)batch_kernel;
     kp.gridDim = dim3((unsigned)blocks);
