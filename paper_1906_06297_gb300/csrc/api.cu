@@ -588,14 +588,44 @@ namespace {
 // of `hrow` = L/16 bytes, copied into `stage` (black's plane, then white's)
 // and converted to and from MSC4 on the compute stream around each band's
 // half-sweeps.
-constexpr int kMaxHostBands = 64;
+constexpr int kMaxHostBands = 72;
 
-// Bands of about 16 MiB per host plane: 16 .. 64 bands, and at least 8 rows each.
+// Nominal bands of about 16 MiB per host plane: 16 .. 64 bands, and at least
+// 8 rows each.
 int host_band_count(int64_t L, size_t hrow)
 {
     const int64_t by_bytes = (int64_t)(((size_t)L * hrow) >> 24);
-    const int64_t k = std::min<int64_t>(std::max<int64_t>(by_bytes, 16), kMaxHostBands);
+    const int64_t k = std::min<int64_t>(std::max<int64_t>(by_bytes, 16), 64);
     return (int)std::min<int64_t>(k, L / 8);
+}
+
+// Band starts and sizes (rows): nominal bands, except that where the lattice
+// is large enough the first and last three bands are 1/8, 1/4 and 1/2 of the
+// nominal size (mirrored), so that the first half-sweep waits for little data
+// and the last copies out are short.  Returns the number of bands (>= 3, no
+// empty band, at most kMaxHostBands).
+int host_bands(int64_t L, size_t hrow, int64_t *b0, int64_t *br)
+{
+    const int nk = host_band_count(L, hrow);
+    const int64_t per = (L + nk - 1) / nk;
+    const int64_t ramp[3] = {per / 8, per / 4, per / 2};
+    int K = 0;
+    int64_t at = 0;
+    auto add = [&](int64_t rows) {
+        b0[K] = at;
+        br[K] = rows;
+        at += rows;
+        ++K;
+    };
+    if (per >= 64 && L >= 4 * per) {
+        const int64_t ends = ramp[0] + ramp[1] + ramp[2];
+        for (int i = 0; i < 3; ++i) add(ramp[i]);
+        while (at < L - ends) add(std::min<int64_t>(per, L - ends - at));
+        for (int i = 2; i >= 0; --i) add(ramp[i]);
+    } else {
+        while (at < L) add(std::min<int64_t>(per, L - at));
+    }
+    return K;
 }
 
 // The events of the banded host path, per device, made on first use; the
@@ -625,13 +655,8 @@ int sweep_host_banded(const ising_lattice_t *dev, char *host[2], char *stage, si
                       const RoundKeys &rk, uint64_t t, int64_t *trace_dev, int64_t *trace_host, cudaStream_t s)
 {
     const int64_t L = dev->L;
-    const int64_t per = (L + host_band_count(L, hrow) - 1) / host_band_count(L, hrow);
-    const int K = (int)((L + per - 1) / per);  // no empty band
     int64_t b0[kMaxHostBands], br[kMaxHostBands];
-    for (int k = 0; k < K; ++k) {
-        b0[k] = k * per;
-        br[k] = std::min<int64_t>(per, L - b0[k]);
-    }
+    const int K = host_bands(L, hrow, b0, br);
     cudaStream_t cmp, out;
     int rc = aux_streams(&cmp, &out);
     if (rc) return rc;
