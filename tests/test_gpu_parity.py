@@ -404,6 +404,29 @@ def test_host_bits_sweep_in_many_ragged_bands_equals_device_sweep():
     torch.cuda.empty_cache()
 
 
+def test_host_entry_points_with_zero_sweeps_return_the_lattice_unchanged():
+    """n_sweeps = 0: the lattice goes in and comes back out (through the MSC4
+    device lattice) unchanged, in both host formats; trace buffers untouched."""
+    L, seed = 192, 31
+    s = oracle.init(L, oracle.MODE_RANDOM, seed)
+    b, w = oracle.to_planes_msc4(s)
+    hb = torch.from_numpy(b.view(np.uint8).copy()).pin_memory()
+    hw = torch.from_numpy(w.view(np.uint8).copy()).pin_memory()
+    dev = ising.Lattice(L, "msc4", row_stride_bytes=L // 4 + 16)
+    tr_dev = torch.full((1, 2), 7, dtype=torch.int64, device="cuda")
+    tr_host = torch.full((1, 2), 7, dtype=torch.int64).pin_memory()
+    ising.ising_sweep_host(dev, hb.data_ptr(), hw.data_ptr(), 0.44, 0, seed, 0, tr_dev, tr_host.data_ptr())
+    bb, bw = pinned_bits(*oracle.to_planes_bits(s))
+    nb = ising.ising_bits_bytes(L)
+    stage = torch.empty(2 * nb, dtype=torch.uint8, device="cuda")
+    ising.ising_sweep_host_bits(dev, bb, bw, stage, 0.44, 0, seed, 0, tr_dev, tr_host.data_ptr())
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(oracle.from_planes_msc4(L, hb.numpy().view(np.uint64).reshape(L, -1),
+                                                          hw.numpy().view(np.uint64).reshape(L, -1)), s)
+    np.testing.assert_array_equal(oracle.from_planes_bits(L, bb.numpy(), bw.numpy()), s)
+    assert int(tr_host[0, 0]) == 7 and int(tr_dev[0, 0].item()) == 7
+
+
 def test_bit_format_arguments_are_checked_before_any_work():
     """Wrong layout, unaligned host planes, a missing stage or trace staging
     buffer and a negative beta are rejected with ISING_EINVAL, and nothing is
