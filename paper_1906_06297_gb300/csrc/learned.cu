@@ -1072,6 +1072,8 @@ __global__ void __launch_bounds__(kThreads) pool_kernel(int L, int64_t C, int br
         const int x = bg * 32 + lane;
         const int xs[3] = {wrap(x - 1, L), x, wrap(x + 1, L)};
         float part = 0.0f;
+        // unrolled: the loads of all 8 rows are issued before the sums (same order of additions)
+#pragma unroll
         for (int yy = by * kBlk; yy < by * kBlk + kBlk; ++yy) {
             const int ys[3] = {wrap(yy - 1, L), yy, wrap(yy + 1, L)};
             float z = b4;
