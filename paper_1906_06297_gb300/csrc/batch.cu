@@ -214,19 +214,43 @@ __device__ void batch_half(const BatchParams &p, int colour, uint64_t t)
         }
         ones = dsum = nitems = 0;
     };
+    // this lane's item as (lattice li of the group, row r, item q of the row):
+    // derived by division at a group's first chunk, then stepped 32 items per
+    // chunk (a warp's chunks are consecutive) with one carry into the row and
+    // at most one wrap into the next lattice
+    int cur_g = -1;
+    int64_t li = 0;
+    int r = 0, q = 0, dr = 0, dq = 0;
     for (int64_t c = cb; c < ce; ++c) {
         while (gi + 1 < p.n_groups && c >= p.g[gi + 1].chunk_begin) ++gi;
         const BatchGroup &G = p.g[gi];
-        const int64_t item = (c - G.chunk_begin) * 32 + lane;
-        const int64_t li = item / G.items;
+        if (gi != cur_g) {
+            cur_g = gi;
+            const int64_t item = (c - G.chunk_begin) * 32 + lane;
+            li = item / G.items;
+            const int64_t within = item - li * G.items;
+            r = (int)(within / G.gpr);
+            q = (int)(within - (int64_t)r * G.gpr);
+            dr = 32 / G.gpr;
+            dq = 32 - dr * G.gpr;
+        } else {
+            q += dq;
+            r += dr;
+            if (q >= G.gpr) {
+                q -= G.gpr;
+                ++r;
+            }
+            if (r >= G.L) {
+                r -= G.L;
+                ++li;
+            }
+        }
         const int64_t lat = G.first + li;
         if (lat != cur_lat) {
             flush();
             cur_lat = lat;
         }
-        const int64_t within = item - li * G.items;
-        const int r = (int)(within / G.gpr);
-        const int w0 = (int)(within - (int64_t)r * G.gpr) * G.wpt;
+        const int w0 = q * G.wpt;
         const int64_t base = G.word_base + li * (int64_t)G.L * G.wpr;
         const int slot = p.slot_of[lat];
         dc.T3 = p.thr[2 * slot];
