@@ -88,6 +88,30 @@ def test_forward_matches_oracle(L, C):
     assert torch.equal(again, logits)
 
 
+def test_forward_at_full_size_on_sampled_chains():
+    """The launch configuration of the benchmark's network leg: 1024 chains of
+    128^2 after 20 sweeps.  Full forward and flipped-band forward of all
+    chains on the GPU; chains 0, 517 and 1023 against the oracle."""
+    L, C = 128, 1024
+    mv = chains(L, C, 13, sweeps=20)
+    th = theta32(2)
+    params = torch.from_numpy(th).cuda()
+    nb = (L // 8) ** 2
+    logits = torch.zeros((C, nb), dtype=torch.float32, device="cuda")
+    logits_f = torch.zeros_like(logits)
+    flips = torch.tensor([(7 * c + 3) % nb for c in range(C)], dtype=torch.int32, device="cuda")
+    ising.ising_net_forward(L, C, mv.black, mv.white, None, params, logits, mv.work)
+    ising.ising_net_forward_flipped(L, C, mv.black, mv.white, flips, params, logits, logits_f, mv.work)
+    ising.ising_net_check()
+    torch.cuda.synchronize()
+    sample = [0, 517, 1023]
+    s = np.stack([oracle.from_planes_msc4(L, *mv.batch.planes_numpy(c)) for c in sample]).astype(np.float64)
+    tb = ln.bf16_round(th)
+    assert_logits_close(logits.cpu().numpy()[sample], ln.forward(tb, s, B=8))
+    f = flips.cpu().numpy()[sample]
+    assert_logits_close(logits_f.cpu().numpy()[sample], ln.forward(tb, s, B=8, flip=f))
+
+
 @pytest.mark.parametrize("L,C", [(128, 6), (256, 3), (384, 2), (64, 3), (96, 2)])
 def test_flipped_band_pass_equals_full_pass(L, C):
     """ising_net_forward_flipped recomputes a band of rows around each chain's
