@@ -667,7 +667,7 @@ int sweep_host_banded(const ising_lattice_t *dev, char *host[2], char *stage, si
     cudaEvent_t *ev = nullptr;
     rc = host_events(devi, &ev);
     if (rc) return rc;
-    cudaEvent_t start = ev[0], end = ev[1], *ev_in = ev + 2, *ev_b = ev_in + K, *ev_w = ev_b + K;
+    cudaEvent_t start = ev[0], end = ev[1], *ev_in = ev + 2, *ev_flush = ev_in + K;  // 2K flush events
     const bool bits = stage != nullptr;
     char *devp[2] = {(char *)dev->black, (char *)dev->white};
     char *stg[2] = {stage, bits ? stage + (size_t)L * hrow : nullptr};
@@ -684,15 +684,9 @@ int sweep_host_banded(const ising_lattice_t *dev, char *host[2], char *stage, si
                   : cudaMemcpy2DAsync(h, hrow, d, pitch, hrow, (size_t)br[k], cudaMemcpyDeviceToHost, st);
     };
     // bits mode: staged band -> MSC4 band (after its copy in) and back (before its copy out)
-    auto unpack = [&](int c, int k) {
-        if (!bits) return cudaSuccess;
-        return bits_to_msc4((const uint32_t *)(stg[c] + b0[k] * hrow), (uint64_t *)(devp[c] + b0[k] * pitch),
-                            stride_words, L, br[k], cmp);
-    };
-    auto pack = [&](int c, int k) {
-        if (!bits) return cudaSuccess;
-        return msc4_to_bits((const uint64_t *)(devp[c] + b0[k] * pitch), stride_words,
-                            (uint32_t *)(stg[c] + b0[k] * hrow), L, br[k], cmp);
+    // bits mode: staged plane band -> MSC4 band (as a conversion job)
+    auto unpack_job = [&](int c, int k) {
+        return ConvJob{stg[c] + b0[k] * hrow, devp[c] + b0[k] * pitch, br[k]};
     };
     e = cudaEventRecord(start, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cmp, start, 0);
@@ -715,32 +709,57 @@ int sweep_host_banded(const ising_lattice_t *dev, char *host[2], char *stage, si
     if (e == cudaSuccess) e = in_black(K - 1);
     if (e == cudaSuccess && trace_dev) e = cudaMemsetAsync(trace_dev, 0, 2 * sizeof(int64_t), cmp);
     if (e != cudaSuccess) return cuda_fail(e, "host sweep: copy in");
-    // compute, each band followed by its copy-out on `out`; in bits mode the
-    // white bands are unpacked in their copy-in order (K-1, 0, 1, .., K-2) as
-    // far as black k needs them: the first min(k + 3, K) of that order
-    int unpacked = 0;
-    auto black = [&](int k) {
+    // compute.  Plane bands that are final wait in `pend` and are flushed to
+    // the copy-out stream behind one event: in MSC4 mode after every
+    // half-sweep; in bits mode after every white half-sweep, packed by one
+    // conversion launch for all of them (black k and white k-1).  In bits mode
+    // black k first unpacks, in one launch, its own band and the white bands
+    // it is the first to need, in their copy-in order (K-1, 0, 1, .., K-2):
+    // the first min(k + 3, K) of that order.  Fewer, larger launches: each
+    // launch leaves the SMs partly idle at its start and end.
+    int unpacked = 0, n_flush = 0, npend = 0;
+    int pend_c[kMaxConvJobs], pend_k[kMaxConvJobs];
+    auto flush = [&]() -> int {
+        if (npend == 0) return ISING_OK;
+        cudaError_t r = cudaSuccess;
+        if (bits) {
+            ConvJob jobs[kMaxConvJobs];
+            for (int i = 0; i < npend; ++i) {
+                const int c = pend_c[i], k = pend_k[i];
+                jobs[i] = ConvJob{devp[c] + b0[k] * pitch, stg[c] + b0[k] * hrow, br[k]};
+            }
+            r = msc4_to_bits_multi(jobs, npend, stride_words, L, cmp);
+        }
+        cudaEvent_t f = ev_flush[n_flush++];
+        if (r == cudaSuccess) r = cudaEventRecord(f, cmp);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(out, f, 0);
+        for (int i = 0; i < npend && r == cudaSuccess; ++i) r = copy(pend_c[i], pend_k[i], false, out);
+        npend = 0;
+        return r == cudaSuccess ? ISING_OK : cuda_fail(r, "host sweep: copy out");
+    };
+    auto black = [&](int k) -> int {
         cudaError_t r = cudaStreamWaitEvent(cmp, ev_in[k], 0);
-        for (; r == cudaSuccess && unpacked < std::min(k + 3, K); ++unpacked)
-            r = unpack(1, unpacked == 0 ? K - 1 : unpacked - 1);
-        if (r == cudaSuccess) r = unpack(0, k);
+        if (r == cudaSuccess && bits) {
+            ConvJob jobs[kMaxConvJobs];
+            int n = 0;
+            for (; unpacked < std::min(k + 3, K); ++unpacked)
+                jobs[n++] = unpack_job(1, unpacked == 0 ? K - 1 : unpacked - 1);
+            jobs[n++] = unpack_job(0, k);
+            r = bits_to_msc4_multi(jobs, n, stride_words, L, cmp);
+        }
         if (r != cudaSuccess) return cuda_fail(r, "host sweep: unpack");
         int x = band_half_sweep_impl(dev, acc, rk, 0, t, b0[k], br[k], nullptr, cmp);
         if (x) return x;
-        r = pack(0, k);
-        if (r == cudaSuccess) r = cudaEventRecord(ev_b[k], cmp);
-        if (r == cudaSuccess) r = cudaStreamWaitEvent(out, ev_b[k], 0);
-        if (r == cudaSuccess) r = copy(0, k, false, out);
-        return r == cudaSuccess ? ISING_OK : cuda_fail(r, "host sweep: copy out");
+        pend_c[npend] = 0;
+        pend_k[npend++] = k;
+        return bits ? ISING_OK : flush();
     };
-    auto white = [&](int k) {
+    auto white = [&](int k) -> int {
         int x = band_half_sweep_impl(dev, acc, rk, 1, t, b0[k], br[k], trace_dev, cmp);
         if (x) return x;
-        cudaError_t r = pack(1, k);
-        if (r == cudaSuccess) r = cudaEventRecord(ev_w[k], cmp);
-        if (r == cudaSuccess) r = cudaStreamWaitEvent(out, ev_w[k], 0);
-        if (r == cudaSuccess) r = copy(1, k, false, out);
-        return r == cudaSuccess ? ISING_OK : cuda_fail(r, "host sweep: copy out");
+        pend_c[npend] = 1;
+        pend_k[npend++] = k;
+        return flush();
     };
     rc = black(0);
     if (!rc) rc = black(1);

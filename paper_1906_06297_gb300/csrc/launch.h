@@ -34,7 +34,17 @@ cudaError_t msc4_pack(const int8_t *src, int64_t src_stride, uint64_t *dst, int6
 cudaError_t msc4_unpack(const uint64_t *src, int64_t src_stride_words, int8_t *dst, int64_t dst_stride,
                         int64_t L, cudaStream_t s);
 // `rows` rows of an MSC4 plane (row stride in words) <-> the same rows in the
-// bit-packed format (L/16 bytes per row, dense); L % 64 == 0.
+// bit-packed format (L/16 bytes per row, dense); L % 64 == 0.  The _multi
+// forms convert up to kMaxConvJobs row ranges (source, destination, rows) of
+// the same L and stride in one launch.
+constexpr int kMaxConvJobs = 4;
+struct ConvJob {
+    const void *src;
+    void *dst;
+    int64_t rows;
+};
+cudaError_t msc4_to_bits_multi(const ConvJob *jobs, int n, int64_t stride_words, int64_t L, cudaStream_t s);
+cudaError_t bits_to_msc4_multi(const ConvJob *jobs, int n, int64_t stride_words, int64_t L, cudaStream_t s);
 cudaError_t msc4_to_bits(const uint64_t *plane, int64_t stride_words, uint32_t *bits, int64_t L, int64_t rows,
                          cudaStream_t s);
 cudaError_t bits_to_msc4(const uint32_t *bits, uint64_t *plane, int64_t stride_words, int64_t L, int64_t rows,
