@@ -45,7 +45,8 @@ struct DeviceCache {
     std::mutex mu;
     std::mutex host_mu;  // held while ising_sweep_host enqueues its bands
     int sm_count[64] = {};
-    cudaStream_t aux[64][2] = {};  // compute and copy-out streams of ising_sweep_host, made on first use
+    cudaStream_t aux[64][3] = {};  // compute, copy-out and capture streams of ising_sweep_host, made on first use
+    cudaGraphExec_t host_exec[64] = {};  // the last banded schedule, replayed (updated) by the next call
     cudaEvent_t *host_ev[64] = {};  // the events of ising_sweep_host's bands, made on first use
 };
 DeviceCache g_dev;
@@ -248,20 +249,21 @@ int band_half_sweep_impl(const ising_lattice_t *lat, const Accept &acc, const Ro
 }
 
 // The compute and copy-out streams of the banded host path, per device.
-int aux_streams(cudaStream_t *cmp, cudaStream_t *out)
+int aux_streams(cudaStream_t *cmp, cudaStream_t *out, cudaStream_t *cap = nullptr)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= 64) return fail(ISING_ECUDA, "device %d out of range", dev);
     std::lock_guard<std::mutex> lock(g_dev.mu);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 3; ++i)
         if (g_dev.aux[dev][i] == nullptr) {
             e = cudaStreamCreateWithFlags(&g_dev.aux[dev][i], cudaStreamNonBlocking);
             if (e != cudaSuccess) return cuda_fail(e, "stream create");
         }
     *cmp = g_dev.aux[dev][0];
     *out = g_dev.aux[dev][1];
+    if (cap) *cap = g_dev.aux[dev][2];
     return ISING_OK;
 }
 
@@ -651,22 +653,18 @@ int host_events(int dev, cudaEvent_t **ev)
     return ISING_OK;
 }
 
-int sweep_host_banded(const ising_lattice_t *dev, char *host[2], char *stage, size_t hrow, const Accept &acc,
-                      const RoundKeys &rk, uint64_t t, int64_t *trace_dev, int64_t *trace_host, cudaStream_t s)
+// Queues one banded host sweep: stream `s` starts and ends it (it may be a
+// stream in capture), `cmp` and `out` are the compute and copy-out streams,
+// `ev` the event pool (caller holds g_dev.host_mu).
+int enqueue_banded(const ising_lattice_t *dev, char *host[2], char *stage, size_t hrow, const Accept &acc,
+                   const RoundKeys &rk, uint64_t t, int64_t *trace_dev, int64_t *trace_host, cudaStream_t s,
+                   cudaStream_t cmp, cudaStream_t out, cudaEvent_t *ev)
 {
     const int64_t L = dev->L;
     int64_t b0[kMaxHostBands], br[kMaxHostBands];
     const int K = host_bands(L, hrow, b0, br);
-    cudaStream_t cmp, out;
-    int rc = aux_streams(&cmp, &out);
-    if (rc) return rc;
-    int devi = 0;
-    cudaError_t e = cudaGetDevice(&devi);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    std::lock_guard<std::mutex> lock(g_dev.host_mu);
-    cudaEvent_t *ev = nullptr;
-    rc = host_events(devi, &ev);
-    if (rc) return rc;
+    int rc = ISING_OK;
+    cudaError_t e = cudaSuccess;
     cudaEvent_t start = ev[0], end = ev[1], *ev_in = ev + 2, *ev_flush = ev_in + K;  // 2K flush events
     const bool bits = stage != nullptr;
     char *devp[2] = {(char *)dev->black, (char *)dev->white};
@@ -775,6 +773,59 @@ int sweep_host_banded(const ising_lattice_t *dev, char *host[2], char *stage, si
     if (e == cudaSuccess) e = cudaEventRecord(end, out);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, end, 0);
     return e == cudaSuccess ? ISING_OK : cuda_fail(e, "host sweep: copy out");
+}
+
+// One banded host sweep.  The schedule (about 4 launches and 4 copies per
+// band, with cross-stream events) is captured on the library's capture stream
+// and replayed as a CUDA graph on `s`: the executable graph of the previous
+// call is updated in place (new sweep index, keys, buffers) where the
+// topology is the same, else instantiated anew.  Capture and update run on the
+// host while the GPU still executes the previous call.  Any failure of the
+// capture path falls back to launching the schedule directly on `s`.
+int sweep_host_banded(const ising_lattice_t *dev, char *host[2], char *stage, size_t hrow, const Accept &acc,
+                      const RoundKeys &rk, uint64_t t, int64_t *trace_dev, int64_t *trace_host, cudaStream_t s)
+{
+    cudaStream_t cmp = nullptr, out = nullptr, cap = nullptr;
+    int rc = aux_streams(&cmp, &out, &cap);
+    if (rc) return rc;
+    int devi = 0;
+    cudaError_t e = cudaGetDevice(&devi);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lock(g_dev.host_mu);
+    cudaEvent_t *ev = nullptr;
+    rc = host_events(devi, &ev);
+    if (rc) return rc;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const int crc = enqueue_banded(dev, host, stage, hrow, acc, rk, t, trace_dev, trace_host, cap, cmp, out, ev);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(cap, &g);
+        if (crc == ISING_OK && ce == cudaSuccess && g != nullptr) {
+            cudaGraphExec_t &x = g_dev.host_exec[devi];
+            bool ready = false;
+            if (x != nullptr) {
+                cudaGraphExecUpdateResultInfo info;
+                ready = cudaGraphExecUpdate(x, g, &info) == cudaSuccess;
+                if (!ready) {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(x);
+                    x = nullptr;
+                }
+            }
+            if (!ready) {
+                ready = cudaGraphInstantiate(&x, g, 0) == cudaSuccess;
+                if (!ready) x = nullptr;
+            }
+            cudaGraphDestroy(g);
+            if (ready) {
+                e = cudaGraphLaunch(x, s);
+                return e == cudaSuccess ? ISING_OK : cuda_fail(e, "host sweep: graph launch");
+            }
+        } else if (g != nullptr) {
+            cudaGraphDestroy(g);
+        }
+        cudaGetLastError();  // the capture path failed: clear its error, launch directly
+    }
+    return enqueue_banded(dev, host, stage, hrow, acc, rk, t, trace_dev, trace_host, s, cmp, out, ev);
 }
 
 }  // namespace
