@@ -114,12 +114,15 @@ ISING_API int ising_sweep(const ising_lattice_t *lat, double beta, int64_t n_swe
  * the trace (if trace_host is not NULL; trace_dev is then required as device
  * staging of n_sweeps x 2 int64) back.  Pinned host memory makes the copies
  * asynchronous; the call does not synchronise the stream.  One sweep of an
- * MSC4 lattice runs in 16 to 64 row bands on two more streams of the
- * library's own: plane bands are copied in in the order the half-sweeps need
- * them and each is copied out as soon as it is final, so that both directions
- * of the host link are busy while the bands are swept; the work is still
+ * MSC4 lattice runs in row bands (about 16 MiB of host plane each, smaller
+ * first and last bands) on streams of the library's own: plane bands are
+ * copied in in the order the half-sweeps need them and each is copied out as
+ * soon as it is final, so that both directions of the host link are busy
+ * while the bands are swept.  The schedule is captured and replayed on
+ * `stream` as a CUDA graph (launched directly if capture fails); the work is
  * ordered on `stream` (it starts after the work queued on it and the stream
- * waits for all of it), and the result is that of ising_sweep. */
+ * waits for all of it), and the result is that of ising_sweep.  Calls on one
+ * device are serialised while they queue work. */
 ISING_API int ising_sweep_host(const ising_lattice_t *dev, void *black_host, void *white_host, double beta,
                                int64_t n_sweeps, uint64_t seed, uint64_t sweep_offset, int64_t *trace_dev,
                                int64_t *trace_host, ising_stream_t stream);
