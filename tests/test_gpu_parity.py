@@ -404,6 +404,51 @@ def test_host_bits_sweep_in_many_ragged_bands_equals_device_sweep():
     torch.cuda.empty_cache()
 
 
+def test_host_sweeps_alternating_between_lattices_of_one_size():
+    """Calls that alternate between lattices of the same size (other host
+    planes, stage, device lattice and seed, the same band schedule, so the
+    replayed schedule of one call is updated in place for the next) must each
+    act on their own buffers; switching host format changes the schedule and
+    re-instantiates it.  Both formats, 3 rounds, against the oracle."""
+    L, beta = 2112, 0.4406868
+    runs = []
+    # consecutive calls of one format (same schedule, other buffers), then the other format
+    for fmt, seed in (("bits", 41), ("bits", 43), ("msc4", 42), ("msc4", 44)):
+        s = oracle.init(L, oracle.MODE_RANDOM, seed)
+        if fmt == "bits":
+            hb, hw = pinned_bits(*oracle.to_planes_bits(s))
+            nb = ising.ising_bits_bytes(L)
+            extra = torch.empty(2 * nb, dtype=torch.uint8, device="cuda")
+        else:
+            b, w = oracle.to_planes_msc4(s)
+            hb = torch.from_numpy(b.view(np.uint8).copy()).pin_memory()
+            hw = torch.from_numpy(w.view(np.uint8).copy()).pin_memory()
+            extra = None
+        dev = ising.Lattice(L, "msc4")
+        tr_dev = torch.zeros((1, 2), dtype=torch.int64, device="cuda")
+        tr_host = torch.zeros((1, 2), dtype=torch.int64).pin_memory()
+        runs.append(dict(fmt=fmt, seed=seed, s=s, hb=hb, hw=hw, stage=extra, dev=dev, tr_dev=tr_dev,
+                         tr_host=tr_host))
+    for k in range(3):
+        for r in runs:
+            if r["fmt"] == "bits":
+                ising.ising_sweep_host_bits(r["dev"], r["hb"], r["hw"], r["stage"], beta, 1, r["seed"], k,
+                                            r["tr_dev"], r["tr_host"].data_ptr())
+            else:
+                ising.ising_sweep_host(r["dev"], r["hb"].data_ptr(), r["hw"].data_ptr(), beta, 1, r["seed"], k,
+                                       r["tr_dev"], r["tr_host"].data_ptr())
+        torch.cuda.synchronize()
+        for r in runs:
+            tr_o = oracle.run(r["s"], beta, 1, r["seed"], off=k)
+            if r["fmt"] == "bits":
+                got = oracle.from_planes_bits(L, r["hb"].numpy(), r["hw"].numpy())
+            else:
+                got = oracle.from_planes_msc4(L, r["hb"].numpy().view(np.uint64).reshape(L, -1),
+                                              r["hw"].numpy().view(np.uint64).reshape(L, -1))
+            np.testing.assert_array_equal(got, r["s"])
+            np.testing.assert_array_equal(r["tr_host"].numpy(), tr_o)
+
+
 def test_host_entry_points_with_zero_sweeps_return_the_lattice_unchanged():
     """n_sweeps = 0: the lattice goes in and comes back out (through the MSC4
     device lattice) unchanged, in both host formats; trace buffers untouched."""
