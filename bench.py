@@ -8,9 +8,12 @@ L^2 x sweeps / ns (attempted updates).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 runs under torchrun, one independent replica per GPU (weak scaling,
-seed 1234 + rank, no data-path collective); the value is all replicas' flips
-divided by the slowest rank's time.  ``--impl reference`` times the CPU oracle
+N > 1 runs under torchrun and cuts the one lattice into N horizontal slabs,
+one per GPU, with the boundary rows exchanged point to point (NCCL) beside
+the interior updates (Sec. 4; strong scaling: the lattice is the same for
+every N); ``--workload replicas`` runs one independent lattice per GPU
+instead (weak scaling, seed 1234 + rank, no data-path collective).  The value
+is all ranks' flips divided by the slowest rank's time.  ``--impl reference`` times the CPU oracle
 (the plain C implementation the kernels are checked against) on the host
 cores instead.  Rank 0 prints one JSON line.
 """
@@ -45,17 +48,23 @@ def parse_args(argv=None):
     p.add_argument("--seed", type=int, default=1234)
     p.add_argument("--init", choices=["random", "up"], default="random")
     p.add_argument("--e2e-steps", type=int, default=10)
-    p.add_argument("--cpu-L", type=int, default=8192, help="oracle sample lattice side")
-    p.add_argument("--cpu-sweeps", type=int, default=10, help="oracle sample sweeps")
+    p.add_argument("--cpu-L", type=int, default=16384, help="oracle sample lattice side")
+    p.add_argument("--cpu-sweeps", type=int, default=20, help="oracle sample sweeps (all cores)")
+    p.add_argument("--ref-L", type=int, default=8192, help="oracle lattice side of one reference-arm step")
+    p.add_argument("--cpu-sweeps-1t", type=int, default=1, help="oracle sweeps of 16384^2 on one thread")
+    p.add_argument("--cpu-short", action="store_true",
+                   help="cpu baseline: only the headline sample (no 1-thread, 256^2 or 65536^2 spot check)")
     p.add_argument("--no-extras", action="store_true", help="skip per-beta, rng probe, e2e and cpu legs")
     p.add_argument("--no-batch", action="store_true", help="skip the batched parallel-tempering leg")
     p.add_argument("--pt-sweeps", type=int, default=10000)
     p.add_argument("--slabs", type=int, default=4, help="slabs on one GPU for the slab leg / workload")
     p.add_argument("--no-binder", action="store_true", help="skip the Binder-crossing leg")
     p.add_argument("--binder-sweeps", type=int, default=100000)
-    p.add_argument("--workload", choices=["sweep", "pt", "learned", "network", "train", "slabs", "binder", "host"],
+    p.add_argument("--workload", choices=["sweep", "replicas", "pt", "learned", "network", "train", "slabs", "binder",
+                                          "host"],
                    default="sweep",
-                   help="sweep: the 65536^2 lattice (default); pt / learned: only that leg")
+                   help="sweep: the 65536^2 lattice (default; with several GPUs cut into one slab per rank); "
+                        "replicas: one independent lattice per GPU; pt / learned / ...: only that leg")
     p.add_argument("--no-learned", action="store_true", help="skip the learned block-proposal leg")
     p.add_argument("--learned-steps", type=int, default=1000, help="training steps of the proposal network")
     p.add_argument("--learned-cycles", type=int, default=400, help="measured sweep + move cycles")
@@ -168,13 +177,45 @@ def measured_peaks():
 
 
 # Integer roofline of the sweep kernel.  A spin update needs a quarter of a
-# Philox4x32-10 block: 20 32x32->64-bit multiplies per 4 draws.  On sm_103a a
-# warp-wide IMAD.WIDE.U32 keeps the FMA-heavy pipe of its SM sub-partition busy
-# for 4 cycles (ncu: fmaheavy busy cycles against the per-opcode counts), i.e.
-# 8 wide multiplies per clock per sub-partition, 4 sub-partitions per SM.
+# Philox4x32-10 block: 20 32x32->64-bit multiplies per 4 draws.  The peak rate
+# of that multiply is measured by the wide-multiply probe (ising_mulwide_probe:
+# independent chains of dependent multiply-adds on a full grid, no memory
+# traffic).  Beside it, the rate the ncu counters suggest: a warp-wide
+# IMAD.WIDE.U32 keeps the FMA-heavy pipe of its SM sub-partition busy for 4
+# cycles (fmaheavy busy cycles against the per-opcode counts), i.e. 8 wide
+# multiplies per clock per sub-partition, 4 sub-partitions per SM.
 WIDE_MUL_PER_SPIN = 5
 WIDE_MUL_PER_CLK_PER_SMSP = 8
 SMSP_PER_SM = 4
+
+
+def mulwide_rate(ising, torch, stream, form, iters=16384, reps=10):
+    """One form of the wide-multiply probe, timed with CUDA events on its
+    stream after warm-up launches: multiplies per second (median launch)."""
+    sink = torch.zeros(1, dtype=torch.int64, device=stream.device)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        n = ising.ising_mulwide_probe(form, iters, sink, stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(reps):
+            ising.ising_mulwide_probe(form, iters, sink, stream)
+            ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    times = [ev[k].elapsed_time(ev[k + 1]) for k in range(reps)]
+    med = statistics.median(times)
+    return {"t_mul_per_s": round(n / (med * 1e-3) / 1e12, 3), "t_mul_per_s_best": round(n / (min(times) * 1e-3) / 1e12, 3),
+            "ms_median": round(med, 4), "multiplies_per_launch": n, "launches": reps}
+
+
+def mulwide_peak(ising, torch, stream):
+    """Measured peak of the 32 x 32 -> 64-bit multiply in the form a Philox
+    round issues it (form 0), with the register-addend form beside it."""
+    philox_form = mulwide_rate(ising, torch, stream, 0)
+    addend_form = mulwide_rate(ising, torch, stream, 1)
+    return dict(philox_form, kernel="mulwide_probe_kernel<0>: 16 chains per thread of x = hi ^ lo of "
+                "mul.wide.u32(x, immediate), full grid", addend_form=addend_form)
 
 
 def source_digest() -> str:
@@ -203,11 +244,12 @@ def profiled_traffic(L: int):
     return round(per_spin * L * L / 2), f"ncu capture at L={rec['L']}, scaled by spins per launch"
 
 
-def sweep_roofline(torch, device, L, plane_bytes, launch_ms):
+def sweep_roofline(torch, device, L, plane_bytes, launch_ms, mul_peak=None):
     peaks, peak_kind = measured_peaks()
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     clk_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    peak_tmul = sms * SMSP_PER_SM * WIDE_MUL_PER_CLK_PER_SMSP * clk_hz / 1e12
+    derived_tmul = sms * SMSP_PER_SM * WIDE_MUL_PER_CLK_PER_SMSP * clk_hz / 1e12
+    peak_tmul = mul_peak["t_mul_per_s"] if mul_peak else derived_tmul
     spins = L * L / 2
     achieved_tmul = WIDE_MUL_PER_SPIN * spins / (launch_ms * 1e-3) / 1e12
     alg_bytes = 3 * plane_bytes  # read + write the target plane, read the source plane
@@ -217,9 +259,13 @@ def sweep_roofline(torch, device, L, plane_bytes, launch_ms):
         "bound": "alu", "achieved": round(achieved_tmul, 3), "peak": round(peak_tmul, 3),
         "unit": "T wide-mul/s", "frac": round(achieved_tmul / peak_tmul, 4), "traffic": traffic,
         "traffic_source": traffic_src,
-        "peak_derivation": f"{sms} SMs x {SMSP_PER_SM} sub-partitions x {WIDE_MUL_PER_CLK_PER_SMSP} "
-                           f"IMAD.WIDE/clk x {clk_hz / 1e6:.0f} MHz; {WIDE_MUL_PER_SPIN} wide multiplies "
-                           "per spin update (Philox4x32-10 per 4 draws)",
+        "peak_source": ("measured: wide-multiply probe on this GPU in this run (median of "
+                        f"{mul_peak['launches']} launches)" if mul_peak else "derived (probe not run)"),
+        "peak_probe": mul_peak,
+        "peak_derived": {"t_mul_per_s": round(derived_tmul, 3),
+                         "derivation": f"{sms} SMs x {SMSP_PER_SM} sub-partitions x {WIDE_MUL_PER_CLK_PER_SMSP} "
+                                       f"IMAD.WIDE/clk x {clk_hz / 1e6:.0f} MHz"},
+        "work_per_spin": f"{WIDE_MUL_PER_SPIN} wide multiplies per spin update (Philox4x32-10 per 4 draws)",
         "peak_flips_per_ns": round(peak_tmul * 1e12 / WIDE_MUL_PER_SPIN / 1e9, 1),
         "alg_bytes_per_launch": alg_bytes,
         "hbm": {"achieved": round(hbm_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -284,7 +330,8 @@ def run_ours(args, world, rank, local):
 
     _, plane_bytes = ising.ising_lattice_bytes(L, ising.ISING_MSC4)
     launch_ms = statistics.mean(black + white)
-    roofline = sweep_roofline(torch, device, L, plane_bytes, launch_ms)
+    mul_peak = mulwide_peak(ising, torch, stream)
+    roofline = sweep_roofline(torch, device, L, plane_bytes, launch_ms, mul_peak)
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
@@ -318,7 +365,8 @@ def run_ours(args, world, rank, local):
         result["scale_leg"] = run_scale_leg(ising, torch, args, device, stream)
         result["rng_probe"] = rng_probe(ising, torch, L, seed, stream)
         result["e2e"] = run_e2e(ising, torch, args, L, beta, seed, device, stream)
-        result["cpu_baseline"] = cpu_baseline(args)
+        spot = None if args.cpu_short else gpu_spot(ising, torch, lat, L, beta, seed, stream)
+        result["cpu_baseline"] = cpu_baseline(args, spot)
         if not args.no_batch:
             result["pt_batch"] = run_pt_batch(ising, torch, args, device, stream)
         if not args.no_learned:
@@ -817,20 +865,81 @@ def run_learned(ising, torch, args, device, stream):
             "note": "tau from series of this length are lower bounds where they approach the run length"}
 
 
-def cpu_baseline(args):
-    """The oracle as it stands, on the host cores: a bounded sample of the
-    same workload (a smaller lattice, same beta and start)."""
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def time_oracle(L, beta, sweeps, seed, threads):
+    """One oracle run from the keyed random start: (flips/ns, seconds)."""
     import oracle
 
-    L = args.cpu_L
-    s = oracle.init(L, oracle.MODE_RANDOM, args.seed)
-    threads = oracle.max_threads()
+    s = oracle.init(L, oracle.MODE_RANDOM, seed)
     t0 = time.perf_counter()
-    oracle.run(s, args.beta, args.cpu_sweeps, args.seed, trace=True, nthreads=threads)
+    oracle.run(s, beta, sweeps, seed, trace=True, nthreads=threads)
     dt = time.perf_counter() - t0
-    return {"value": round(L * L * args.cpu_sweeps / (dt * 1e9), 4), "unit": UNIT, "cores": threads,
-            "kind": "oracle", "sample": f"int8 L={L} random start seed {args.seed}, {args.cpu_sweeps} sweeps at "
-            f"beta={args.beta}, {threads} OpenMP threads ({dt:.1f} s)"}
+    return {"L": L, "sweeps": sweeps, "threads": threads, "flips_per_ns": round(L * L * sweeps / (dt * 1e9), 5),
+            "s": round(dt, 2)}
+
+
+def cpu_baseline(args, spot=None):
+    """The oracle as it stands, on the host cores: bounded samples of the same
+    workload (same beta and keyed random start).  The headline value is the
+    16384^2 lattice on all cores; beside it the 256^2 parity workload (1000
+    sweeps), one sweep of 16384^2 on one thread, and the at-scale spot check:
+    two oracle sweeps of the full 65536^2 lattice compared with the GPU's
+    trace and rows after the same two sweeps."""
+    import oracle
+
+    threads = oracle.max_threads()
+    main = time_oracle(args.cpu_L, args.beta, args.cpu_sweeps, args.seed, threads)
+    out = {"value": main["flips_per_ns"], "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"int8 L={args.cpu_L} random start seed {args.seed}, {args.cpu_sweeps} sweeps at "
+                     f"beta={args.beta}, {threads} OpenMP threads ({main['s']:.1f} s)",
+           "nproc": os.cpu_count(), "cpu_model": cpu_model(), "machine": os.uname().machine}
+    if args.cpu_short:
+        return out
+    out["all_cores_L16384"] = main if args.cpu_L == 16384 else time_oracle(16384, args.beta, 20, args.seed, threads)
+    out["one_thread_L16384"] = time_oracle(16384, args.beta, args.cpu_sweeps_1t, args.seed, 1)
+    out["config1_L256"] = time_oracle(256, args.beta, 1000, args.seed, threads)
+    if spot is not None:
+        L, sweeps = spot["L"], spot["sweeps"]
+        s = oracle.init(L, oracle.MODE_RANDOM, args.seed)
+        t0 = time.perf_counter()
+        tr = oracle.run(s, args.beta, sweeps, args.seed, trace=True, nthreads=threads)
+        dt = time.perf_counter() - t0
+        rows_equal = all(bool((oracle.row_from_planes_msc4(L, i, b, w) == s[i]).all())
+                         for i, (b, w) in spot["rows"].items())
+        out["spot_check_L65536"] = {
+            "L": L, "sweeps": sweeps, "threads": threads, "s": round(dt, 2),
+            "flips_per_ns": round(L * L * sweeps / (dt * 1e9), 5),
+            "trace_equal": bool((tr == spot["trace"]).all()), "rows_checked": sorted(spot["rows"]),
+            "rows_equal": rows_equal}
+        del s
+    return out
+
+
+def gpu_spot(ising, torch, lat, L, beta, seed, stream, sweeps=2):
+    """The GPU side of the at-scale spot check: the lattice re-initialised
+    from the seed, `sweeps` sweeps with the trace, and a few rows copied back."""
+    ising.ising_init_lattice(lat, ising.ISING_INIT_RANDOM, seed, stream)
+    tr = torch.zeros((sweeps, 2), dtype=torch.int64, device=stream.device)
+    ising.ising_sweep(lat, beta, sweeps, seed, 0, tr, stream)
+    torch.cuda.synchronize()
+    import numpy as np
+
+    rows = {}
+    for i in (0, 1, L // 2, L - 1):
+        b = np.ascontiguousarray(lat.black[i, :lat.row_bytes].cpu().numpy()).view(np.uint64)
+        w = np.ascontiguousarray(lat.white[i, :lat.row_bytes].cpu().numpy()).view(np.uint64)
+        rows[i] = (b.copy(), w.copy())
+    return {"L": L, "sweeps": sweeps, "trace": tr.cpu().numpy(), "rows": rows}
 
 
 # ---------------------------------------------------------------------------
@@ -841,7 +950,7 @@ def run_reference(args, world, rank):
 
     if rank != 0:
         return None
-    L = args.cpu_L
+    L = args.ref_L
     s = oracle.init(L, oracle.MODE_RANDOM, args.seed)
     threads = oracle.max_threads()
     for k in range(args.warmup):
@@ -873,7 +982,8 @@ def main(argv=None):
         res = run_reference(args, world, rank)
     elif args.workload == "pt":
         res = run_pt_only(args, world, rank, local)
-    elif args.workload == "slabs":
+    elif args.workload == "slabs" or (args.workload == "sweep" and world > 1):
+        # several GPUs: one lattice cut into one horizontal slab per rank (Sec. 4)
         res = run_slabs(args, world, rank, local)
     elif args.workload == "host":
         # the host-buffer legs alone: one sweep per step of the L^2 lattice

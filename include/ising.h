@@ -37,6 +37,10 @@
  *     the given stream (NULL = legacy default stream) unless stated.
  *   - Errors: every call returns an ising_status; arguments are checked before
  *     any work is queued, and nothing aborts the process.
+ *   - Per-device state: streams, events, instantiated graphs and symbol
+ *     addresses that some entry points create on first use are kept per
+ *     device for the life of the process.  Do not use the library on a device
+ *     after a cudaDeviceReset of that device.
  */
 #ifndef ISING_H
 #define ISING_H
@@ -169,9 +173,28 @@ ISING_API int ising_unpack(const ising_lattice_t *msc4_src, const ising_lattice_
  * compute the Philox block with counter (q_lo, q_hi, t_lo, colour | t_hi << 8)
  * and key (seed), compare each of its 4 words with threshold T3 and ADD the
  * number of words below it to *count_dev (uint64, caller zeroes it).  Used to
- * measure the generator's throughput ceiling and to check the stream. */
+ * measure the generator's throughput ceiling and to check the stream.  The
+ * kernel is shaped like the sweep's draws: each thread step makes 8 blocks
+ * sharing counter words 1..3, with 32-bit indices, on a full grid.  EINVAL:
+ * colour not 0 or 1, n_blocks > 2^34. */
 ISING_API int ising_rng_probe(uint64_t n_blocks, uint64_t seed, uint64_t t, int32_t colour, uint32_t T3,
                               uint64_t *count_dev, ising_stream_t stream);
+
+/* Throughput probe of the 32 x 32 -> 64-bit multiply that every Philox round
+ * is built on (two per round, 20 per block of 4 draws; Sec. 3.3 draws the
+ * random numbers inside the sweep kernel, so this multiply bounds it).  Not a
+ * step of the method.  One launch on a full grid of the current device:
+ * every thread runs 16 independent chains of `iters` dependent wide
+ * multiplies, with no memory traffic.  form 0 is the multiply as a Philox
+ * round issues it (by an immediate multiplier, no addend; the chain goes on
+ * through the XOR of the product's halves); form 1 is a multiply-add with a
+ * 64-bit register addend.  *multiplies (host) receives the number of wide
+ * multiplies the launch performs; time the launch on `stream` to get the
+ * rate.  sink_dev (one uint64, device) may be incremented: it keeps the
+ * chains from being optimised away.  EINVAL: form not 0 or 1, iters == 0,
+ * NULL pointers. */
+ISING_API int ising_mulwide_probe(int32_t form, uint32_t iters, uint64_t *sink_dev, uint64_t *multiplies,
+                                  ising_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Horizontal slabs (Sec. 4: the lattice is cut into horizontal slabs, each   */
@@ -197,7 +220,11 @@ typedef struct {
     int64_t row0;             /* global row of the first own row, 0 <= row0 < L */
     int64_t rows;             /* own rows, 1 <= rows, row0 + rows <= L */
     int32_t layout;           /* must be ISING_MSC4 */
-    int32_t reserved;         /* must be 0 */
+    int32_t spare_sms;        /* SMs the half-sweep kernel leaves without a block
+                                 (0: none; at most the device's SMs - 1), so that
+                                 kernels of another stream, such as the halo
+                                 messages of a multi-rank sweep, can run beside
+                                 it */
     int64_t row_stride_bytes; /* bytes between plane rows; >= L / 4 */
 } ising_slab_t;
 
@@ -264,7 +291,10 @@ typedef struct ising_batch ising_batch_t;
 
 /* Workspace bytes for a batch.  EINVAL: n not a multiple of S, a side not a
  * multiple of 32 in [32, 65536], unequal sides within a ladder, betas not
- * increasing by >= 1e-4 or not > 0. */
+ * increasing by >= 1e-4 or not > 0, or a beta so small (below about 1.4e-17)
+ * that exp(-4 beta) rounds to 1: the batched decision holds the a = 3 and
+ * a = 4 thresholds as 32-bit words and has no form for the always-flip
+ * entry 2^32. */
 ISING_API int ising_batch_bytes(int64_t n, const int64_t *L, int32_t ladder_size, const double *beta,
                                 size_t *bytes);
 
@@ -326,11 +356,18 @@ ISING_API int ising_batch_barrier_selftest(ising_batch_t *batch, int64_t timeout
  * library, which every GPU that loads the library holds until exit.  Batches
  * whose scratch exceeds it are rejected with ISING_EINVAL and a message
  * giving the size.  The first call on a device looks up the array's address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Calls share the array: calls that overlap on
- * the GPU race.  Each call clears what must start at zero.  Synchronous:
- * returns after the sweeps, with ISING_ETIMEOUT if a barrier wait ran out.
- * Results equal ising_batch_run's for the same arguments. */
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life
+ * of the process: do not use the library across a cudaDeviceReset.  Calls
+ * share the array: calls that overlap on the GPU race.  Each call clears what
+ * must start at zero.  Synchronous (it waits on `stream` and reads words back
+ * to the host), so it can never be called on a capturing stream: returns
+ * after the sweeps, with ISING_ETIMEOUT if a barrier wait ran out.  Before
+ * any launch it checks the caller's buffers: planes 16-byte aligned, trace
+ * 8-byte and slot arrays 4-byte aligned, each inside its device allocation;
+ * the slot arrays are read back and must be a valid state (slot_of[i] in
+ * [0, S), lattice_at[l*S + k] a lattice of ladder l, the two inverse to each
+ * other), else ISING_EINVAL.  Results equal ising_batch_run's for the same
+ * arguments. */
 ISING_API int ising_batch_run_noalloc(int64_t n, const int64_t *L, int32_t ladder_size, const double *beta,
                                       void *black_dev, void *white_dev, int32_t *slot_of_dev,
                                       int32_t *lattice_at_dev, int64_t n_sweeps, uint64_t seed,

@@ -51,7 +51,7 @@ class ising_slab_t(ctypes.Structure):
         ("row0", ctypes.c_int64),
         ("rows", ctypes.c_int64),
         ("layout", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("spare_sms", ctypes.c_int32),
         ("row_stride_bytes", ctypes.c_int64),
     ]
 
@@ -91,6 +91,7 @@ def _load():
             "ising_pack": [LP, LP, P],
             "ising_unpack": [LP, LP, P],
             "ising_rng_probe": [u64, u64, u64, i32, u32, P, P],
+            "ising_mulwide_probe": [i32, u32, P, P, P],
             "ising_slab_bytes": [i64, i64, i32, P, P],
             "ising_slab_init": [SP, i32, u64, P],
             "ising_slab_half_sweep": [SP, dbl, i32, u64, u64, P, P],
@@ -275,6 +276,16 @@ def ising_rng_probe(n_blocks: int, seed: int, t: int, colour: int, T3: int, coun
     _check(_load().ising_rng_probe(n_blocks, seed, t, colour, T3, _addr(count), _stream(stream)), "ising_rng_probe")
 
 
+def ising_mulwide_probe(form: int, iters: int, sink, stream=None) -> int:
+    """Launches the wide-multiply throughput probe (form 0: as a Philox round
+    issues it; form 1: with a 64-bit addend); returns the number of
+    32 x 32 -> 64-bit multiplies the launch performs."""
+    n = ctypes.c_uint64()
+    _check(_load().ising_mulwide_probe(form, iters, _addr(sink), ctypes.byref(n), _stream(stream)),
+           "ising_mulwide_probe")
+    return n.value
+
+
 # ---------------------------------------------------------------------------
 # Lattice storage (PyTorch owns the device memory)
 # ---------------------------------------------------------------------------
@@ -395,10 +406,26 @@ class Slab:
         self.row_bytes, _ = ising_slab_bytes(self.L, self.rows)
         self.black = torch.zeros((self.rows + 2, self.row_bytes), dtype=torch.uint8, device=device)
         self.white = torch.zeros((self.rows + 2, self.row_bytes), dtype=torch.uint8, device=device)
+        self.spare_sms = 0
 
     def struct(self) -> ising_slab_t:
-        return ising_slab_t(self.black.data_ptr(), self.white.data_ptr(), self.L, self.row0, self.rows, ISING_MSC4, 0,
-                            self.row_bytes)
+        return ising_slab_t(self.black.data_ptr(), self.white.data_ptr(), self.L, self.row0, self.rows, ISING_MSC4,
+                            self.spare_sms, self.row_bytes)
+
+    def view(self, first: int, count: int, spare_sms: int = 0) -> "Slab":
+        """Own rows first .. first+count-1 as a slab of their own, sharing this
+        slab's storage: its halo rows are the rows next to them (own rows of
+        this slab, or this slab's halos at its ends).  A half-sweep of the
+        view updates exactly those rows as the half-sweep of the whole slab
+        does (the random numbers are keyed by the global row)."""
+        if not (0 <= first and count >= 1 and first + count <= self.rows):
+            raise ValueError(f"rows {first}..{first + count - 1} are not own rows of a {self.rows}-row slab")
+        v = Slab.__new__(Slab)
+        v.L, v.row0, v.rows, v.row_bytes = self.L, self.row0 + first, int(count), self.row_bytes
+        v.black = self.black[first:first + count + 2]
+        v.white = self.white[first:first + count + 2]
+        v.spare_sms = int(spare_sms)
+        return v
 
     def plane(self, colour: int):
         return self.black if colour == 0 else self.white
@@ -428,22 +455,16 @@ def _world(group):
     return dist.get_rank(group), dist.get_world_size(group)
 
 
-def exchange_halos(slab: Slab, colour: int, group=None, stream=None):
-    """Make the colour-`colour` halo rows of this rank's slab current.  Rank r
-    holds the r-th slab of the lattice (ranks in row order, periodic): its
-    halo above receives the last own row of rank r-1, its halo below the first
-    own row of rank r+1.  One process: the library's copy (the slab is its own
-    neighbour).  Several: point-to-point messages of one row each through
-    torch.distributed (NCCL between GPUs), tagged 0 for rows travelling down
-    and 1 for rows travelling up; with two ranks both messages between the
-    pair are posted in the same order on both sides, so they also match where
-    tags are ignored."""
+def _post_halos(slab: Slab, colour: int, group=None, stream=None):
+    """Start making the colour-`colour` halo rows of this rank's slab current
+    and return what to wait for (a list of torch.distributed works, empty when
+    the exchange was queued on `stream` itself)."""
     import torch.distributed as dist
 
     rank, world = _world(group)
     if world == 1:
         ising_slab_exchange([slab], colour, stream)
-        return
+        return []
     p = slab.plane(colour)
     up, down = (rank - 1) % world, (rank + 1) % world
     peer = (lambda r: dist.get_global_rank(group, r)) if group is not None else (lambda r: r)
@@ -454,35 +475,78 @@ def exchange_halos(slab: Slab, colour: int, group=None, stream=None):
         dist.P2POp(dist.irecv, p[slab.rows + 1], peer(down), group, tag=1),
     ]
     with _on_stream(stream):  # messages ordered after the half-sweeps queued on `stream`
-        for w in dist.batch_isend_irecv(ops):
+        return dist.batch_isend_irecv(ops)
+
+
+def _wait_halos(works, stream=None):
+    with _on_stream(stream):  # NCCL: `stream` waits for the messages; gloo: the host does
+        for w in works:
             w.wait()
 
 
+def exchange_halos(slab: Slab, colour: int, group=None, stream=None):
+    """Make the colour-`colour` halo rows of this rank's slab current.  Rank r
+    holds the r-th slab of the lattice (ranks in row order, periodic): its
+    halo above receives the last own row of rank r-1, its halo below the first
+    own row of rank r+1.  One process: the library's copy (the slab is its own
+    neighbour).  Several: point-to-point messages of one row each through
+    torch.distributed (NCCL between GPUs), tagged 0 for rows travelling down
+    and 1 for rows travelling up; with two ranks both messages between the
+    pair are posted in the same order on both sides, so they also match where
+    tags are ignored."""
+    _wait_halos(_post_halos(slab, colour, group, stream), stream)
+
+
 def slab_sweep(slab: Slab, beta: float, n_sweeps: int, seed: int, sweep_offset: int = 0, trace=None, group=None,
-               half_sweep=None, stream=None):
+               half_sweep=None, stream=None, overlap: bool = True):
     """n_sweeps sweeps of a lattice distributed as one slab per rank (Sec. 4).
-    Per sweep: white halos, black half-sweep, black halos, white half-sweep;
     `trace` (n_sweeps x 2 int64, on the slab's device) ends with the
     whole-lattice sums {sum of spins, sum over bonds} after each sweep.  The
     lattice equals ising_sweep of the whole lattice bit for bit.
 
+    Order without overlap, per sweep: white halos, black half-sweep, black
+    halos, white half-sweep.  With overlap (slabs of 3 rows or more), each
+    half-sweep first updates the slab's first and last own rows, then posts
+    those rows' messages to the neighbours and updates the interior rows
+    while the messages travel; the next half-sweep waits for them before it
+    starts.  The interior update leaves `slab.spare_sms` (at least one when
+    there are several ranks) SMs free, so that the messages' kernels can run
+    beside it.  Both orders give the same lattice: a half-sweep reads only the
+    other colour's rows, and the boundary rows it sends are final once updated.
+
     ``half_sweep(slab, beta, colour, seed, t, obs)`` does the update of one
-    colour of the slab's own rows; the default is the library's
+    colour of a slab's own rows; the default is the library's
     ising_slab_half_sweep.  Replacing it lets the exchange and ordering logic
     run against another implementation of the same rule."""
     import torch.distributed as dist
 
     hs = half_sweep or (lambda sl, b, c, sd, t, obs: ising_slab_half_sweep(sl, b, c, sd, t, obs, stream))
     _, world = _world(group)
+    rows = slab.rows
     with _on_stream(stream):  # the fill, the messages and the half-sweeps in one stream order
         if trace is not None:
             trace.zero_()
-        for k in range(n_sweeps):
-            t = sweep_offset + k
-            exchange_halos(slab, 1, group, stream)
-            hs(slab, beta, 0, seed, t, None)
-            exchange_halos(slab, 0, group, stream)
-            hs(slab, beta, 1, seed, t, trace[k] if trace is not None else None)
+        if not overlap or rows < 3:
+            for k in range(n_sweeps):
+                t = sweep_offset + k
+                exchange_halos(slab, 1, group, stream)
+                hs(slab, beta, 0, seed, t, None)
+                exchange_halos(slab, 0, group, stream)
+                hs(slab, beta, 1, seed, t, trace[k] if trace is not None else None)
+        else:
+            first, last = slab.view(0, 1), slab.view(rows - 1, 1)
+            interior = slab.view(1, rows - 2, spare_sms=max(slab.spare_sms, 1 if world > 1 else 0))
+            if n_sweeps > 0:
+                exchange_halos(slab, 1, group, stream)
+            for k in range(n_sweeps):
+                t = sweep_offset + k
+                for colour in (0, 1):
+                    obs = trace[k] if (trace is not None and colour == 1) else None
+                    hs(first, beta, colour, seed, t, obs)
+                    hs(last, beta, colour, seed, t, obs)
+                    works = _post_halos(slab, colour, group, stream)
+                    hs(interior, beta, colour, seed, t, obs)
+                    _wait_halos(works, stream)
         if trace is not None and world > 1:
             dist.all_reduce(trace, group=group)
 

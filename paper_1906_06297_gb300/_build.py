@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libising.so")
-SOURCES = ["api.cu", "msc4.cu", "bits.cu", "int8.cu", "batch.cu", "learned.cu"]
+SOURCES = ["api.cu", "msc4.cu", "bits.cu", "int8.cu", "batch.cu", "learned.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
                      f"-I{INCLUDE}"]

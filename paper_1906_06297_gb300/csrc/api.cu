@@ -166,7 +166,7 @@ int check_slab(const ising_slab_t *sl)
     size_t row = 0;
     int rc = row_bytes_of(sl->L, sl->layout, &row);
     if (rc) return rc;
-    if (sl->reserved != 0) return fail(ISING_EINVAL, "reserved field must be 0");
+    if (sl->spare_sms < 0 || sl->spare_sms > 4095) return fail(ISING_EINVAL, "spare_sms = %d out of range", sl->spare_sms);
     if (sl->rows < 1) return fail(ISING_EINVAL, "slab rows = %lld must be >= 1", (long long)sl->rows);
     if (sl->row0 < 0 || sl->row0 >= sl->L || sl->rows > sl->L - sl->row0)
         return fail(ISING_EINVAL, "slab rows [%lld, %lld) are not inside 0..L-1 (L = %lld)", (long long)sl->row0,
@@ -290,7 +290,13 @@ int slab_half_sweep_impl(const ising_slab_t *sl, const Accept &acc, const RoundK
     p.acc = acc;
     p.rk = rk;
     p.obs = (long long *)obs;
-    cudaError_t e = msc4_half_sweep(p, colour, s);
+    p.spare_sms = sl->spare_sms;
+    DeviceInfo info;
+    cudaError_t e = device_info(&info);
+    if (e != cudaSuccess) return cuda_fail(e, "device info");
+    if (sl->spare_sms >= info.sm_count)
+        return fail(ISING_EINVAL, "spare_sms = %d leaves no SM of %d", sl->spare_sms, info.sm_count);
+    e = msc4_half_sweep(p, colour, s);
     return e == cudaSuccess ? ISING_OK : cuda_fail(e, "slab half-sweep launch");
 }
 
@@ -1049,6 +1055,7 @@ ISING_API int ising_rng_probe(uint64_t n_blocks, uint64_t seed, uint64_t t, int3
                               uint64_t *count_dev, ising_stream_t stream)
 {
     if (colour != 0 && colour != 1) return fail(ISING_EINVAL, "colour must be 0 or 1");
+    if (n_blocks > (uint64_t(1) << 34)) return fail(ISING_EINVAL, "n_blocks must be at most 2^34");
     int rc = check_device_range(count_dev, sizeof(uint64_t), "count");
     if (rc) return rc;
     if (n_blocks == 0) return ISING_OK;
@@ -1056,6 +1063,17 @@ ISING_API int ising_rng_probe(uint64_t n_blocks, uint64_t seed, uint64_t t, int3
                               counter_word3(colour, kPurposeMetropolis, t), T3, (unsigned long long *)count_dev,
                               (cudaStream_t)stream);
     return e == cudaSuccess ? ISING_OK : cuda_fail(e, "rng probe launch");
+}
+
+ISING_API int ising_mulwide_probe(int32_t form, uint32_t iters, uint64_t *sink_dev, uint64_t *multiplies,
+                                  ising_stream_t stream)
+{
+    if (form != 0 && form != 1) return fail(ISING_EINVAL, "form must be 0 or 1");
+    if (iters == 0 || multiplies == nullptr) return fail(ISING_EINVAL, "iters must be > 0 and multiplies non-NULL");
+    int rc = check_device_range(sink_dev, sizeof(uint64_t), "sink");
+    if (rc) return rc;
+    cudaError_t e = mulwide_probe(form, iters, (unsigned long long *)sink_dev, multiplies, (cudaStream_t)stream);
+    return e == cudaSuccess ? ISING_OK : cuda_fail(e, "multiply probe launch");
 }
 
 }  // extern "C"

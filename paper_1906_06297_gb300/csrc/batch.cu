@@ -589,6 +589,17 @@ static int check_batch_args(int64_t n, const int64_t *L, int32_t S, const double
             return bfail(ISING_EINVAL, "betas must increase by at least 1e-4");
     }
     if (beta[0] <= 0.0) return bfail(ISING_EINVAL, "beta = 0 is not supported in a batch");
+    // The batched decision compares each draw with T3 and T4 as 32-bit words
+    // (flip iff d >= [u >= T3] + [u >= T4]); a threshold of 2^32 (p = 1, the
+    // Metropolis rule of Sec. 2 flipping always) has no 32-bit form there.
+    // exp(-4 beta) rounds to 1 in FP64 for beta below about 1.4e-17, so such
+    // betas are refused rather than run with a truncated table.
+    for (int32_t k = 0; k < S; ++k) {
+        uint64_t T[5];
+        if (ising_thresholds(beta[k], T) != ISING_OK) return bfail(ISING_EINVAL, "bad beta");
+        if (T[3] >= (uint64_t(1) << 32) || T[4] >= (uint64_t(1) << 32))
+            return bfail(ISING_EINVAL, "beta too small for a batch: exp(-4 beta) rounds to 1 (use beta >= 1e-16)");
+    }
     return ISING_OK;
 }
 
@@ -1017,7 +1028,13 @@ extern "C" ISING_API int ising_batch_run_noalloc(int64_t n, const int64_t *L, in
                  o, (size_t)ISING_NOALLOC_SCRATCH_BYTES);
         return bfail(ISING_EINVAL, msg);
     }
-    // the caller's buffers must cover what the kernel touches
+    // the caller's buffers must be aligned for the kernel's accesses and cover
+    // what the kernel touches
+    if (((uintptr_t)black_dev | (uintptr_t)white_dev) % 16 != 0)
+        return bfail(ISING_EINVAL, "black_dev and white_dev must be 16-byte aligned");
+    if (((uintptr_t)slot_of_dev | (uintptr_t)lattice_at_dev) % 4 != 0)
+        return bfail(ISING_EINVAL, "slot_of_dev and lattice_at_dev must be 4-byte aligned");
+    if ((uintptr_t)trace_dev % 8 != 0) return bfail(ISING_EINVAL, "trace_dev must be 8-byte aligned");
     const size_t plane = lay.plane_words * 8;
     if (check_device_range(black_dev, plane, "black") || check_device_range(white_dev, plane, "white") ||
         check_device_range(slot_of_dev, (size_t)n * 4, "slot_of") ||
@@ -1029,11 +1046,31 @@ extern "C" ISING_API int ising_batch_run_noalloc(int64_t n, const int64_t *L, in
         if (events > 0 && check_device_range(trace_dev, (size_t)events * (size_t)n * 16, "trace") != ISING_OK)
             return bfail(ISING_EINVAL, "trace must be device memory of events x n x 2 int64");
     }
+    cudaStream_t s = (cudaStream_t)stream;
+    // The kernel indexes its tables and the planes with the slot state, which
+    // here is the caller's (ising_batch_run fills its own): read it back and
+    // check that it is a valid state before anything is launched.
+    {
+        std::vector<int32_t> slot((size_t)n), at((size_t)n);
+        cudaError_t ce = cudaMemcpyAsync(slot.data(), slot_of_dev, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(at.data(), lattice_at_dev, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) return bfail(ISING_ECUDA, cudaGetErrorString(ce));
+        for (int64_t i = 0; i < n; ++i)
+            if (slot[(size_t)i] < 0 || slot[(size_t)i] >= ladder_size)
+                return bfail(ISING_EINVAL, "slot_of holds a slot outside [0, ladder_size)");
+        for (int64_t l = 0; l < n / ladder_size; ++l)
+            for (int32_t k = 0; k < ladder_size; ++k) {
+                const int64_t a = at[(size_t)(l * ladder_size + k)];
+                if (a < l * ladder_size || a >= (l + 1) * ladder_size || slot[(size_t)a] != k)
+                    return bfail(ISING_EINVAL, "lattice_at is not the inverse of slot_of within each ladder");
+            }
+    }
     void *scr = nullptr;
     rc = noalloc_scratch(&scr);
     if (rc) return rc;
     char *sc = (char *)scr;
-    cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(sc + s_thr, thr.data(), thr.size() * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !len.empty())
         e = cudaMemcpyAsync(sc + s_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice, s);

@@ -102,6 +102,7 @@ struct Msc4SweepParams {
     Accept acc;
     RoundKeys rk;
     long long *obs;       // {sum s, sum bonds} accumulators or nullptr
+    int32_t spare_sms = 0;  // host side: SMs the launch leaves without a block
 };
 
 struct Int8SweepParams {

@@ -113,25 +113,6 @@ __global__ void __launch_bounds__(256) int8_obs_kernel(const int8_t *black, cons
     block_reduce_add2<256>(sum_s, sum_b, out);
 }
 
-__global__ void __launch_bounds__(256) rng_probe_kernel(uint64_t n_blocks, const __grid_constant__ RoundKeys rk,
-                                                        uint32_t c2, uint32_t c3, uint32_t T3,
-                                                        unsigned long long *count)
-{
-    long long cnt = 0;
-    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_blocks;
-         q += (uint64_t)gridDim.x * blockDim.x) {
-        const uint4 u = philox((uint32_t)q, (uint32_t)(q >> 32), c2, c3, rk);
-        cnt += (u.x < T3) + (u.y < T3) + (u.z < T3) + (u.w < T3);
-    }
-    long long zero = 0;
-    __shared__ long long buf[2];
-    if (threadIdx.x == 0) buf[0] = buf[1] = 0;
-    __syncthreads();
-    block_reduce_add2<256>(cnt, zero, buf);
-    __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(count, (unsigned long long)buf[0]);
-}
-
 unsigned grid_for(int64_t n, int threads, int per_sm)
 {
     DeviceInfo info{1};
@@ -170,14 +151,6 @@ cudaError_t int8_observables(const int8_t *black, const int8_t *white, int64_t L
                              cudaStream_t s)
 {
     int8_obs_kernel<<<grid_for(L * (L / 2), 256, 8), 256, 0, s>>>(black, white, L, stride, out);
-    return cudaGetLastError();
-}
-
-cudaError_t rng_probe(uint64_t n_blocks, const RoundKeys &rk, uint32_t c2, uint32_t c3, uint32_t T3,
-                      unsigned long long *count, cudaStream_t s)
-{
-    rng_probe_kernel<<<grid_for((int64_t)std::min<uint64_t>(n_blocks, 1ull << 40), 256, 8), 256, 0, s>>>(
-        n_blocks, rk, c2, c3, T3, count);
     return cudaGetLastError();
 }
 

@@ -57,9 +57,12 @@ cudaError_t int8_half_sweep(const Int8SweepParams &p, int colour, cudaStream_t s
 cudaError_t int8_observables(const int8_t *black, const int8_t *white, int64_t L, int64_t stride,
                              long long *out, cudaStream_t s);
 
-// Generator alone.
+// Throughput probes (probe.cu): the generator alone, shaped like the sweep
+// (n_blocks <= 2^34), and the 32 x 32 -> 64-bit multiply alone (*multiplies
+// receives the number the launch performs).
 cudaError_t rng_probe(uint64_t n_blocks, const RoundKeys &rk, uint32_t c2, uint32_t c3, uint32_t T3,
                       unsigned long long *count, cudaStream_t s);
+cudaError_t mulwide_probe(int form, uint32_t iters, unsigned long long *sink, uint64_t *multiplies, cudaStream_t s);
 
 // ISING_OK if [ptr, ptr + bytes) is device memory of the current device inside
 // one allocation; else ISING_EINVAL with the reason in ising_last_error().

@@ -15,10 +15,13 @@
 //
 // Sweep kernel design (GB300, sm_103a):
 //   * Each warp owns a 64-word column chunk (lane l holds words 2l, 2l+1, one
-//     128-bit load per plane row) and marches down a contiguous range of rows,
-//     keeping rows i-1, i, i+1 of the source plane in registers: every source
-//     word is read from memory once per half-sweep (plus one halo row at each
-//     end of the range).
+//     16-byte copy per plane row) and marches down a contiguous range of rows.
+//     Rows i-1, i, i+1 of the source plane, the target row and the next rows
+//     in flight sit in a per-warp ring in shared memory, filled by cp.async
+//     two rows ahead: every source word is read from memory once per
+//     half-sweep (plus one halo row at each end of the range), and moving to
+//     the next row changes which slot is read instead of moving registers
+//     (register moves would compete with Philox for the multiply-add pipe).
 //   * The side word is the neighbouring lane's centre word (one warp shuffle);
 //     only the chunk edges read a single extra word.
 //   * Work is split evenly: the (chunk, row) units of the plane are cut into
@@ -28,7 +31,7 @@
 //     thresholds; everything else is bit-parallel over nibbles.
 //   * Observables (white half-sweep): after the update, each white site adds
 //     s * (sum of its 4 black neighbours), which visits every bond once; the
-//     black centre words already in registers give the black magnetisation.
+//     black centre words already loaded give the black magnetisation.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -54,43 +57,58 @@ constexpr int kThreads = ISING_MSC4_THREADS;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMinRowsPerWarp = 16;
 
-// 128-bit load that only the lanes holding words execute; the registers of
-// the other lanes are left undefined (their values never reach a valid lane).
-__device__ __forceinline__ uint4 ld128_if(const uint64_t *p, bool pred)
-{
-    uint4 v;
-    asm volatile("{\n\t"
-                 ".reg .pred q;\n\t"
-                 "setp.ne.b32 q, %5, 0;\n\t"
-                 "@q ld.global.v4.u32 {%0, %1, %2, %3}, [%4];\n\t"
-                 "}"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p), "r"((int)pred));
-    return v;
-}
-
-__device__ __forceinline__ uint32_t ld32_if(const uint32_t *p, bool pred)
-{
-    uint32_t v;
-    asm volatile("{\n\t"
-                 ".reg .pred q;\n\t"
-                 "setp.ne.b32 q, %2, 0;\n\t"
-                 "@q ld.global.u32 %0, [%1];\n\t"
-                 "}"
-                 : "=r"(v)
-                 : "l"(p), "r"((int)pred));
-    return v;
-}
-
 __device__ __forceinline__ void st128(uint64_t *p, uint4 v)
 {
     *reinterpret_cast<uint4 *>(p) = v;
 }
 
-template <int COLOR, bool OBS, bool ALWAYS>
+// Each warp keeps its lanes' rows in a ring in shared memory: 4 source rows
+// (r-1, r, r+1 and the row r+2 being fetched), 2 target rows and the 4 edge
+// words that belong to the source rows.  A lane only ever reads the slots it
+// filled itself, so no lane waits for another.
+constexpr int kRing = 4;
+struct WarpRing {
+    uint4 src[kRing][32];
+    uint4 tgt[2][32];
+    uint32_t edge[kRing][32];
+};
+constexpr size_t kRingBytes = sizeof(WarpRing) * kWarps;
+
+// Asynchronous global -> shared copies of 16 / 4 bytes that only lanes with
+// `pred` issue (cp.async: no registers hold the data in flight).
+__device__ __forceinline__ void cp16_if(void *smem, const void *gmem, bool pred)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("{\n\t"
+                 ".reg .pred q;\n\t"
+                 "setp.ne.b32 q, %2, 0;\n\t"
+                 "@q cp.async.cg.shared.global [%0], [%1], 16;\n\t"
+                 "}" ::"r"(s), "l"(gmem), "r"((int)pred) : "memory");
+}
+
+__device__ __forceinline__ void cp4_if(void *smem, const void *gmem, bool pred)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("{\n\t"
+                 ".reg .pred q;\n\t"
+                 "setp.ne.b32 q, %2, 0;\n\t"
+                 "@q cp.async.ca.shared.global [%0], [%1], 4;\n\t"
+                 "}" ::"r"(s), "l"(gmem), "r"((int)pred) : "memory");
+}
+
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// all groups but the most recent one have landed (and are visible to this thread)
+__device__ __forceinline__ void cp_wait_all_but_last() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Q64: the Philox counter q = site / 4 needs 64 bits (L above 185363);
+// otherwise its high word is 0 and only the low word is carried per row.
+template <int COLOR, bool OBS, bool ALWAYS, bool Q64>
 __global__ void __launch_bounds__(kThreads, ISING_MSC4_MIN_BLOCKS)
     msc4_sweep_kernel(const __grid_constant__ Msc4SweepParams p)
 {
+    extern __shared__ __align__(16) unsigned char ring_smem[];
+    WarpRing &ring = reinterpret_cast<WarpRing *>(ring_smem)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t nw = (int64_t)gridDim.x * kWarps;
@@ -99,13 +117,15 @@ __global__ void __launch_bounds__(kThreads, ISING_MSC4_MIN_BLOCKS)
     const int64_t R = p.rows, stride = p.stride;
     // row r (local) has the neighbour word on the left iff r + pofs is even
     const int64_t pofs = p.row0 + COLOR;
+    // local row indices fit 32 bits (rows <= L <= 2^18)
+    const int32_t wrap_row = (int32_t)p.wrap_row, wrap_to = (int32_t)p.wrap_to;
 
     uint32_t ones = 0, dsum = 0, nrows = 0;
 
     for (int64_t lin = begin; lin < end;) {
         const int64_t chunk = lin / R;
-        const int64_t r0 = lin - chunk * R;
-        const int64_t r1 = min(R, r0 + (end - lin));
+        const int32_t r0 = (int32_t)(lin - chunk * R);
+        const int32_t r1 = (int32_t)min(R, r0 + (end - lin));
         lin += r1 - r0;
 
         const int64_t w0 = chunk * 64 + 2 * lane;
@@ -118,36 +138,43 @@ __global__ void __launch_bounds__(kThreads, ISING_MSC4_MIN_BLOCKS)
         const int64_t off_left = 2 * ((w0 == 0 ? p.wpr : w0) - 1 - w0) + 1;
         const int64_t off_right = 2 * ((w0 + 2 >= p.wpr ? 0 : w0 + 2) - w0);
         const bool edge_left = lane == 0;
-
         const uint64_t *col = p.src + w0;  // this lane's column of the source plane
-        auto edge_of = [&](const uint64_t *row, int64_t r) -> uint32_t {
-            const bool left = ((r + pofs) & 1) == 0;
-            const uint32_t *h = reinterpret_cast<const uint32_t *>(row) + (left ? off_left : off_right);
-            return ld32_if(h, left ? edge_left : edge_right);
+        // source row `row` (local index, wrapped) and its edge word into slot k
+        auto fetch_src = [&](const uint64_t *rowp, int32_t row, int k) {
+            cp16_if(&ring.src[k][lane], rowp, valid);
+            const bool left = ((row + pofs) & 1) == 0;
+            const uint32_t *h = reinterpret_cast<const uint32_t *>(rowp) + (left ? off_left : off_right);
+            cp4_if(&ring.edge[k][lane], h, left ? edge_left : edge_right);
         };
 
-        // rows r-1, r, r+1 of the source and row r of the target are in
-        // registers at the top of each iteration; rows r+2 / r+1 are fetched
-        // before the arithmetic of row r
-        // row of the next source fetch
-        int64_t rn = r0 + 2 >= p.wrap_row ? r0 + 2 - p.wrap_row + p.wrap_to : r0 + 2;
-        const uint64_t *pn = col + rn * stride;
-        const uint64_t *p_up = col + (r0 == 0 ? p.first_up : r0 - 1) * stride;
-        const uint64_t *p_cur = col + r0 * stride;
-        const uint64_t *p_dn = col + (r0 + 1 == p.wrap_row ? p.wrap_to : r0 + 1) * stride;
-        uint4 up = ld128_if(p_up, valid);
-        uint4 cur = ld128_if(p_cur, valid);
-        uint4 dn = ld128_if(p_dn, valid);
-        uint32_t edge = edge_of(p_cur, r0);
-        uint32_t edge_dn = edge_of(p_dn, r0 + 1);
-        uint64_t *tp = p.tgt + w0 + r0 * stride;  // target row r
-        uint4 tg = ld128_if(tp, valid);
+        // rows r0-1, r0, r0+1 of the source and row r0 of the target, then in
+        // each iteration the source row two ahead and the next target row
+        int32_t rn = r0 + 2 >= wrap_row ? r0 + 2 - wrap_row + wrap_to : r0 + 2;
+        const uint64_t *pn = col + (int64_t)rn * stride;
+        {
+            const int64_t ru = r0 == 0 ? p.first_up : r0 - 1;
+            const int32_t rd = r0 + 1 == wrap_row ? wrap_to : r0 + 1;
+            cp16_if(&ring.src[(r0 + 3) & 3][lane], col + ru * stride, valid);
+            fetch_src(col + (int64_t)r0 * stride, r0, r0 & 3);
+            fetch_src(col + (int64_t)rd * stride, r0 + 1, (r0 + 1) & 3);
+            cp16_if(&ring.tgt[r0 & 1][lane], p.tgt + w0 + (int64_t)r0 * stride, valid);
+            cp_commit();
+        }
+        uint64_t *tp = p.tgt + w0 + (int64_t)r0 * stride;  // target row r
         uint64_t q0 = (uint64_t)(p.row0 + r0) * (uint64_t)p.qrow + 4 * (uint64_t)w0;
+        uint32_t q32 = (uint32_t)q0;
 
-        for (int64_t r = r0; r < r1; ++r) {
-            const uint4 nxt = ld128_if(pn, valid);
-            const uint32_t edge_nxt = edge_of(pn, rn);
-            const uint4 tg_nxt = ld128_if(tp + stride, valid && r + 1 < r1);
+        for (int32_t r = r0; r < r1; ++r) {
+            const int k = r & 3;
+            fetch_src(pn, rn, (k + 2) & 3);
+            cp16_if(&ring.tgt[(k + 1) & 1][lane], tp + stride, valid && r + 1 < r1);
+            cp_commit();
+            cp_wait_all_but_last();  // rows r-1 .. r+1, target row r and the edge of row r
+            const uint4 up = ring.src[(k + 3) & 3][lane];
+            const uint4 cur = ring.src[k][lane];
+            const uint4 dn = ring.src[(k + 1) & 3][lane];
+            const uint4 tg = ring.tgt[k & 1][lane];
+            const uint32_t edge = ring.edge[k][lane];
 
             // side words, as 32-bit halves: .x/.y = lo/hi of word w0, .z/.w of w0+1
             uint4 sd;
@@ -168,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, ISING_MSC4_MIN_BLOCKS)
             }
             // Philox blocks q0 .. q0+7 cover the lane's 32 sites; q0 % 8 == 0,
             // so the low counter word never carries within them
-            const uint32_t c0 = (uint32_t)q0, c1 = (uint32_t)(q0 >> 32);
+            const uint32_t c0 = Q64 ? (uint32_t)q0 : q32, c1 = Q64 ? (uint32_t)(q0 >> 32) : 0u;
             uint32_t dacc = 0;
             uint4 ns;
             // nibble-wise neighbour sums stay in 0..4: no carry leaves a nibble
@@ -188,20 +215,18 @@ __global__ void __launch_bounds__(kThreads, ISING_MSC4_MIN_BLOCKS)
                 dsum += (dacc * 0x01010101u) >> 24;  // 4 byte lanes of at most 32
                 nrows += 1;
             }
-            up = cur;
-            cur = dn;
-            dn = nxt;
-            tg = tg_nxt;
-            edge = edge_dn;
-            edge_dn = edge_nxt;
             tp += stride;
-            q0 += (uint64_t)p.qrow;
+            if (Q64) q0 += (uint64_t)p.qrow;
+            else q32 += (uint32_t)p.qrow;
             pn += stride;
-            if (++rn == p.wrap_row) {
-                rn = p.wrap_to;
-                pn = col + rn * stride;
+            if (++rn == wrap_row) {
+                rn = wrap_to;
+                pn = col + (int64_t)rn * stride;
             }
         }
+        // the last group (the unused prefetch) lands before the slots serve
+        // the next range
+        cp_wait_all();
     }
     if (OBS) {
         // per lane and row: 32 white + 32 black spins; 32 white sites x 4 bonds
@@ -213,48 +238,58 @@ __global__ void __launch_bounds__(kThreads, ISING_MSC4_MIN_BLOCKS)
 
 struct Occupancy {
     std::mutex mu;
-    int blocks[64][8] = {};  // per device: colour x obs x always
+    int blocks[64][16] = {};  // per device: colour x obs x always x q64
 };
 Occupancy g_occ;
 
-template <int COLOR, bool OBS, bool ALWAYS>
+template <int COLOR, bool OBS, bool ALWAYS, bool Q64>
 int sweep_blocks_per_sm()
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
     std::lock_guard<std::mutex> lock(g_occ.mu);
-    int &b = g_occ.blocks[dev][COLOR * 4 + (OBS ? 2 : 0) + (ALWAYS ? 1 : 0)];
+    int &b = g_occ.blocks[dev][COLOR * 8 + (OBS ? 4 : 0) + (ALWAYS ? 2 : 0) + (Q64 ? 1 : 0)];
     if (b == 0) {
+        auto k = msc4_sweep_kernel<COLOR, OBS, ALWAYS, Q64>;
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, msc4_sweep_kernel<COLOR, OBS, ALWAYS>, kThreads, 0) !=
-                cudaSuccess ||
-            n < 1)
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads, kRingBytes) != cudaSuccess || n < 1)
             n = 1;
         b = n;
     }
     return b;
 }
 
-template <int COLOR, bool OBS, bool ALWAYS>
+template <int COLOR, bool OBS, bool ALWAYS, bool Q64>
 cudaError_t launch_sweep(const Msc4SweepParams &p, cudaStream_t s)
 {
     DeviceInfo info;
     cudaError_t e = device_info(&info);
     if (e != cudaSuccess) return e;
-    const int64_t max_warps = (int64_t)info.sm_count * sweep_blocks_per_sm<COLOR, OBS, ALWAYS>() * kWarps;
+    const int per_sm = sweep_blocks_per_sm<COLOR, OBS, ALWAYS, Q64>();
+    const int64_t sms = std::max<int64_t>(1, (int64_t)info.sm_count - p.spare_sms);
+    const int64_t max_warps = sms * per_sm * kWarps;
     const int64_t want = std::max<int64_t>(1, (p.total + kMinRowsPerWarp - 1) / kMinRowsPerWarp);
     const int64_t warps = std::min(max_warps, want);
     const int64_t blocks = (warps + kWarps - 1) / kWarps;
-    msc4_sweep_kernel<COLOR, OBS, ALWAYS><<<(unsigned)blocks, kThreads, 0, s>>>(p);
+    msc4_sweep_kernel<COLOR, OBS, ALWAYS, Q64><<<(unsigned)blocks, kThreads, kRingBytes, s>>>(p);
     return cudaGetLastError();
+}
+
+template <int COLOR, bool OBS, bool ALWAYS>
+cudaError_t launch_sweep_q(const Msc4SweepParams &p, cudaStream_t s)
+{
+    // the Philox counter of the last row's blocks fits 32 bits up to L = 185363
+    const bool q64 = (uint64_t)(p.row0 + p.rows + 1) * (uint64_t)p.qrow > 0xFFFFFFFFull;
+    return q64 ? launch_sweep<COLOR, OBS, ALWAYS, true>(p, s) : launch_sweep<COLOR, OBS, ALWAYS, false>(p, s);
 }
 
 template <int COLOR>
 cudaError_t launch_sweep_colour(const Msc4SweepParams &p, cudaStream_t s)
 {
     const bool obs = p.obs != nullptr, always = p.acc.always != 0;
-    if (always) return obs ? launch_sweep<COLOR, true, true>(p, s) : launch_sweep<COLOR, false, true>(p, s);
-    return obs ? launch_sweep<COLOR, true, false>(p, s) : launch_sweep<COLOR, false, false>(p, s);
+    if (always) return obs ? launch_sweep_q<COLOR, true, true>(p, s) : launch_sweep_q<COLOR, false, true>(p, s);
+    return obs ? launch_sweep_q<COLOR, true, false>(p, s) : launch_sweep_q<COLOR, false, false>(p, s);
 }
 
 // ---------------------------------------------------------------------------

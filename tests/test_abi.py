@@ -105,3 +105,20 @@ def test_sweep_rejects_bad_counts_and_colours():
         ising.ising_half_sweep(lat, 0.4, 2, 1, 0, None, stream=0)
     with pytest.raises(ising.IsingError):
         ising.ising_rng_probe(10, 1, 0, 5, 0, None, stream=0)
+
+
+def test_batch_refuses_betas_whose_thresholds_reach_two_to_the_32():
+    """exp(-4 beta) rounds to 1 in FP64 below beta ~ 1.4e-17; the batched
+    decision keeps T3, T4 as 32-bit words, so such a beta is refused
+    (Sec. 2 Metropolis rule: p = 1 would need the entry 2^32)."""
+    for beta in ([1e-18, 0.4], [1e-17, 0.3], [0.2, 0.3]):
+        if beta[0] < 1.4e-17:
+            assert oracle.thresholds(beta[0])[3] == 2 ** 32
+            with pytest.raises(ising.IsingError) as e:
+                ising.ising_batch_bytes([32, 32], 2, beta)
+            assert e.value.status == ising.ISING_EINVAL
+        else:
+            assert ising.ising_batch_bytes([32, 32], 2, beta) > 0
+    # just above the cut-off the table is ordinary: T3 < 2^32
+    assert oracle.thresholds(2e-16)[3] < 2 ** 32
+    assert ising.ising_batch_bytes([32, 32], 2, [2e-16, 0.3]) > 0

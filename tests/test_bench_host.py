@@ -44,11 +44,20 @@ def test_two_gloo_ranks_agree_on_the_slowest_time():
 
 
 def test_reference_arm_runs_on_rank_zero_only():
-    args = bench.parse_args(["--impl", "reference", "--steps", "2", "--warmup", "1", "--cpu-L", "64"])
+    args = bench.parse_args(["--impl", "reference", "--steps", "2", "--warmup", "1", "--ref-L", "64"])
     assert bench.run_reference(args, 2, 1) is None
     res = bench.run_reference(args, 1, 0)
     assert res["impl"] == "reference" and res["unit"] == "flips/ns" and res["value"] > 0
     assert res["e2e"]["h2d_bytes_per_step"] == 0 and res["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_cpu_baseline_reports_the_host():
+    """The CPU baseline names the host it ran on (core count, CPU model) and
+    the threads the oracle used."""
+    args = bench.parse_args(["--cpu-L", "64", "--cpu-sweeps", "2", "--cpu-short"])
+    res = bench.cpu_baseline(args)
+    assert res["kind"] == "oracle" and res["value"] > 0 and res["cores"] >= 1
+    assert res["nproc"] == os.cpu_count() and isinstance(res["cpu_model"], str)
 
 
 def test_integrated_time_of_an_ar1_series():

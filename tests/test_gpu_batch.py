@@ -146,3 +146,19 @@ def test_invalid_batches_are_rejected():
         with pytest.raises(ising.IsingError) as e:
             ising.Batch(L, S, beta)
         assert e.value.status == ising.ISING_EINVAL
+
+
+def test_beta_whose_threshold_reaches_two_to_the_32_is_refused():
+    """At beta = 1e-18, exp(-4 beta) rounds to 1 and T3 = 2^32, which the
+    batched 32-bit compare cannot hold: creation refuses it."""
+    with pytest.raises(ising.IsingError) as e:
+        ising.Batch([32, 32, 64, 64], 2, [1e-18, 0.4])
+    assert e.value.status == ising.ISING_EINVAL
+
+
+def test_smallest_betas_near_the_cutoff_match_oracle():
+    """beta = 2e-16 has T3 = 2^32 - 1 and T4 < 2^32: ordinary tables, and the
+    batch must follow the oracle's uint64 rule bit for bit (Sec. 2)."""
+    L = [32] * 2 + [64] * 2
+    g, o, tr, tr_o = run_both(L, 2, [2e-16, 0.3], 21, 12, 3, True)
+    assert_same(g, o, tr, tr_o)

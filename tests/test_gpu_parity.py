@@ -212,14 +212,31 @@ def test_pack_unpack_against_oracle_encoding(L):
     np.testing.assert_array_equal(full_from_gpu(back), s)
 
 
-def test_rng_probe_counts_match_oracle():
-    n_blocks, seed, t, colour = 5000, 321, 3, 1
+@pytest.mark.parametrize("n_blocks", [5000, 5003, 7, 1, 8 * 40000 + 5])
+def test_rng_probe_counts_match_oracle(n_blocks):
+    """The Philox-only probe (groups of 8 blocks sharing counter words 1..3,
+    a ragged last group) counts exactly the oracle's draws below T3."""
+    seed, t, colour = 321, 3, 1
     T3 = int(oracle.thresholds(0.4406868)[3])
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     ising.ising_rng_probe(n_blocks, seed, t, colour, T3, cnt)
     torch.cuda.synchronize()
     expect = sum(int(oracle.draw(seed, site, t, colour) < T3) for site in range(4 * n_blocks))
     assert int(cnt.item()) == expect
+
+
+def test_mulwide_probe_launches_a_full_grid():
+    """The wide-multiply probe runs and reports the multiplies of one launch:
+    a whole number of 256-thread blocks per SM, 16 chains, `iters` each."""
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for form in (0, 1):
+        n = ising.ising_mulwide_probe(form, 64, sink)
+        torch.cuda.synchronize()
+        assert n % (sms * 256 * 16 * 64) == 0 and n >= sms * 256 * 16 * 64
+    for form, iters in ((0, 0), (2, 64)):
+        with pytest.raises(ising.IsingError):
+            ising.ising_mulwide_probe(form, iters, sink)
 
 
 @pytest.mark.parametrize("layout,L,stride", [("msc4", 256, None), ("int8", 256, None), ("int8", 130, 80)])
@@ -447,6 +464,38 @@ def test_host_sweeps_alternating_between_lattices_of_one_size():
                                               r["hw"].numpy().view(np.uint64).reshape(L, -1))
             np.testing.assert_array_equal(got, r["s"])
             np.testing.assert_array_equal(r["tr_host"].numpy(), tr_o)
+
+
+@pytest.mark.parametrize("fmt", ["msc4", "bits"])
+def test_host_sweeps_on_pageable_host_planes(fmt):
+    """Plain numpy (pageable, not pinned) host planes through the banded
+    one-sweep path, two calls in a row: the schedule's copies from and to
+    pageable memory (captured and replayed, or launched directly where the
+    capture is refused) give the oracle's lattice and trace bit for bit."""
+    L, beta, seed = 2112, 0.4406868, 47
+    s = oracle.init(L, oracle.MODE_RANDOM, seed)
+    if fmt == "bits":
+        hb, hw = (np.ascontiguousarray(x) for x in oracle.to_planes_bits(s))
+        nb = ising.ising_bits_bytes(L)
+        stage = torch.empty(2 * nb, dtype=torch.uint8, device="cuda")
+    else:
+        hb, hw = (np.ascontiguousarray(x).copy() for x in oracle.to_planes_msc4(s))
+    dev = ising.Lattice(L, "msc4")
+    tr_dev = torch.zeros((1, 2), dtype=torch.int64, device="cuda")
+    tr_host = np.zeros((1, 2), dtype=np.int64)
+    for k in range(2):
+        if fmt == "bits":
+            ising.ising_sweep_host_bits(dev, hb, hw, stage, beta, 1, seed, k, tr_dev, tr_host)
+        else:
+            ising.ising_sweep_host(dev, hb, hw, beta, 1, seed, k, tr_dev, tr_host)
+        torch.cuda.synchronize()
+        tr_o = oracle.run(s, beta, 1, seed, off=k)
+        if fmt == "bits":
+            got = oracle.from_planes_bits(L, hb, hw)
+        else:
+            got = oracle.from_planes_msc4(L, hb.view(np.uint64).reshape(L, -1), hw.view(np.uint64).reshape(L, -1))
+        np.testing.assert_array_equal(got, s)
+        np.testing.assert_array_equal(tr_host, tr_o)
 
 
 def test_host_entry_points_with_zero_sweeps_return_the_lattice_unchanged():

@@ -134,6 +134,35 @@ def test_half_sweeps_by_hand_equal_slab_sweep():
     assert own_rows_equal(one, lat)
 
 
+@pytest.mark.parametrize("spare", [0, 8])
+def test_overlapped_driver_order_equals_the_serial_order(spare):
+    """The driver's overlapped order (first and last own rows, then their
+    halo exchange beside the interior rows, views of the slab's storage) and
+    its serial order give the whole-lattice sweep, planes and trace, also when
+    the half-sweep kernel leaves SMs free."""
+    L, n, seed, beta = 256, 5, 12, 0.4406868
+    lat = whole(L, seed)
+    tr_w = torch.zeros((n, 2), dtype=torch.int64, device="cuda")
+    ising.ising_sweep(lat, beta, n, seed, 2, tr_w)
+    for overlap in (False, True):
+        one = slabs_of(L, [(0, L)], seed)[0]
+        one.spare_sms = spare
+        tr = torch.zeros((n, 2), dtype=torch.int64, device="cuda")
+        ising.slab_sweep(one, beta, n, seed, 2, tr, overlap=overlap)
+        torch.cuda.synchronize()
+        assert torch.equal(tr, tr_w), f"overlap={overlap}"
+        assert own_rows_equal(one, lat), f"overlap={overlap}"
+
+
+def test_slab_views_are_bounded():
+    sl = slabs_of(128, [(0, 128)], 1)[0]
+    for first, count in ((-1, 2), (0, 0), (120, 9)):
+        with pytest.raises(ValueError):
+            sl.view(first, count)
+    v = sl.view(5, 7)
+    assert (v.row0, v.rows) == (5, 7) and v.black.data_ptr() == sl.black[5].data_ptr()
+
+
 def test_full_size_four_slabs_match_whole_lattice():
     """65536^2 as four slabs of 16384 rows, 2 sweeps, cold start and random
     start: planes compared on the device, traces exactly."""
@@ -185,6 +214,11 @@ def test_bad_slabs_are_rejected():
     expect_einval(lambda: ising.ising_slab_half_sweep(st[0], -1.0, 0, 1, 0))
     obs = torch.zeros(2, dtype=torch.int64, device="cuda")
     expect_einval(lambda: ising.ising_slab_half_sweep(st[0], 0.4, 0, 1, 0, obs))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for spare in (-1, sms):  # no SM left, or a negative count
+        bad = ising.ising_slab_t.from_buffer_copy(st[0])
+        bad.spare_sms = spare
+        expect_einval(lambda: ising.ising_slab_half_sweep(bad, 0.4, 0, 1, 0))
     # nothing above touched the planes
     fresh = slabs_of(L, ising.slab_partition(L, 2), 1)
     torch.cuda.synchronize()

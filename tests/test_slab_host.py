@@ -60,7 +60,7 @@ def oracle_slab_half_sweep(sl, beta, colour, seed, t, obs):
         obs[1] += bonds
 
 
-def _worker(rank, world, port, L, n_sweeps, seed, q):
+def _worker(rank, world, port, L, n_sweeps, seed, q, overlap=True):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
@@ -70,7 +70,7 @@ def _worker(rank, world, port, L, n_sweeps, seed, q):
         b, w = oracle.to_planes_msc4(s)
         sl.load_own_numpy(b[row0:row0 + rows], w[row0:row0 + rows])
         trace = torch.zeros((n_sweeps, 2), dtype=torch.int64)
-        ising.slab_sweep(sl, BETA, n_sweeps, seed, 5, trace, half_sweep=oracle_slab_half_sweep)
+        ising.slab_sweep(sl, BETA, n_sweeps, seed, 5, trace, half_sweep=oracle_slab_half_sweep, overlap=overlap)
         want_trace = oracle.run(s, BETA, n_sweeps, seed, 5)
         wb, ww = oracle.to_planes_msc4(s)
         gb, gw = sl.own_numpy()
@@ -84,16 +84,19 @@ def _worker(rank, world, port, L, n_sweeps, seed, q):
         dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("overlap", [False, True])
 @pytest.mark.parametrize("world,L", [(2, 64), (3, 128)])
-def test_gloo_slabs_match_the_whole_lattice(world, L):
+def test_gloo_slabs_match_the_whole_lattice(world, L, overlap):
     """Two ranks (the pair exchanges both rows with each other) and three
-    ranks (slabs of 43/43/42 rows: a slab starting on an odd row)."""
+    ranks (slabs of 43/43/42 rows: a slab starting on an odd row), in the
+    serial order and in the overlapped one (boundary rows first, their
+    messages posted before the interior rows are updated)."""
     oracle.build()
     ising.build()
     port = _free_port()
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, L, 4, 99, q)) for r in range(world)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, L, 4, 99, q, overlap)) for r in range(world)]
     for p in procs:
         p.start()
     out = sorted(q.get(timeout=300) for _ in range(world))
