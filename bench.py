@@ -61,7 +61,7 @@ def parse_args(argv=None):
     p.add_argument("--no-binder", action="store_true", help="skip the Binder-crossing leg")
     p.add_argument("--binder-sweeps", type=int, default=100000)
     p.add_argument("--workload", choices=["sweep", "replicas", "pt", "learned", "network", "train", "slabs", "binder",
-                                          "host"],
+                                          "host", "probes"],
                    default="sweep",
                    help="sweep: the 65536^2 lattice (default; with several GPUs cut into one slab per rank); "
                         "replicas: one independent lattice per GPU; pt / learned / ...: only that leg")
@@ -568,8 +568,11 @@ def rng_probe(ising, torch, L, seed, stream):
         e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
-    return {"half_sweep_sites_per_ns": round(4 * n_blocks / (ms * 1e6), 1), "ms": round(ms, 4),
-            "flips_per_ns_ceiling": round(4 * n_blocks / (ms * 1e6), 1)}
+    rate = 4 * n_blocks / (ms * 1e6)
+    return {"half_sweep_sites_per_ns": round(rate, 1), "ms": round(ms, 4), "flips_per_ns_ceiling": round(rate, 1),
+            "kernel": "rng_probe_kernel: 8 Philox blocks per thread step sharing counter words 1..3, 32-bit "
+                      "indices, full grid; one compare per draw",
+            "t_mul_per_s_algorithmic": round(rate * WIDE_MUL_PER_SPIN / 1e3, 3)}
 
 
 def run_e2e(ising, torch, args, L, beta, seed, device, stream):
@@ -985,6 +988,26 @@ def main(argv=None):
     elif args.workload == "slabs" or (args.workload == "sweep" and world > 1):
         # several GPUs: one lattice cut into one horizontal slab per rank (Sec. 4)
         res = run_slabs(args, world, rank, local)
+    elif args.workload == "probes":
+        # the integer ceiling alone: wide-multiply probe (both forms) and the
+        # Philox-only probe over the sites of one half-sweep of an L^2 lattice
+        import torch
+
+        import paper_1906_06297_gb300 as ising
+
+        ising.build()
+        torch.cuda.set_device(local)
+        device = torch.device("cuda", local)
+        stream = torch.cuda.Stream(device=device)
+        with ClockSampler(local) as clk:
+            mul = mulwide_peak(ising, torch, stream)
+            rng = rng_probe(ising, torch, args.L, args.seed, stream)
+        res = {"metric": "wide multiplies/s", "value": mul["t_mul_per_s"], "unit": "T/s", "impl": "ours",
+               "higher_is_better": True,
+               "config": {"workload": f"integer probes; Philox-only probe over {args.L}^2 / 2 sites"},
+               "mulwide": mul, "rng_probe": rng,
+               "rng_probe_frac_of_mul_peak": round(rng["t_mul_per_s_algorithmic"] / mul["t_mul_per_s"], 4),
+               "clocks": clk.summary()}
     elif args.workload == "host":
         # the host-buffer legs alone: one sweep per step of the L^2 lattice
         # held in pinned host memory (bit-packed, and MSC4 beside it)

@@ -80,8 +80,8 @@ __global__ void __launch_bounds__(kProbeThreads) mulwide_probe_kernel(uint32_t i
     if (FORM == 0 ? (uint32_t)y == 0x5bd1e995u : (uint32_t)y == (uint32_t)(y >> 32)) atomicAdd(sink, 1ull);
 }
 
-// Counts draws below T3 with two predicated adds per draw into one counter,
-// the form the sweep's threshold marks take.
+// Counts a draw below T3 with one compare and one predicated add into a
+// counter, the form each of the sweep's two threshold marks takes.
 __device__ __forceinline__ void count_below(uint32_t &cnt, uint32_t u, uint32_t T3)
 {
     asm("{\n\t"
