@@ -57,6 +57,9 @@ def parse_args(argv=None):
     p.add_argument("--no-extras", action="store_true", help="skip per-beta, rng probe, e2e and cpu legs")
     p.add_argument("--no-batch", action="store_true", help="skip the batched parallel-tempering leg")
     p.add_argument("--pt-sweeps", type=int, default=10000)
+    p.add_argument("--pt-ess-sweeps", type=int, default=100000,
+                   help="sweeps of each matched-error run of the batch (with and without exchanges)")
+    p.add_argument("--pt-ess-warm", type=int, default=20000, help="sweeps before the matched-error records")
     p.add_argument("--slabs", type=int, default=4, help="slabs on one GPU for the slab leg / workload")
     p.add_argument("--no-binder", action="store_true", help="skip the Binder-crossing leg")
     p.add_argument("--binder-sweeps", type=int, default=100000)
@@ -67,7 +70,7 @@ def parse_args(argv=None):
                         "replicas: one independent lattice per GPU; pt / learned / ...: only that leg")
     p.add_argument("--no-learned", action="store_true", help="skip the learned block-proposal leg")
     p.add_argument("--learned-steps", type=int, default=1000, help="training steps of the proposal network")
-    p.add_argument("--learned-cycles", type=int, default=400, help="measured sweep + move cycles")
+    p.add_argument("--learned-cycles", type=int, default=4500, help="measured sweep + move cycles")
     p.add_argument("--learned-configs", type=int, default=100000, help="training configurations")
     p.add_argument("--learned-chains", type=int, default=1024, help="chains of the measured learned cycles")
     p.add_argument("--net-reps", type=int, default=10, help="timed network evaluations (--workload network)")
@@ -646,6 +649,7 @@ def run_pt_batch(ising, torch, args, device, stream):
     b = ising.Batch(L, S, beta, device=device)
     b.init(ising.ISING_INIT_RANDOM, seed, stream)
     threads, wpt = b.autotune(2, stream)
+    args._pt_tuned = (threads, wpt)
     b.run(warm, seed, 0, every, True, None, True, stream)
     b.check(stream)
     sweeps = args.pt_sweeps
@@ -681,36 +685,84 @@ def run_pt_batch(ising, torch, args, device, stream):
                                     "gpu_launches": 2 * loop_sweeps * len(L)}
     out["speedup_vs_loop"] = round(out["flips_per_ns"] / out["loop_int8_per_lattice"]["flips_per_ns"], 1)
     del lats
-    # effective samples at the temperature nearest beta_c, side-32 ladders
+    out["matched_error"] = pt_matched_error(ising, torch, args, device, stream)
+    return out
+
+
+def pt_matched_error(ising, torch, args, device, stream):
+    """Replica exchange against the plain sweep at matched observable error,
+    per lattice side of the batch, at the ladder temperature nearest beta_c.
+
+    Both runs sweep the whole 4096-lattice batch in the same persistent
+    kernel, with and without exchanges: after `pt_ess_warm` sweeps, records
+    every 10 sweeps for `pt_ess_sweeps` sweeps.  For each side L the series of
+    |m| and e at slot k* (nearest beta_c) are taken per ladder: with exchanges
+    the slot's trajectory across replicas, without them the lattice that stays
+    at k*.  Cost of one record of one chain at beta*, from each run's measured
+    rate R (flips/ns): plain, the chain's own 10 sweeps (a plain sweep can give
+    the whole GPU to chains at beta*): 10 L^2 / R; with exchanges, its whole
+    ladder's 10 sweeps and the exchanges: 10 S L^2 / R.  The time to a
+    standard error of 1% of the mean (the same eps for both methods) then
+    follows from each method's tau_int and variance (analysis.seconds_to_error)."""
+    import numpy as np
+
+    from paper_1906_06297_gb300 import analysis, workloads
+
+    L, S, beta = workloads.pt_batch()
+    spins = int(sum(x * x for x in L))
+    every, seg = 10, 10000
     k = int(np.argmin(np.abs(beta - 0.5 * np.log(1 + np.sqrt(2)))))
-    n32 = sum(1 for x in L if x == 32)
-    L32 = [32] * n32
-    ess = {}
-    for name, ladder_S, betas, swaps in (("exchange", S, beta, True), ("plain", 1, [float(beta[k])], False)):
-        bb = ising.Batch(L32, ladder_S, betas, device=device)
-        bb.init(ising.ISING_INIT_RANDOM, seed, stream)
-        bb.run(2000, seed, 0, every, swaps, None, True, stream)  # equilibration
-        nev = bb.n_events(sweeps, 2000, every)
-        tr = torch.zeros((nev, n32, 2), dtype=torch.int64, device=device)
-        torch.cuda.synchronize()  # the fill precedes the run on `stream`
-        with torch.cuda.stream(stream):
-            e0.record(stream)
-            bb.run(sweeps, seed, 2000, every, swaps, tr, True, stream)
-            e1.record(stream)
-        bb.check(stream)
-        t_ms = e0.elapsed_time(e1)
-        h = tr.cpu().numpy()
-        cols = range(k, n32, S) if name == "exchange" else range(n32)
-        m = [np.abs(h[:, c, 0]) / 1024.0 for c in cols]
-        e = [-h[:, c, 1] / 1024.0 for c in cols]
-        em, ee = analysis.effective_samples(m), analysis.effective_samples(e)
-        ess[name] = {"beta": round(float(beta[k]), 5), "chains_at_beta": len(m), "ms": round(t_ms, 2),
-                     "tau_abs_m_sweeps": round(em["tau_int"] * every, 1), "tau_e_sweeps": round(ee["tau_int"] * every, 1),
-                     "ess_per_s_abs_m": round(em["effective"] / (t_ms * 1e-3), 1),
-                     "ess_per_s_e": round(ee["effective"] / (t_ms * 1e-3), 1),
-                     "mean_abs_m": round(float(np.mean(np.concatenate(m))), 5)}
-        del bb, tr
-    out["ess_side32_near_beta_c"] = ess
+    n_lad = len(L) // S
+    side = np.array([L[l * S] for l in range(n_lad)])
+    sweeps = max(seg, (args.pt_ess_sweeps // seg) * seg)
+    runs = {}
+    for name, swaps in (("exchange", True), ("plain", False)):
+        b = ising.Batch(L, S, beta, device=device)
+        b.init(ising.ISING_INIT_RANDOM, args.seed + 7, stream)
+        if getattr(args, "_pt_tuned", None):
+            b.config(*args._pt_tuned)
+        else:
+            b.autotune(2, stream)
+        b.run(args.pt_ess_warm, args.seed + 7, 0, every, swaps, None, True, stream)
+        b.check(stream)
+        rows, ms = [], 0.0
+        n_ev = b.n_events(seg, 0, every)
+        tr = torch.zeros((n_ev, len(L), 2), dtype=torch.int64, device=device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for j in range(sweeps // seg):
+            off = args.pt_ess_warm + j * seg
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                b.run(seg, args.seed + 7, off, every, swaps, tr, True, stream)
+                e1.record(stream)
+            b.check(stream)
+            ms += e0.elapsed_time(e1)
+            rows.append(tr[:, k::S, :].cpu().numpy())  # slot k* of every ladder
+        runs[name] = {"h": np.concatenate(rows), "rate": spins * sweeps / (ms * 1e6), "ms": ms}
+        del tr, b
+    out = {"beta": round(float(beta[k]), 5), "sweeps": sweeps, "warm": args.pt_ess_warm, "record_every": every,
+           "eps": "1% of the mean (same eps for both methods)",
+           "rate_flips_per_ns": {n: round(r["rate"], 1) for n, r in runs.items()}, "sides": {}}
+    for Lside in sorted(set(side.tolist())):
+        lads = np.nonzero(side == Lside)[0]
+        area = float(Lside * Lside)
+        res = {"chains_at_beta": int(lads.size)}
+        for obs, col, f in (("abs_m", 0, lambda v: np.abs(v) / area), ("e", 1, lambda v: -v / area)):
+            series = {n: [f(r["h"][:, l, col].astype(np.float64)) for l in lads] for n, r in runs.items()}
+            eps = 0.01 * abs(float(np.mean(np.concatenate(series["plain"]))))
+            per = {}
+            for n, r in runs.items():
+                records = r["h"].shape[0] * lads.size
+                per_record = every * area * (S if n == "exchange" else 1) / (r["rate"] * 1e9)
+                st = analysis.seconds_to_error(series[n], records * per_record, eps)
+                per[n] = {"seconds_to_error": round(st["seconds_to_error"], 6),
+                          "tau_int_sweeps": round(st["tau_int"] * every, 1), "mean": round(st["mean"], 5),
+                          "series_over_tau": round(st["series_over_tau"], 1), "reliable": st["reliable"]}
+            per["plain_over_exchange"] = round(per["plain"]["seconds_to_error"] /
+                                               max(per["exchange"]["seconds_to_error"], 1e-30), 4)
+            res[obs] = per
+        out["sides"][str(Lside)] = res
     return out
 
 
@@ -824,9 +876,9 @@ def run_learned(ising, torch, args, device, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     train_ms = e0.elapsed_time(e1)
-    C, cycles, warm = args.learned_chains, args.learned_cycles, 500
+    C, cycles, warm = args.learned_chains, args.learned_cycles, 5000
     net = time_network(ising, torch, L, C, tr["params"], beta, seed, device, stream)
-    variants = {}
+    variants, series = {}, {}
     for name in ("plain", "uniform", "learned"):
         mv = ising.BlockMove(L, C, beta, device=device)
         mv.batch.init(ising.ISING_INIT_RANDOM, seed, stream)
@@ -858,14 +910,29 @@ def run_learned(ising, torch, args, device, stream):
                           "block_acceptance": (round(float(acc_rows.sum().item()) / (C * cycles), 5)
                                                if name != "plain" else None),
                           "mean_e": round(float(np.mean(np.concatenate(e))), 5)}
+        series[name] = (m, e, ms * 1e-3)
         del mv, trace
     ising.ising_net_check(stream)
+    # time to a standard error of 1% of the plain sweep's mean, the same eps
+    # for every variant (matched observable error)
+    for obs, j in (("abs_m", 0), ("e", 1)):
+        eps = 0.01 * abs(float(np.mean(np.concatenate(series["plain"][j]))))
+        for name in series:
+            st = analysis.seconds_to_error(series[name][j], series[name][2], eps)
+            variants[name][f"seconds_to_error_{obs}"] = round(st["seconds_to_error"], 6)
+            variants[name][f"series_over_tau_{obs}"] = round(st["series_over_tau"], 1)
+            variants[name][f"reliable_{obs}"] = st["reliable"]
+        for name in ("uniform", "learned"):
+            variants[name][f"time_ratio_vs_plain_{obs}"] = round(
+                variants[name][f"seconds_to_error_{obs}"] / max(variants["plain"][f"seconds_to_error_{obs}"], 1e-30), 2)
     return {"workload": f"{C} chains of {L}x{L} at beta={beta}; network trained for {args.learned_steps} Adam steps "
                         f"(batch 64) on {args.learned_configs} plain-sweep configurations 10 sweeps apart; "
                         f"{cycles} measured cycles after {warm} sweeps",
             "train_ms": round(train_ms, 1), "train_loss_first_last": [round(tr["loss"][0], 4), round(tr["loss"][-1], 4)],
             "network": net, "variants": variants,
-            "note": "tau from series of this length are lower bounds where they approach the run length"}
+            "matched_error": "seconds_to_error_*: GPU seconds for a standard error of 1% of the plain sweep's mean "
+                             "(the same eps for all three); time_ratio_vs_plain > 1 means slower than the plain sweep",
+            "note": "reliable_*: each chain's series is at least 50 tau_int long"}
 
 
 def cpu_model() -> str:

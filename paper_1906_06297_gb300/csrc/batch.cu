@@ -41,6 +41,12 @@
 // Size of the fixed scratch array of ising_batch_run_noalloc (4 MiB).
 #define ISING_NOALLOC_SCRATCH_BYTES (4u << 20)
 
+// Smallest lattice side swept by the row-marching path (sides that are powers
+// of two from this value up to 2048; other sides use the item path).
+#ifndef ISING_BATCH_MARCH_MIN_L
+#define ISING_BATCH_MARCH_MIN_L 128
+#endif
+
 namespace ising {
 
 namespace {
@@ -56,6 +62,7 @@ struct BatchGroup {
     int64_t weight_begin; // cumulative work weight of the groups before this one
     int32_t L, wpr, wpt, gpr;  // side, words per row, words per item, items per row
     int32_t weight;       // work weight of one chunk: wpt + kappa
+    int32_t march;        // 1: rows marched by lane groups (side a power of two, 128 .. 2048)
 };
 
 struct BatchParams {
@@ -168,13 +175,168 @@ __device__ __forceinline__ void sweep_item(const uint64_t *__restrict__ src, uin
     if (OBS) dsum += (dacc & 0xFFu) + ((dacc >> 8) & 0xFFu) + ((dacc >> 16) & 0xFFu) + (dacc >> 24);
 }
 
+// ---------------------------------------------------------------------------
+// Row-marching path for lattices whose side L is a power of two from 128 to
+// 2048.  A row of L/32 words is held whole by a group of L/64 lanes, 2 words
+// (16 bytes) per lane, so a warp holds 32 / (L/64) rows side by side.  The
+// chunks a warp owns in such a group are consecutive rows of the group's row
+// space (lattice-major); they are cut into one run of consecutive rows per lane
+// group, and each lane group marches down its run as the single-lattice kernel
+// does: each lane copies its 16 bytes of the source row two ahead and of the
+// next target row into a per-warp ring in shared memory with cp.async, and
+// reads rows r-1, r, r+1 back from its own slots.  The side word comes from the
+// neighbouring lane of the same row (periodic within the lane group), so no lane
+// loads an edge word.  At the start of each lattice of its run a lane group
+// refetches rows L-1, 0, 1 of that lattice (the rows before do not belong to
+// it) and takes the lattice's stream and thresholds.
+// ---------------------------------------------------------------------------
+struct MarchRing {
+    uint4 src[4][32];
+    uint4 tgt[2][32];
+};
+
+__device__ __forceinline__ void cp16_if(void *smem, const void *gmem, bool pred)
+{
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("{\n\t"
+                 ".reg .pred q;\n\t"
+                 "setp.ne.b32 q, %2, 0;\n\t"
+                 "@q cp.async.cg.shared.global [%0], [%1], 16;\n\t"
+                 "}" ::"r"(sa), "l"(gmem), "r"((int)pred) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all_but_last() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Adds a lane group's observables of one lattice: per lane and row 32 white
+// sites (4 bonds each) and 32 black centres were counted, `ones` of them up.
+template <bool OBS>
+__device__ __forceinline__ void march_flush(const BatchParams &p, int64_t lat, unsigned gmask, int lpr, int j,
+                                            uint32_t &ones, uint32_t &dsum, uint32_t &nrows)
+{
+    if (!OBS) return;
+    long long a = ones, b = dsum, c = nrows;
+    for (int off = lpr >> 1; off > 0; off >>= 1) {
+        a += __shfl_xor_sync(gmask, a, off);
+        b += __shfl_xor_sync(gmask, b, off);
+        c += __shfl_xor_sync(gmask, c, off);
+    }
+    if (j == 0 && c > 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(p.acc + 2 * lat), (unsigned long long)(2 * a - 64 * c));
+        atomicAdd(reinterpret_cast<unsigned long long *>(p.acc + 2 * lat + 1), (unsigned long long)(128 * c - 2 * b));
+    }
+    ones = dsum = nrows = 0;
+}
+
+// Chunks [c0, c1) (relative to the group) of march group G: rows
+// [c0 P, c1 P) of the group's row space, P = rows per warp, as P runs of
+// n = c1 - c0 rows, run k for lane group k.
+template <bool OBS>
+__device__ void march_rows(const BatchParams &p, const BatchGroup &G, int64_t c0, int64_t c1, int colour,
+                           uint64_t t, MarchRing &ring)
+{
+    const int lane = threadIdx.x & 31;
+    const int lpr = G.gpr;  // lanes per row
+    const int P = 32 / lpr;
+    const int grp = lane / lpr, j = lane - grp * lpr;
+    const unsigned gmask = lpr == 32 ? 0xffffffffu : ((1u << lpr) - 1u) << (grp * lpr);
+    const int n = (int)(c1 - c0);
+    const int L = G.L, wpr = G.wpr;
+    const int64_t rho = c0 * P + (int64_t)grp * n;  // first row of this lane group's run
+    int64_t li = rho / L;
+    int r = (int)(rho - li * L);
+    const int64_t lat_words = (int64_t)L * wpr;
+    const uint64_t *src_all = (colour == 0 ? p.white : p.black) + G.word_base + 2 * j;
+    uint64_t *tgt_all = (colour == 0 ? p.black : p.white) + G.word_base + 2 * j;
+    const int left_lane = grp * lpr + (j == 0 ? lpr - 1 : j - 1);
+    const int right_lane = grp * lpr + (j + 1 == lpr ? 0 : j + 1);
+    // Philox block of the lane's first site: q = r * L/8 + 4 * (2j), below 2^19
+    const uint32_t qrow = (uint32_t)(L / 8), qlane = 8u * (uint32_t)j;
+    DrawCtx dc{(uint32_t)t, counter_word3(colour, kPurposeMetropolis, t), 0u, 0u, 0u};
+    const uint64_t *src = src_all;
+    uint64_t *tgt = tgt_all;
+    int64_t lat = 0;
+    uint32_t stream = 0, ones = 0, dsum = 0, nrows = 0;
+    // lattice li from row r on, for step s: its stream and thresholds, and
+    // source rows r-1, r, r+1 and target row r into the slots of step s
+    auto enter = [&](int s) {
+        lat = G.first + li;
+        src = src_all + li * lat_words;
+        tgt = tgt_all + li * lat_words;
+        const int slot = p.slot_of[lat];
+        dc.T3 = p.thr[2 * slot];
+        dc.T4 = p.thr[2 * slot + 1];
+        stream = (uint32_t)lat;
+        const int ru = r == 0 ? L - 1 : r - 1, rd = r + 1 == L ? 0 : r + 1;
+        cp16_if(&ring.src[(s + 3) & 3][lane], src + (int64_t)ru * wpr, true);
+        cp16_if(&ring.src[s & 3][lane], src + (int64_t)r * wpr, true);
+        cp16_if(&ring.src[(s + 1) & 3][lane], src + (int64_t)rd * wpr, true);
+        cp16_if(&ring.tgt[s & 1][lane], tgt + (int64_t)r * wpr, true);
+        cp_commit();
+    };
+    if (n > 0) enter(0);
+    for (int s = 0; s < n; ++s) {
+        const bool last_row = r + 1 == L, more = s + 1 < n;
+        // rows two ahead (source) and one ahead (target) of the same lattice;
+        // none after its last row, where the next step enters a new lattice
+        const bool ahead = more && !last_row;
+        const int r2 = r + 2 >= L ? r + 2 - L : r + 2;
+        cp16_if(&ring.src[(s + 2) & 3][lane], src + (int64_t)r2 * wpr, ahead);
+        cp16_if(&ring.tgt[(s + 1) & 1][lane], tgt + (int64_t)(r + 1) * wpr, ahead);
+        cp_commit();
+        cp_wait_all_but_last();
+        const uint4 up = ring.src[(s + 3) & 3][lane];
+        const uint4 cur = ring.src[s & 3][lane];
+        const uint4 dn = ring.src[(s + 1) & 3][lane];
+        const uint4 tg = ring.tgt[s & 1][lane];
+        const uint32_t prev = __shfl_sync(0xffffffffu, cur.w, left_lane);
+        const uint32_t next = __shfl_sync(0xffffffffu, cur.x, right_lane);
+        uint4 sd;  // side words as 32-bit halves
+        if (((r + colour) & 1) == 0) {  // left neighbour word: shift up one spin
+            sd.x = __funnelshift_l(prev, cur.x, 4);
+            sd.y = __funnelshift_l(cur.x, cur.y, 4);
+            sd.z = __funnelshift_l(cur.y, cur.z, 4);
+            sd.w = __funnelshift_l(cur.z, cur.w, 4);
+        } else {  // right neighbour word: shift down one spin
+            sd.x = __funnelshift_r(cur.x, cur.y, 4);
+            sd.y = __funnelshift_r(cur.y, cur.z, 4);
+            sd.z = __funnelshift_r(cur.z, cur.w, 4);
+            sd.w = __funnelshift_r(cur.w, next, 4);
+        }
+        const uint32_t q = (uint32_t)r * qrow + qlane;
+        uint32_t dacc = 0;
+        uint4 ns;
+        ns.x = update_half<OBS, false>(tg.x, up.x + dn.x + cur.x, sd.x, q, stream, dc, p.rk, dacc);
+        ns.y = update_half<OBS, false>(tg.y, up.y + dn.y + cur.y, sd.y, q | 2, stream, dc, p.rk, dacc);
+        ns.z = update_half<OBS, false>(tg.z, up.z + dn.z + cur.z, sd.z, q | 4, stream, dc, p.rk, dacc);
+        ns.w = update_half<OBS, false>(tg.w, up.w + dn.w + cur.w, sd.w, q | 6, stream, dc, p.rk, dacc);
+        *reinterpret_cast<uint4 *>(tgt + (int64_t)r * wpr) = ns;
+        if (OBS) {
+            const uint32_t n8 = ns.x + ns.y + ns.z + ns.w + cur.x + cur.y + cur.z + cur.w;
+            const uint32_t sb = (n8 & 0x0F0F0F0Fu) + ((n8 >> 4) & 0x0F0F0F0Fu);
+            ones += (sb * 0x01010101u) >> 24;
+            dsum += (dacc * 0x01010101u) >> 24;
+            nrows += 1;
+        }
+        ++r;
+        if (last_row) {
+            march_flush<OBS>(p, lat, gmask, lpr, j, ones, dsum, nrows);
+            ++li;
+            r = 0;
+            if (more) enter(s + 1);
+        }
+    }
+    if (n > 0 && r != 0) march_flush<OBS>(p, lat, gmask, lpr, j, ones, dsum, nrows);
+    cp_wait_all();
+}
+
 // One half-sweep of every lattice.  Each chunk carries a work weight wpt +
 // kappa (its words plus a fixed per-chunk cost, kappa chosen by the
 // autotuner); warp gw owns the contiguous chunks whose starting weight lies in
 // [gw * W / nw, (gw + 1) * W / nw) of the total W.  Observables are flushed
 // with one pair of atomics whenever the warp moves to another lattice.
 template <bool OBS>
-__device__ void batch_half(const BatchParams &p, int colour, uint64_t t)
+__device__ void batch_half(const BatchParams &p, int colour, uint64_t t, MarchRing &ring)
 {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -224,6 +386,17 @@ __device__ void batch_half(const BatchParams &p, int colour, uint64_t t)
     for (int64_t c = cb; c < ce; ++c) {
         while (gi + 1 < p.n_groups && c >= p.g[gi + 1].chunk_begin) ++gi;
         const BatchGroup &G = p.g[gi];
+        if (G.march) {
+            // this warp's chunks of the group, all at once (warp-uniform)
+            const int64_t gend = gi + 1 < p.n_groups ? p.g[gi + 1].chunk_begin : p.n_chunks;
+            const int64_t c1 = ce < gend ? ce : gend;
+            flush();
+            cur_lat = -1;
+            march_rows<OBS>(p, G, c - G.chunk_begin, c1 - G.chunk_begin, colour, t, ring);
+            c = c1 - 1;
+            cur_g = -1;
+            continue;
+        }
         if (gi != cur_g) {
             cur_g = gi;
             const int64_t item = (c - G.chunk_begin) * 32 + lane;
@@ -320,15 +493,18 @@ __device__ void batch_exchange(const BatchParams &p, uint64_t t)
 
 __global__ void __launch_bounds__(512) batch_kernel(const __grid_constant__ BatchParams p)
 {
+    // one MarchRing per warp (dynamic shared memory)
+    extern __shared__ __align__(16) unsigned char batch_smem[];
+    MarchRing &ring = reinterpret_cast<MarchRing *>(batch_smem)[threadIdx.x >> 5];
     for (int64_t s = 0; s < p.n_sweeps; ++s) {
         const uint64_t t = p.t0 + (uint64_t)s;
         const bool rec = p.record_every > 0 && (t + 1) % (uint64_t)p.record_every == 0;
-        batch_half<false>(p, 0, t);
+        batch_half<false>(p, 0, t, ring);
         if (!grid_sync(p)) return;
         if (rec)
-            batch_half<true>(p, 1, t);
+            batch_half<true>(p, 1, t, ring);
         else
-            batch_half<false>(p, 1, t);
+            batch_half<false>(p, 1, t, ring);
         if (!grid_sync(p)) return;
         if (rec) {
             batch_exchange(p, t);
@@ -494,11 +670,16 @@ int build_groups(const ising_batch_t *b, int wpt_max, int kappa, BatchParams &p)
         G.word_base = b->word_off[i];
         G.L = (int32_t)b->L[i];
         G.wpr = G.L / 32;
+        G.march = (G.L & (G.L - 1)) == 0 && G.L >= ISING_BATCH_MARCH_MIN_L && G.L <= 2048;
         G.wpt = 1;
-        for (int w : {4, 2}) {
-            if (w <= wpt_max && G.wpr % w == 0) {
-                G.wpt = w;
-                break;
+        if (G.march) {
+            G.wpt = 2;  // 16 bytes of a row per lane
+        } else {
+            for (int w : {4, 2}) {
+                if (w <= wpt_max && G.wpr % w == 0) {
+                    G.wpt = w;
+                    break;
+                }
             }
         }
         G.gpr = G.wpr / G.wpt;
@@ -538,13 +719,19 @@ BatchParams base_params(const ising_batch_t *b)
     return p;
 }
 
+// Dynamic shared memory of a launch: one MarchRing per warp.
+size_t smem_for(int threads) { return (size_t)(threads / 32) * sizeof(MarchRing); }
+
 int blocks_for(int threads, int *blocks)
 {
     DeviceInfo info{1};
     cudaError_t e = device_info(&info);
     if (e != cudaSuccess) return bfail(ISING_ECUDA, cudaGetErrorString(e));
+    // allow the largest ring (16 warps) beside the kernel's static shared memory
+    e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for(512));
+    if (e != cudaSuccess) return bfail(ISING_ECUDA, cudaGetErrorString(e));
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, threads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, threads, smem_for(threads));
     if (e != cudaSuccess || per_sm < 1) return bfail(ISING_ECUDA, "batch kernel does not fit on an SM");
     *blocks = info.sm_count * per_sm;
     return ISING_OK;
@@ -555,6 +742,7 @@ cudaError_t launch_coop(const BatchParams &p, int blocks, int threads, cudaStrea
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)blocks);
     cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem_for(threads);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -783,6 +971,7 @@ static int run_impl(ising_batch_t *b, uint64_t *black, uint64_t *white, int64_t 
     kp.func = (void *)batch_kernel;
     kp.gridDim = dim3((unsigned)blocks);
     kp.blockDim = dim3((unsigned)b->threads);
+    kp.sharedMemBytes = (unsigned)smem_for(b->threads);
     kp.kernelParams = args;
     cudaError_t e = cudaGraphExecKernelNodeSetParams(b->exec, b->node, &kp);
     if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);

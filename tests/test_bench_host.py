@@ -78,3 +78,34 @@ def test_integrated_time_of_an_ar1_series():
     assert abs(tau - (1 + phi) / (2 * (1 - phi))) < 0.2
     e = analysis.effective_samples([x[: n // 2], x[n // 2:]])
     assert abs(e["effective"] - n / (2 * e["tau_int"])) < 1e-6
+
+
+def test_seconds_to_error_of_ar1_series():
+    """For AR(1) with coefficient phi and unit innovations the per-sample
+    variance is 1/(1 - phi^2) and tau = (1 + phi)/(2(1 - phi)); the time to a
+    standard error eps is seconds * 2 tau var / (eps^2 N), and halving eps
+    quadruples it."""
+    import numpy as np
+
+    from paper_1906_06297_gb300 import analysis
+
+    rng = np.random.default_rng(3)
+    phi, n, chains = 0.6, 100_000, 4
+    xs = []
+    for _ in range(chains):
+        eps_ = rng.standard_normal(n)
+        x = np.empty(n)
+        x[0] = eps_[0] / np.sqrt(1 - phi * phi)
+        for i in range(1, n):
+            x[i] = phi * x[i - 1] + eps_[i]
+        xs.append(x)
+    r = analysis.seconds_to_error(xs, seconds=2.0, eps=0.01)
+    tau, var = (1 + phi) / (2 * (1 - phi)), 1 / (1 - phi * phi)
+    assert abs(r["tau_int"] - tau) < 0.1 * tau and abs(r["var"] - var) < 0.05 * var
+    want = 2.0 * 2 * tau * var / (0.01 ** 2 * n * chains)
+    assert abs(r["seconds_to_error"] - want) < 0.15 * want
+    assert r["reliable"] and r["series_over_tau"] > 50
+    r2 = analysis.seconds_to_error(xs, seconds=2.0, eps=0.005)
+    assert abs(r2["seconds_to_error"] / r["seconds_to_error"] - 4.0) < 1e-9
+    short = analysis.seconds_to_error([x[:20] for x in xs], seconds=1.0, eps=0.01)
+    assert not short["reliable"]
