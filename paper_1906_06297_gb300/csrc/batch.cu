@@ -8,7 +8,10 @@
 // offset word_off[i] of one black and one white buffer.  Lattices of equal
 // side that are adjacent in the batch form a group; group g is cut into work
 // items of wpt_g consecutive words of one row, 32 items to a chunk, and every
-// chunk lies inside one lattice.
+// chunk lies inside one lattice.  Groups whose side is a power of two from
+// 128 to 2048 are swept by the row-marching path instead (see march_rows):
+// items of 2 words, a chunk is a warp's worth of whole rows, and a warp's
+// chunks are marched row after row by its lane groups.
 //
 // Draws.  Lattice i uses Philox4x32-10 with the batch seed as key and i added
 // to counter word 1 (its "stream"); lattice 0 of a batch therefore follows
@@ -41,17 +44,13 @@
 // Size of the fixed scratch array of ising_batch_run_noalloc (4 MiB).
 #define ISING_NOALLOC_SCRATCH_BYTES (4u << 20)
 
-// Smallest lattice side swept by the row-marching path (sides that are powers
-// of two from this value up to 2048; other sides use the item path).
-#ifndef ISING_BATCH_MARCH_MIN_L
-#define ISING_BATCH_MARCH_MIN_L 128
-#endif
 
 namespace ising {
 
 namespace {
 
 constexpr int kMaxGroups = 16;
+constexpr int kMarchMinL = 128;  // smallest side of the row-marching path
 
 struct BatchGroup {
     int64_t first;        // first lattice id of the group
@@ -491,7 +490,11 @@ __device__ void batch_exchange(const BatchParams &p, uint64_t t)
     }
 }
 
-__global__ void __launch_bounds__(512) batch_kernel(const __grid_constant__ BatchParams p)
+// One 512-thread block per SM may use up to 128 registers: the march path's
+// Philox blocks then stay in flight together (measured: 127 registers, 1285
+// flips/ns on the replica-exchange batch, against 1216 at the compiler's own
+// choice of 95 and 1236 at 64 with two blocks per SM).
+__global__ void __launch_bounds__(512, 1) batch_kernel(const __grid_constant__ BatchParams p)
 {
     // one MarchRing per warp (dynamic shared memory)
     extern __shared__ __align__(16) unsigned char batch_smem[];
@@ -670,7 +673,9 @@ int build_groups(const ising_batch_t *b, int wpt_max, int kappa, BatchParams &p)
         G.word_base = b->word_off[i];
         G.L = (int32_t)b->L[i];
         G.wpr = G.L / 32;
-        G.march = (G.L & (G.L - 1)) == 0 && G.L >= ISING_BATCH_MARCH_MIN_L && G.L <= 2048;
+        // marching pays from 128 up (64: one lane per row, 1239 against 1285
+        // flips/ns on the replica-exchange batch; starting at 256: 1206)
+        G.march = (G.L & (G.L - 1)) == 0 && G.L >= kMarchMinL && G.L <= 2048;
         G.wpt = 1;
         if (G.march) {
             G.wpt = 2;  // 16 bytes of a row per lane
