@@ -586,8 +586,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv32_tc_kernel(const __grid
 // Dependencies: MMA step t waits on epilogue steps < t only, epilogue step t
 // on MMA steps <= t only, so no wait can close a cycle.
 constexpr int kRing = 8;        // staged rows (a power of two)
-constexpr int kAcc = 4;         // accumulators of 32 TMEM columns
-constexpr int kUnitRows = 16;   // output rows per work unit
+constexpr int kAcc = 4;         // accumulators of 32 TMEM columns (6: 1.76 against 1.73 ms per full forward)
+// output rows per work unit: each unit stages 2 halo rows and restarts the
+// pipeline; 32 rows per unit measured 1.66 ms per full forward of 1024
+// chains of 128^2 against 1.73 (16), 1.72 (64), 1.75 (128), 1.89 (24)
+constexpr int kUnitRows = 32;
 constexpr int kEpiWarps = 8;
 constexpr int kRingThreads = 64 + 32 * kEpiWarps;
 constexpr int kProjN = 16;      // the 9 taps of layer 4, padded to an MMA N
@@ -847,6 +850,12 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
             const uint32_t idesc_p = tc::idesc_bf16_f32(kTileM, kProjN);
             const uint32_t ring_u32 = tc::smem_u32(ring), b_u32 = tc::smem_u32(sB);
             const uint32_t a3_u32 = tc::smem_u32(a3s), w4_u32 = tc::smem_u32(sW4);
+            // descriptors of the ring's first byte and of the weights' first byte,
+            // as 32-bit words (the MMAs of a tile add offsets to the low words)
+            const uint64_t a_desc0 = tc::smem_desc(ring_u32, kRingPlane, 128);
+            const uint64_t b_desc0 = tc::smem_desc(b_u32, kCh * 16, 128);
+            const uint32_t a_lo0 = (uint32_t)a_desc0, a_hi = (uint32_t)(a_desc0 >> 32);
+            const uint32_t b_lo0 = (uint32_t)b_desc0, b_hi = (uint32_t)(b_desc0 >> 32);
             // layer-4 projection of tile s (its a3 staged by the epilogue)
             auto issue_proj = [&](int64_t s) -> bool {
                 const int b = (int)(s & 1);
@@ -876,14 +885,17 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
                         ok = false;
                     if (!ok) break;
                     tc::fence_after_sync();
+                    // low descriptor words of the three staged rows this tile reads
+                    uint32_t row_lo[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+                        row_lo[d] = a_lo0 + ((((uint32_t)(n0 + j) + (uint32_t)d) & (kRing - 1)) * kRowBytes >> 4);
 #pragma unroll
                     for (int st = 0; st < 2 * kTaps; ++st) {
                         const int k = st >> 1, h = st & 1, dy = k / 3 - 1, dx = k % 3 - 1;
-                        const int slot = (int)((n0 + j + 1 + dy) % kRing);
-                        const uint64_t ad =
-                            tc::smem_desc(ring_u32 + slot * kRowBytes + 2 * h * kRingPlane + (1 + dx) * 16, kRingPlane, 128);
-                        const uint64_t bd = tc::smem_desc(b_u32 + (k * kGroups + 2 * h) * kCh * 16, kCh * 16, 128);
-                        tc::mma_bf16(tmem + (uint32_t)(a * kCh), ad, bd, idesc, st > 0 ? 1u : 0u);
+                        const uint32_t a_lo = row_lo[1 + dy] + ((2 * h * kRingPlane + (1 + dx) * 16) >> 4);
+                        const uint32_t b_lo = b_lo0 + (((k * kGroups + 2 * h) * kCh * 16) >> 4);
+                        tc::mma_bf16_w(tmem + (uint32_t)(a * kCh), a_lo, a_hi, b_lo, b_hi, idesc, st > 0 ? 1u : 0u);
                     }
                     if (!(p.withhold && t == 0)) tc::mma_commit(&accf[a]);
                     tc::mma_commit(&empty[(n0 + j) % kRing]);
