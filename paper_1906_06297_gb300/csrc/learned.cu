@@ -599,17 +599,27 @@ constexpr int kProjN = 16;      // the 9 taps of layer 4, padded to an MMA N
 constexpr uint32_t kRingPlane = 17 * 128;
 constexpr uint32_t kRowBytes = kGroups * kRingPlane;   // one staged row, or one a3 tile
 constexpr uint32_t kW4Bytes = kGroups * kProjN * 16;   // 1024
-constexpr uint32_t kSmRing = 0;
-constexpr uint32_t kSmA3 = kSmRing + kRing * kRowBytes;
-constexpr uint32_t kSmB = kSmA3 + 2 * kRowBytes;
-constexpr uint32_t kSmW4 = kSmB + kBBytes;
-constexpr uint32_t kSmBias = kSmW4 + kW4Bytes;
-constexpr uint32_t kSmBar = kSmBias + kCh * 4;
 constexpr int kRingBars = 2 * kRing + 2 * kAcc + 8 + 1;
-constexpr uint32_t kRingSmem = kSmBar + kRingBars * 8 + 16;
+// Shared-memory layout: the staged rows, then (only in the kernel that
+// projects onto layer 4) two a3 tiles, the weights, (PROJ) W4^T, the bias and
+// the barriers.  Without the a3 tiles two CTAs take 173 KB, so the SM keeps
+// ~60 KB of L1 (a 196 KB carveout), enough for layer 1's 32 KB table that the
+// fused first layer reads for every pixel (with the a3 tiles: 28 KB, and about
+// 40% of its table reads missed L1).
+template <bool PROJ>
+struct RingLayout {
+    static constexpr uint32_t ring = 0;
+    static constexpr uint32_t a3 = ring + kRing * kRowBytes;
+    static constexpr uint32_t b = PROJ ? a3 + 2 * kRowBytes : a3;
+    static constexpr uint32_t w4 = b + kBBytes;
+    static constexpr uint32_t bias = PROJ ? w4 + kW4Bytes : w4;
+    static constexpr uint32_t bar = bias + kCh * 4;
+    static constexpr uint32_t bytes = bar + kRingBars * 8 + 16;
+};
 constexpr uint32_t kRingTmemCols = 256;  // 4 x 32 accumulator + 2 x 16 projection columns, as a power of two
 static_assert((kRing & (kRing - 1)) == 0 && kRing >= 6, "ring of a power-of-two rows, 3 in use and 3 ahead");
-static_assert(2 * kRingSmem <= 228 * 1024, "two CTAs per SM");
+static_assert(2 * RingLayout<true>::bytes <= 228 * 1024, "two CTAs per SM");
+static_assert(2 * RingLayout<false>::bytes + 2048 <= 196 * 1024, "two CTAs per SM in a 196 KB carveout");
 static_assert(kAcc * kCh + 2 * kProjN <= (int)kRingTmemCols && 2 * kRingTmemCols <= 512, "TMEM columns");
 
 struct RingConv {
@@ -698,12 +708,13 @@ template <bool PROJ, bool BWD, bool FUSED>
 __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __grid_constant__ RingConv p)
 {
     extern __shared__ __align__(1024) uint8_t ring_smem[];
-    uint8_t *ring = ring_smem + kSmRing;
-    uint8_t *a3s = ring_smem + kSmA3;
-    uint8_t *sB = ring_smem + kSmB;
-    uint8_t *sW4 = ring_smem + kSmW4;
-    float *sBias = reinterpret_cast<float *>(ring_smem + kSmBias);
-    uint64_t *full = reinterpret_cast<uint64_t *>(ring_smem + kSmBar);
+    using Lay = RingLayout<PROJ>;
+    uint8_t *ring = ring_smem + Lay::ring;
+    uint8_t *a3s = ring_smem + Lay::a3;
+    uint8_t *sB = ring_smem + Lay::b;
+    uint8_t *sW4 = ring_smem + Lay::w4;
+    float *sBias = reinterpret_cast<float *>(ring_smem + Lay::bias);
+    uint64_t *full = reinterpret_cast<uint64_t *>(ring_smem + Lay::bar);
     uint64_t *empty = full + kRing, *accf = empty + kRing, *acce = accf + kAcc;
     uint64_t *a3full = acce + kAcc, *a3empty = a3full + 2, *pfull = a3empty + 2, *pempty = pfull + 2;
     uint64_t *drain = pempty + 2;
@@ -1735,8 +1746,9 @@ int launch_ring_bwd(int L, int64_t C, const float *params, int w_off, const __nv
     p.units_per_col = (L + kUnitRows - 1) / kUnitRows;
     p.units = C * p.segs * p.units_per_col;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.units, 2 * info.sm_count));
-    cudaFuncSetAttribute(conv32_ring_kernel<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmem);
-    conv32_ring_kernel<false, true, false><<<grid, kRingThreads, kRingSmem, s>>>(p);
+    cudaFuncSetAttribute(conv32_ring_kernel<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)RingLayout<false>::bytes);
+    conv32_ring_kernel<false, true, false><<<grid, kRingThreads, RingLayout<false>::bytes, s>>>(p);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ISING_OK : nfail(ISING_ECUDA, cudaGetErrorString(e));
 }
@@ -1773,11 +1785,14 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
     if (L % kTileM == 0) {
         // row-ring kernels; the second one also projects onto layer 4's taps
         cudaFuncSetAttribute(conv32_ring_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kRingSmem);
+                             (int)RingLayout<false>::bytes);
         cudaFuncSetAttribute(conv32_ring_kernel<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kRingSmem);
+                             (int)RingLayout<false>::bytes);
         cudaFuncSetAttribute(conv32_ring_kernel<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kRingSmem);
+                             (int)RingLayout<true>::bytes);
+        // shared memory for two CTAs of the first conv, the rest as L1 for the layer-1 table
+        cudaFuncSetAttribute(conv32_ring_kernel<false, false, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             86);
         __nv_bfloat16 *outs[2] = {w.a2, train ? w.a3 : nullptr};
         for (int l = 0; l < 2; ++l) {
             RingConv p{};
@@ -1800,11 +1815,11 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
             p.withhold = withhold && l == 0;
             const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.units, 2 * info.sm_count));
             if (fused)
-                conv32_ring_kernel<false, false, true><<<grid, kRingThreads, kRingSmem, s>>>(p);
+                conv32_ring_kernel<false, false, true><<<grid, kRingThreads, RingLayout<false>::bytes, s>>>(p);
             else if (l == 0)
-                conv32_ring_kernel<false, false, false><<<grid, kRingThreads, kRingSmem, s>>>(p);
+                conv32_ring_kernel<false, false, false><<<grid, kRingThreads, RingLayout<false>::bytes, s>>>(p);
             else
-                conv32_ring_kernel<true, false, false><<<grid, kRingThreads, kRingSmem, s>>>(p);
+                conv32_ring_kernel<true, false, false><<<grid, kRingThreads, RingLayout<true>::bytes, s>>>(p);
         }
     } else {
         cudaFuncSetAttribute(conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
