@@ -593,6 +593,9 @@ constexpr int kAcc = 4;         // accumulators of 32 TMEM columns (6: 1.76 agai
 constexpr int kUnitRows = 32;
 constexpr int kEpiWarps = 8;
 constexpr int kRingThreads = 64 + 32 * kEpiWarps;
+constexpr int kRingLoader2 = 2 + kEpiWarps;  // the second loader warp of the fused first conv
+template <bool FUSED>
+constexpr int ring_threads() { return FUSED ? kRingThreads + 32 : kRingThreads; }
 constexpr int kProjN = 16;      // the 9 taps of layer 4, padded to an MMA N
 // channel-group planes 2176 bytes apart: each tensor copy lands on a 128-byte
 // boundary; 130 of its 136 16-byte entries are used
@@ -705,7 +708,7 @@ __device__ __forceinline__ uint32_t chunk_bits(const Chains &ch, const ChunkWord
 }
 
 template <bool PROJ, bool BWD, bool FUSED>
-__global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __grid_constant__ RingConv p)
+__global__ void __launch_bounds__(ring_threads<FUSED>(), 2) conv32_ring_kernel(const __grid_constant__ RingConv p)
 {
     extern __shared__ __align__(1024) uint8_t ring_smem[];
     using Lay = RingLayout<PROJ>;
@@ -774,9 +777,13 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
     const uint32_t tproj = tmem + (uint32_t)(kAcc * kCh);
     bool ok = true;
 
-    if (warp == 0 && FUSED) {
-        // loader building the rows of a1 from the spins
-        uint32_t n = 0;
+    if ((warp == 0 || warp == kRingLoader2) && FUSED) {
+        // two loader warps building the rows of a1 from the spins: warp 0 the
+        // rows of even ring index, the other warp those of odd index (one
+        // warp building rows is a chain of shuffles, table loads and stores
+        // that the MMA thread outpaces)
+        const uint32_t parity = warp == 0 ? 0u : 1u;
+        uint32_t n = 0;  // ring index of the unit's first row
         const uint4 *ta = reinterpret_cast<const uint4 *>(p.ta);
         const int nw = L / 32;
         for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
@@ -792,13 +799,16 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
                 }
                 return k;
             };
-            ChunkWords next = fetch(-1);
-            for (int j = -1; j <= w.nrows; ++j, ++n) {
-                const uint32_t s = n & (kRing - 1);
+            // this warp's rows j of the unit: ring index n + j + 1 of its parity
+            const int j0 = -1 + (int)((parity - n) & 1u);
+            ChunkWords next = j0 <= w.nrows ? fetch(j0) : ChunkWords{0, 0, 0, 0};
+            for (int j = j0; j <= w.nrows; j += 2) {
+                const uint32_t nn = n + (uint32_t)(j + 1);
+                const uint32_t s = nn & (kRing - 1);
                 const ChunkWords cur = next;
-                if (j < w.nrows) next = fetch(j + 1);  // in flight while row j is built
-                if (n >= kRing &&
-                    !__all_sync(0xffffffffu, tc::mbar_wait(&empty[s], ((n / kRing) + 1) & 1, kWaitCycles))) {
+                if (j + 2 <= w.nrows) next = fetch(j + 2);  // in flight while row j is built
+                if (nn >= kRing &&
+                    !__all_sync(0xffffffffu, tc::mbar_wait(&empty[s], ((nn / kRing) + 1) & 1, kWaitCycles))) {
                     ok = false;
                     break;
                 }
@@ -827,6 +837,7 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&full[s]);
             }
+            n += (uint32_t)(w.nrows + 2);
         }
     } else if (warp == 0) {
         // loader
@@ -924,7 +935,7 @@ __global__ void __launch_bounds__(kRingThreads, 2) conv32_ring_kernel(const __gr
             tc::mbar_wait(drain, 0, kWaitCycles);
         }
         __syncwarp();
-    } else {
+    } else if (warp < 2 + kEpiWarps) {
         const int quad = warp & 3, half = (warp - 2) >> 2, m = quad * 32 + lane;
         // P of tile s, pixel q (one tile behind the accumulators)
         auto read_proj = [&](int64_t s, int64_t q) -> bool {
@@ -1815,7 +1826,7 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
             p.withhold = withhold && l == 0;
             const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.units, 2 * info.sm_count));
             if (fused)
-                conv32_ring_kernel<false, false, true><<<grid, kRingThreads, RingLayout<false>::bytes, s>>>(p);
+                conv32_ring_kernel<false, false, true><<<grid, ring_threads<true>(), RingLayout<false>::bytes, s>>>(p);
             else if (l == 0)
                 conv32_ring_kernel<false, false, false><<<grid, kRingThreads, RingLayout<false>::bytes, s>>>(p);
             else
