@@ -560,13 +560,21 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv32_tc_kernel(const __grid
 //           the pattern's row of the table (l1_table_kernel); the lanes then
 //           fence the async proxy and lane 0 arrives on full[slot]: a1 never
 //           goes through global memory;
-//   warp 1: lane 0 issues the 18 MMAs of each tile into one of kAcc
-//           accumulators, then commits to accf[acc] and to empty[slot] of
-//           the row no later tile of the unit reads;
+//   warp 1: lane 0 issues the MMAs row-stationary: each staged row, once
+//           per (dx, K half), times the weights of the three dy taps stacked
+//           along N = 96, into the accumulator blocks of the three output
+//           rows it feeds (a ring of kAcc blocks in descending row order, so
+//           the three are adjacent; two MMAs where the window wraps): 6-8
+//           MMAs per row where a tile-at-a-time schedule needs 18 of N = 32
+//           (the tensor core spends ~45 cycles on an N = 32 MMA and ~56 on an
+//           N = 96 one).  It then commits to empty[slot] of the row (no later
+//           MMA reads it) and to accf[block] of the output row that row
+//           completed;
 //   warps 2-9: epilogue, warp w on TMEM lanes 32 (w % 4) .. + 31 (its 32
 //           pixels) and columns 16 h .. 16 h + 15, h = (w - 2) / 4 (its 16
-//           channels): loads them, frees the accumulator (acce, 8 arrivals),
-//           adds the bias and writes z (training) and a = bf16(gelu(z)).
+//           channels): loads them, zeros them (every MMA accumulates), frees
+//           the block (acce, 8 arrivals), adds the bias and writes z
+//           (training) and a = bf16(gelu(z)).
 //           Two warps per TMEM lane quadrant, four per SM sub-partition with
 //           two CTAs per SM, hide the latency of the GELU arithmetic.
 // PROJ (the last 32-channel layer): layer 4's channel contraction is done
@@ -583,10 +591,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv32_tc_kernel(const __grid
 // W[o][i][k] dz(p - off_k)[o] and -off_k = off_{8-k}; the epilogue multiplies
 // by gelu'(z_prev) and writes dz_prev in FP32 (and in bfloat16 with halo
 // columns when a_out is set, for the next data gradient).
-// Dependencies: MMA step t waits on epilogue steps < t only, epilogue step t
-// on MMA steps <= t only, so no wait can close a cycle.
+// Dependencies: the MMAs of staged row i wait on the epilogue of output rows
+// up to i + 1 - kAcc only, the epilogue of row t on the MMAs of staged rows up
+// to t + 1 only, so no wait can close a cycle.
 constexpr int kRing = 8;        // staged rows (a power of two)
-constexpr int kAcc = 4;         // accumulators of 32 TMEM columns (6: 1.76 against 1.73 ms per full forward)
+constexpr int kAcc = 7;         // accumulator blocks of 32 TMEM columns, one per output row in flight
 // output rows per work unit: each unit stages 2 halo rows and restarts the
 // pipeline; 32 rows per unit measured 1.66 ms per full forward of 1024
 // chains of 128^2 against 1.73 (16), 1.72 (64), 1.75 (128), 1.89 (24)
@@ -619,7 +628,13 @@ struct RingLayout {
     static constexpr uint32_t bar = bias + kCh * 4;
     static constexpr uint32_t bytes = bar + kRingBars * 8 + 16;
 };
-constexpr uint32_t kRingTmemCols = 256;  // 4 x 32 accumulator + 2 x 16 projection columns, as a power of two
+constexpr uint32_t kRingTmemCols = 256;  // 7 x 32 accumulator + 2 x 16 projection columns
+constexpr int kStackN = 3 * kCh;         // the weights of the three dy taps stacked along N
+// accumulator block of output row t (counted over a CTA's units, 32-bit: the
+// MMA thread does this arithmetic for every row): descending, so that rows
+// t + 1, t, t - 1 sit in consecutive blocks; and the parity of its use
+__device__ __forceinline__ int ring_blk(uint32_t t) { return kAcc - 1 - (int)(t % (uint32_t)kAcc); }
+__device__ __forceinline__ uint32_t ring_use(uint32_t t) { return t / (uint32_t)kAcc; }
 static_assert((kRing & (kRing - 1)) == 0 && kRing >= 6, "ring of a power-of-two rows, 3 in use and 3 ahead");
 static_assert(2 * RingLayout<true>::bytes <= 228 * 1024, "two CTAs per SM");
 static_assert(2 * RingLayout<false>::bytes + 2048 <= 196 * 1024, "two CTAs per SM in a 196 KB carveout");
@@ -751,7 +766,10 @@ __global__ void __launch_bounds__(ring_threads<FUSED>(), 2) conv32_ring_kernel(c
         // BWD: row n = input channel i, K = output channels 8g .. 8g+7 of tap 8 - k
         const int st = BWD ? kCh * 9 : 9;
         const float *w = p.params + p.w_off + (BWD ? ((8 * g) * kCh + n) * 9 + (8 - k) : (n * kCh + 8 * g) * 9 + k);
-        *reinterpret_cast<uint4 *>(sB + e * 16) =
+        // stacked operand of (dx, K half h): N = 96 rows, row 32 (dy + 1) + n,
+        // K = channel groups 2h and 2h + 1 (LBO = 96 x 16 bytes, SBO = 128)
+        const int dyi = k / 3, dxi = k % 3, h = g >> 1, gl = g & 1;
+        *reinterpret_cast<uint4 *>(sB + ((((dxi * 2 + h) * 2 + gl) * kStackN) + kCh * dyi + n) * 16) =
             make_uint4(pack_bf16x2(w[0], w[st]), pack_bf16x2(w[2 * st], w[3 * st]),
                        pack_bf16x2(w[4 * st], w[5 * st]), pack_bf16x2(w[6 * st], w[7 * st]));
     }
@@ -775,6 +793,16 @@ __global__ void __launch_bounds__(ring_threads<FUSED>(), 2) conv32_ring_kernel(c
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
     const uint32_t tproj = tmem + (uint32_t)(kAcc * kCh);
+    // every accumulator block starts at zero, so that all MMAs accumulate
+    if (warp >= 2 && warp < 2 + kEpiWarps) {
+        const int quad = warp & 3, half = (warp - 2) >> 2;
+        for (int a = 0; a < kAcc; ++a)
+            tc::tmem_st16_zero(tmem + (uint32_t)(a * kCh + 16 * half) + ((uint32_t)(quad * 32) << 16));
+        tc::tmem_wait_st();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
     bool ok = true;
 
     if ((warp == 0 || warp == kRingLoader2) && FUSED) {
@@ -868,14 +896,16 @@ __global__ void __launch_bounds__(ring_threads<FUSED>(), 2) conv32_ring_kernel(c
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = tc::idesc_bf16_f32(kTileM, kCh);
+            // N = 32, 64 or 96: one, two or three accumulator blocks per MMA
+            // (the N field holds N / 8 from bit 17)
+            const uint32_t idesc0 = tc::idesc_bf16_f32(kTileM, 0);
             const uint32_t idesc_p = tc::idesc_bf16_f32(kTileM, kProjN);
             const uint32_t ring_u32 = tc::smem_u32(ring), b_u32 = tc::smem_u32(sB);
             const uint32_t a3_u32 = tc::smem_u32(a3s), w4_u32 = tc::smem_u32(sW4);
-            // descriptors of the ring's first byte and of the weights' first byte,
-            // as 32-bit words (the MMAs of a tile add offsets to the low words)
+            // descriptors of the ring's first byte and of the stacked weights'
+            // first byte, as 32-bit words (the MMAs add offsets to the low words)
             const uint64_t a_desc0 = tc::smem_desc(ring_u32, kRingPlane, 128);
-            const uint64_t b_desc0 = tc::smem_desc(b_u32, kCh * 16, 128);
+            const uint64_t b_desc0 = tc::smem_desc(b_u32, kStackN * 16, 128);
             const uint32_t a_lo0 = (uint32_t)a_desc0, a_hi = (uint32_t)(a_desc0 >> 32);
             const uint32_t b_lo0 = (uint32_t)b_desc0, b_hi = (uint32_t)(b_desc0 >> 32);
             // layer-4 projection of tile s (its a3 staged by the epilogue)
@@ -894,42 +924,62 @@ __global__ void __launch_bounds__(ring_threads<FUSED>(), 2) conv32_ring_kernel(c
                 tc::mma_commit(&a3empty[b]);
                 return true;
             };
-            int64_t n0 = 0, t = 0, ready = 0;
+            // Row-stationary: staged input row i of a unit is multiplied once,
+            // for each (dx, K half), by the three dy taps stacked along N, into
+            // the accumulator blocks of the output rows it feeds, i + 1 (dy =
+            // -1), i and i - 1 (dy = +1), those of them inside the unit.  Output
+            // row t (counted over the units) has block kAcc - 1 - t % kAcc, so
+            // rows i + 1, i, i - 1 have consecutive blocks and one MMA covers
+            // them, two where the window passes the last block.  Every output
+            // element still accumulates its 18 K steps in the order dy, dx, K.
+            // (One M128 x N96 MMA costs a third of three N32 ones: the tensor
+            // core takes ~45 cycles per N32 MMA and ~56 per N96 one.)
+            uint32_t n0 = 0, t = 0, ready = 0;  // n0: ring index of the unit's row -1; t: rows of the units before
             for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
                 const RingUnit w = ring_unit(p, u);
-                for (int j = 0; j < w.nrows && ok; ++j, ++t) {
-                    while (ready < n0 + j + 3 && ok) {
-                        if (!tc::mbar_wait(&full[ready % kRing], (uint32_t)((ready / kRing) & 1), kWaitCycles)) ok = false;
+                for (int i = -1; i <= w.nrows && ok; ++i) {
+                    while (ready < n0 + (uint32_t)(i + 2) && ok) {
+                        if (!tc::mbar_wait(&full[ready & (kRing - 1)], (ready / kRing) & 1u, kWaitCycles)) ok = false;
                         ++ready;
                     }
-                    const int a = (int)(t % kAcc);
-                    if (ok && t >= kAcc && !tc::mbar_wait(&acce[a], (uint32_t)(((t / kAcc) + 1) & 1), kWaitCycles))
-                        ok = false;
+                    // row i + 1 enters its block now: the block's last row must be read out
+                    if (ok && i + 1 < w.nrows) {
+                        const uint32_t tn = t + (uint32_t)(i + 1);
+                        if (tn >= (uint32_t)kAcc &&
+                            !tc::mbar_wait(&acce[ring_blk(tn)], (ring_use(tn) + 1u) & 1u, kWaitCycles))
+                            ok = false;
+                    }
                     if (!ok) break;
                     tc::fence_after_sync();
-                    // low descriptor words of the three staged rows this tile reads
-                    uint32_t row_lo[3];
+                    const int o_hi = min(i + 1, w.nrows - 1), o_lo = max(i - 1, 0);
+                    const int cnt = o_hi - o_lo + 1;                    // blocks of the window (1 .. 3)
+                    const int b0 = ring_blk(t + (uint32_t)o_hi);        // its first block
+                    const int len0 = min(cnt, kAcc - b0);               // blocks before the wrap
+                    const uint32_t dy0 = (uint32_t)(i - o_hi + 1);      // dy + 1 of the first block
+                    const uint32_t row_lo = a_lo0 + (((n0 + (uint32_t)(i + 1)) & (kRing - 1)) * kRowBytes >> 4);
+                    const uint32_t idesc_a = idesc0 | ((uint32_t)(len0 * kCh / 8) << 17);
+                    const uint32_t idesc_b = idesc0 | ((uint32_t)((cnt - len0) * kCh / 8) << 17);
 #pragma unroll
-                    for (int d = 0; d < 3; ++d)
-                        row_lo[d] = a_lo0 + ((((uint32_t)(n0 + j) + (uint32_t)d) & (kRing - 1)) * kRowBytes >> 4);
-#pragma unroll
-                    for (int st = 0; st < 2 * kTaps; ++st) {
-                        const int k = st >> 1, h = st & 1, dy = k / 3 - 1, dx = k % 3 - 1;
-                        const uint32_t a_lo = row_lo[1 + dy] + ((2 * h * kRingPlane + (1 + dx) * 16) >> 4);
-                        const uint32_t b_lo = b_lo0 + (((k * kGroups + 2 * h) * kCh * 16) >> 4);
-                        tc::mma_bf16_w(tmem + (uint32_t)(a * kCh), a_lo, a_hi, b_lo, b_hi, idesc, st > 0 ? 1u : 0u);
+                    for (int st = 0; st < 6; ++st) {
+                        const int dxi = st >> 1, h = st & 1;
+                        const uint32_t a_lo = row_lo + ((2 * h * kRingPlane + dxi * 16) >> 4);
+                        const uint32_t b_lo =
+                            b_lo0 + ((uint32_t)((dxi * 2 + h) * 2 * kStackN * 16) >> 4) + dy0 * (kCh * 16 >> 4);
+                        tc::mma_bf16_w(tmem + (uint32_t)(b0 * kCh), a_lo, a_hi, b_lo, b_hi, idesc_a, 1u);
+                        if (len0 < cnt)
+                            tc::mma_bf16_w(tmem, a_lo, a_hi, b_lo + (uint32_t)len0 * (kCh * 16 >> 4), b_hi, idesc_b, 1u);
                     }
-                    if (!(p.withhold && t == 0)) tc::mma_commit(&accf[a]);
-                    tc::mma_commit(&empty[(n0 + j) % kRing]);
-                    if (j == w.nrows - 1) {
-                        tc::mma_commit(&empty[(n0 + j + 1) % kRing]);
-                        tc::mma_commit(&empty[(n0 + j + 2) % kRing]);
+                    tc::mma_commit(&empty[(n0 + (uint32_t)(i + 1)) & (kRing - 1)]);  // no later MMA reads row i
+                    if (i >= 1) {
+                        const uint32_t td = t + (uint32_t)(i - 1);  // row i - 1 has all 18 steps now
+                        if (!(p.withhold && td == 0)) tc::mma_commit(&accf[ring_blk(td)]);
+                        if (PROJ && td >= 1 && !issue_proj((int64_t)td - 1)) ok = false;
                     }
-                    if (PROJ && t >= 1 && !issue_proj(t - 1)) ok = false;
                 }
-                n0 += w.nrows + 2;
+                n0 += (uint32_t)(w.nrows + 2);
+                t += (uint32_t)w.nrows;
             }
-            if (PROJ && ok && t >= 1 && !issue_proj(t - 1)) ok = false;
+            if (PROJ && ok && t >= 1 && !issue_proj((int64_t)t - 1)) ok = false;
             // every MMA has completed before the TMEM is freed
             tc::mma_commit(drain);
             tc::mbar_wait(drain, 0, kWaitCycles);
@@ -956,14 +1006,18 @@ __global__ void __launch_bounds__(ring_threads<FUSED>(), 2) conv32_ring_kernel(c
         for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
             const RingUnit w = ring_unit(p, u);
             for (int j = 0; j < w.nrows; ++j, ++t) {
-                const int a = (int)(t % kAcc);
-                if (!__all_sync(0xffffffffu, tc::mbar_wait(&accf[a], (uint32_t)((t / kAcc) & 1), kWaitCycles))) {
+                const int a = ring_blk((uint32_t)t);
+                if (!__all_sync(0xffffffffu, tc::mbar_wait(&accf[a], ring_use((uint32_t)t) & 1u, kWaitCycles))) {
                     ok = false;
                     break;
                 }
                 tc::fence_after_sync();
                 float v[16];
-                tc::tmem_ld16(tmem + (uint32_t)(a * kCh + 16 * half) + ((uint32_t)(quad * 32) << 16), v);
+                const uint32_t ta = tmem + (uint32_t)(a * kCh + 16 * half) + ((uint32_t)(quad * 32) << 16);
+                tc::tmem_ld16(ta, v);
+                // the block's next row accumulates onto zeros
+                tc::tmem_st16_zero(ta);
+                tc::tmem_wait_st();
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&acce[a]);

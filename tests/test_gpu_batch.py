@@ -162,3 +162,17 @@ def test_smallest_betas_near_the_cutoff_match_oracle():
     L = [32] * 2 + [64] * 2
     g, o, tr, tr_o = run_both(L, 2, [2e-16, 0.3], 21, 12, 3, True)
     assert_same(g, o, tr, tr_o)
+
+
+@pytest.mark.parametrize("L,S,beta", [
+    ([512] * 2 + [1024] * 2 + [2048] * 2, 2, MIXED_BETA),           # 8, 16 and 32 lanes per row
+    ([160] * 2 + [128] * 4 + [96] * 2 + [2048] * 2, 2, MIXED_BETA),  # item and march groups interleaved
+])
+def test_row_marching_sides_match_oracle(L, S, beta):
+    """Sides 128 .. 2048 that are powers of two go through the row-marching
+    path (a row held by L/64 lanes, lane groups marching down whole rows);
+    other sides through the item path.  Both, side by side in one launch and
+    across lattice starts within a lane group's run, equal the oracle's
+    batched run bit for bit, with exchanges and traces."""
+    g, o, tr, tr_o = run_both(L, S, beta, 61, 9, 3, True)
+    assert_same(g, o, tr, tr_o)
