@@ -79,6 +79,18 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
+// Eight FP32 values as two bfloat16 parts, packed in pairs: hi = bf16(v) and
+// lo = bf16(v - hi) (v - hi is exact in FP32), so hi + lo equals v to about
+// 2^-17 relative.
+__device__ __forceinline__ void split_bf16(const float (&v)[8], uint32_t (&hi)[4], uint32_t (&lo)[4])
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        hi[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
+        lo[j] = pack_bf16x2(v[2 * j] - bf16_lo(hi[j]), v[2 * j + 1] - bf16_hi(hi[j]));
+    }
+}
+
 __device__ __forceinline__ float rcp_approx(float x)
 {
     float r;
@@ -644,6 +656,7 @@ struct RingConv {
     CUtensorMap tmap[kGroups];  // a_in viewed as (8 channels, L + 2 pixels, L rows, C chains), channel group g
     const __nv_bfloat16 *a_in;
     __nv_bfloat16 *a_out;  // nullable when PROJ
+    __nv_bfloat16 *a_lo;   // BWD, nullable: bf16(dz_prev - bf16(dz_prev)) beside a_out (for the weight gradient)
     float *z_out;          // nullable
     float *P;              // PROJ: 9 planes of C L^2
     const float *zg;       // BWD: z of the layer below (FP32, NHWC) for gelu'
@@ -1036,11 +1049,18 @@ __global__ void __launch_bounds__(ring_threads<FUSED>(), 2) conv32_ring_kernel(c
                         dq[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
                     }
                     if (p.a_out) {
-                        uint32_t pk[8];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) pk[i] = pack_bf16x2(v[2 * i], v[2 * i + 1]);
-                        store_act(p.a_out, L, w.c, y, w.x0 + m, 16 * half, make_uint4(pk[0], pk[1], pk[2], pk[3]));
-                        store_act(p.a_out, L, w.c, y, w.x0 + m, 16 * half + 8, make_uint4(pk[4], pk[5], pk[6], pk[7]));
+                        for (int h8 = 0; h8 < 2; ++h8) {
+                            float v8[8];
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) v8[i] = v[8 * h8 + i];
+                            uint32_t hb[4], rb[4];
+                            split_bf16(v8, hb, rb);
+                            store_act(p.a_out, L, w.c, y, w.x0 + m, 16 * half + 8 * h8, make_uint4(hb[0], hb[1], hb[2], hb[3]));
+                            if (p.a_lo)
+                                store_act(p.a_lo, L, w.c, y, w.x0 + m, 16 * half + 8 * h8,
+                                          make_uint4(rb[0], rb[1], rb[2], rb[3]));
+                        }
                     }
                 } else {
 #pragma unroll
@@ -1181,7 +1201,7 @@ __global__ void __launch_bounds__(kThreads) pool_kernel(int L, int64_t C, int br
 // dz3 = gelu'(z3) * sum_k W4[i][k] * d4(p - off_k),  d4(p) = dlogit(block of p) / 64.
 __global__ void __launch_bounds__(kThreads) l4_bwd_data_kernel(int L, int64_t C, const float *params,
                                                                const float *dlogits, const float *z3, float *dz3,
-                                                               __nv_bfloat16 *dz3b)
+                                                               __nv_bfloat16 *dz3b, __nv_bfloat16 *dz3r)
 {
     __shared__ float W[kN1];
     for (int i = threadIdx.x; i < kN1; i += blockDim.x) W[i] = bf16r(params[kOffW4 + i]);
@@ -1221,10 +1241,13 @@ __global__ void __launch_bounds__(kThreads) l4_bwd_data_kernel(int L, int64_t C,
         out[0] = make_float4(v[0], v[1], v[2], v[3]);
         out[1] = make_float4(v[4], v[5], v[6], v[7]);
         // bfloat16 copy with halo columns: the operand of the next data gradient on the tensor cores
-        if (dz3b)
-            store_act(dz3b, L, c, y, x, i8,
-                      make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                                 pack_bf16x2(v[6], v[7])));
+        // (and, with the rounding of its remainder, of the weight gradient)
+        if (dz3b) {
+            uint32_t hb[4], rb[4];
+            split_bf16(v, hb, rb);
+            store_act(dz3b, L, c, y, x, i8, make_uint4(hb[0], hb[1], hb[2], hb[3]));
+            if (dz3r) store_act(dz3r, L, c, y, x, i8, make_uint4(rb[0], rb[1], rb[2], rb[3]));
+        }
     }
 }
 
@@ -1453,6 +1476,277 @@ __global__ void __launch_bounds__(32 * kReduceWarps) reduce_partials_kernel(cons
             grad[w_off + e] = t;
         else
             grad[b_off + (e - nw)] = t;
+    }
+}
+
+// Weight gradients of a 32 -> 32 layer on the tensor cores (L a multiple of
+// 128).  With a the layer's input (bfloat16, halo columns) and dz the gradient
+// of its pre-activations,
+//   dW[o][i][k] = sum_p dz(p)[o] a(p + off_k)[i],   db[o] = sum_p dz(p)[o],
+// off_k = (dy - 1, dx - 1) for tap k = 3 dy + dx.  Per 128-pixel row segment
+// of output row y this is, for each dy, one GEMM over the 128 pixels (K):
+//   D_dy[m][n] += sum_x A_y+dy-1[m][x] B_y[n][x]
+// with M = 128 rows, of which rows m = 32 dx + i (dx = 0..2) are the input row
+// y + dy - 1 shifted by dx - 1 and rows 96..127 are not used, and N = 64
+// columns n = 32 h + o: dz in two bfloat16 parts, h = 0 its rounding and
+// h = 1 the rounding of the remainder, so that a x (hi + lo) carries dz to
+// about 2^-17 and the FP32 accumulation sees the unrounded gradient to that
+// accuracy (dW = D[.][o] + D[.][32 + o]).
+// Both operands are MN-major and come straight from the NHWC buffers: a
+// plane of 128 pixels x 16 bytes (8 channels) is the core-matrix form with
+// K rows of 16 bytes, LBO = 128 bytes along K, SBO = 2048 bytes between the
+// planes of 8-channel groups.  A staged input row is 12 tensor copies
+// (dx, channel group) of the row starting at pixel x0 - 1 + dx; the unused M
+// rows 96..127 read the 8 KB after it (the next slot, or the first gradient
+// slot after the last one), whose products land in TMEM lanes no one reads.
+// A staged gradient row holds 8 planes (h, channel group).
+// Work: the (chain, segment, row) lines of all chains are cut into one
+// contiguous range per CTA (ranges differ by at most one row); a range is
+// walked as runs of consecutive rows of one (chain, segment), each staging
+// its input rows r0 - 1 .. r0 + n once.  The three accumulators (3 x 64 TMEM
+// columns) collect the CTA's whole range; at the end they are written as the
+// CTA's partial sums in the weight-gradient layout (e = (o CIN + i) 9 + k,
+// then the biases).
+// Warp roles (bounded mbarrier waits): warp 0 lane 0 issues the tensor
+// copies, up to 3 rows ahead; warp 1 lane 0 the MMAs (three per 16-pixel K
+// step: 24 per row); warps 2..5 add up every staged gradient row for the bias
+// sums (fixed order) and, after the last MMA, read the accumulators.  A
+// gradient slot is free once its MMAs have completed and the four bias
+// warps have read it.
+constexpr int kWgActSlots = 6;                      // staged input rows (3 in use, 3 ahead)
+constexpr int kWgDzSlots = 4;                       // staged gradient rows (1 in use, 3 ahead)
+constexpr int kWgBiasWarps = 4;
+constexpr uint32_t kWgPlane = kTileM * 16;          // 128 pixels x 8 channels, bfloat16
+constexpr uint32_t kWgActBytes = 12 * kWgPlane;     // (dx, channel group)
+constexpr uint32_t kWgDzBytes = 8 * kWgPlane;       // hi and lo, 4 channel groups each
+constexpr uint32_t kWgDz0 = kWgActSlots * kWgActBytes;
+constexpr uint32_t kWgBias = kWgDz0 + kWgDzSlots * kWgDzBytes;   // per bias warp 32 sums
+constexpr uint32_t kWgBar = kWgBias + kWgBiasWarps * kCh * 4;
+constexpr uint32_t kWgSmem = kWgBar + (2 * kWgActSlots + 2 * kWgDzSlots + 1) * 8 + 16;
+constexpr int kWgThreads = 64 + 32 * kWgBiasWarps;
+constexpr int kWgN = 2 * kCh;                       // columns per accumulator (hi, lo)
+constexpr uint32_t kWgTmemCols = 256;               // 3 x 64 used
+static_assert(kWgDz0 >= kWgActBytes + 4 * kWgPlane && kWgSmem <= 227 * 1024,
+              "the unused M rows of the last input slot read the gradient slots; one CTA per SM");
+
+struct WgradTc {
+    CUtensorMap act;  // a: (32 channels, L + 2 pixels, L rows, C chains), boxes 8 x 128 x 1 x 1
+    CUtensorMap hi;   // bf16(dz), same layout
+    CUtensorMap lo;   // bf16(dz - bf16(dz)), same layout
+    float *partial;   // [gridDim.x][kN2 + kCh]
+    int L, segs;
+    int64_t lines;    // C segs L
+};
+
+// The run of this CTA's range that starts at line `lin`: chain, segment, first
+// row and row count.
+__device__ __forceinline__ RingUnit wg_run(const WgradTc &p, int64_t lin, int64_t end)
+{
+    RingUnit w;
+    const int64_t col = lin / p.L;
+    w.r0 = (int)(lin - col * p.L);
+    w.nrows = (int)min((int64_t)(p.L - w.r0), end - lin);
+    w.c = col / p.segs;
+    w.x0 = (int)(col - w.c * p.segs) * kTileM;
+    return w;
+}
+
+__global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_constant__ WgradTc p)
+{
+    extern __shared__ __align__(1024) uint8_t wg_smem[];
+    float *bias_part = reinterpret_cast<float *>(wg_smem + kWgBias);
+    uint64_t *afull = reinterpret_cast<uint64_t *>(wg_smem + kWgBar);
+    uint64_t *aempty = afull + kWgActSlots, *dfull = aempty + kWgActSlots, *dempty = dfull + kWgDzSlots;
+    uint64_t *drain = dempty + kWgDzSlots;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(drain + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int L = p.L;
+    const int64_t begin = blockIdx.x * p.lines / gridDim.x, end = (blockIdx.x + 1) * p.lines / gridDim.x;
+
+    if (warp == 1) tc::tmem_alloc(tslot, kWgTmemCols);
+    if (tid == 0) {
+        for (int s = 0; s < kWgActSlots; ++s) {
+            tc::mbar_init(&afull[s], 1);
+            tc::mbar_init(&aempty[s], 1);
+        }
+        for (int s = 0; s < kWgDzSlots; ++s) {
+            tc::mbar_init(&dfull[s], 1);
+            tc::mbar_init(&dempty[s], 1 + kWgBiasWarps);
+        }
+        tc::mbar_init(drain, 1);
+        tc::fence_mbar_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t na = 0, nd = 0;  // input and gradient rows staged so far
+            auto stage_act = [&](const RingUnit &w, int r) -> bool {
+                const uint32_t s = na % kWgActSlots;
+                if (na >= kWgActSlots && !tc::mbar_wait(&aempty[s], ((na / kWgActSlots) + 1) & 1, kWaitCycles))
+                    return false;
+                const int y = wrap(r, L);
+                tc::mbar_arrive_expect_tx(&afull[s], kWgActBytes);
+                uint8_t *dst = wg_smem + s * kWgActBytes;
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                    for (int g = 0; g < kGroups; ++g)
+                        tc::tma_load_4d(dst + (dx * kGroups + g) * kWgPlane, &p.act, 8 * g, w.x0 + dx, y, (int)w.c,
+                                        &afull[s]);
+                ++na;
+                return true;
+            };
+            auto stage_dz = [&](const RingUnit &w, int r) -> bool {
+                const uint32_t s = nd % kWgDzSlots;
+                if (nd >= kWgDzSlots && !tc::mbar_wait(&dempty[s], ((nd / kWgDzSlots) + 1) & 1, kWaitCycles))
+                    return false;
+                tc::mbar_arrive_expect_tx(&dfull[s], kWgDzBytes);
+                uint8_t *dst = wg_smem + kWgDz0 + s * kWgDzBytes;
+#pragma unroll
+                for (int g = 0; g < kGroups; ++g) {
+                    tc::tma_load_4d(dst + g * kWgPlane, &p.hi, 8 * g, w.x0 + 1, r, (int)w.c, &dfull[s]);
+                    tc::tma_load_4d(dst + (kGroups + g) * kWgPlane, &p.lo, 8 * g, w.x0 + 1, r, (int)w.c, &dfull[s]);
+                }
+                ++nd;
+                return true;
+            };
+            for (int64_t lin = begin; lin < end && ok;) {
+                const RingUnit w = wg_run(p, lin, end);
+                lin += w.nrows;
+                ok = stage_act(w, w.r0 - 1) && stage_act(w, w.r0);
+                for (int j = 0; j < w.nrows && ok; ++j) ok = stage_act(w, w.r0 + j + 1) && stage_dz(w, w.r0 + j);
+            }
+            // on a failure no copy may still be writing into shared memory when the CTA exits
+            if (!ok) {
+                for (uint32_t m = na > kWgActSlots ? na - kWgActSlots : 0; m < na; ++m)
+                    tc::mbar_wait(&afull[m % kWgActSlots], (m / kWgActSlots) & 1, kWaitCycles);
+                for (uint32_t m = nd > kWgDzSlots ? nd - kWgDzSlots : 0; m < nd; ++m)
+                    tc::mbar_wait(&dfull[m % kWgDzSlots], (m / kWgDzSlots) & 1, kWaitCycles);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16_f32_mn(kTileM, kWgN);
+            const uint64_t a_desc0 = tc::smem_desc(tc::smem_u32(wg_smem), 128, kWgPlane);
+            const uint64_t b_desc0 = tc::smem_desc(tc::smem_u32(wg_smem + kWgDz0), 128, kWgPlane);
+            const uint32_t a_lo0 = (uint32_t)a_desc0, a_hi = (uint32_t)(a_desc0 >> 32);
+            const uint32_t b_lo0 = (uint32_t)b_desc0, b_hi = (uint32_t)(b_desc0 >> 32);
+            uint32_t ma = 0, md = 0, ready = 0;  // first input row of the run; gradient rows consumed; input rows landed
+            bool first = true;
+            for (int64_t lin = begin; lin < end && ok;) {
+                const RingUnit w = wg_run(p, lin, end);
+                lin += w.nrows;
+                for (int j = 0; j < w.nrows && ok; ++j) {
+                    // gradient row r0 + j needs input rows r0 + j - 1 .. r0 + j + 1 (indices ma + j .. ma + j + 2)
+                    while (ready < ma + (uint32_t)j + 3 && ok) {
+                        if (!tc::mbar_wait(&afull[ready % kWgActSlots], (ready / kWgActSlots) & 1u, kWaitCycles))
+                            ok = false;
+                        ++ready;
+                    }
+                    const uint32_t ds = md % kWgDzSlots;
+                    if (ok && !tc::mbar_wait(&dfull[ds], (md / kWgDzSlots) & 1u, kWaitCycles)) ok = false;
+                    if (!ok) break;
+                    tc::fence_after_sync();
+                    const uint32_t b_row = b_lo0 + ((ds * kWgDzBytes) >> 4);
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy) {
+                        const uint32_t a_row = a_lo0 + (((ma + (uint32_t)(j + dy)) % kWgActSlots) * kWgActBytes >> 4);
+#pragma unroll
+                        for (int ks = 0; ks < kTileM / 16; ++ks)
+                            tc::mma_bf16_w(tmem + (uint32_t)(dy * kWgN), a_row + (uint32_t)(ks * 16), a_hi,
+                                           b_row + (uint32_t)(ks * 16), b_hi, idesc, (first && ks == 0) ? 0u : 1u);
+                    }
+                    first = false;
+                    tc::mma_commit(&dempty[ds]);
+                    ++md;
+                    tc::mma_commit(&aempty[(ma + (uint32_t)j) % kWgActSlots]);  // input row r0 + j - 1: last use
+                }
+                if (!ok) break;
+                tc::mma_commit(&aempty[(ma + (uint32_t)w.nrows) % kWgActSlots]);
+                tc::mma_commit(&aempty[(ma + (uint32_t)w.nrows + 1) % kWgActSlots]);
+                ma += (uint32_t)w.nrows + 2;
+            }
+            // every MMA has completed before the accumulators are read and the TMEM is freed
+            tc::mma_commit(drain);
+            if (!tc::mbar_wait(drain, 0, kWaitCycles)) ok = false;
+        }
+        __syncwarp();
+    } else {
+        // bias sums: bias warp q adds pixels 32 q .. 32 q + 31 of every staged
+        // gradient row; lane = 4 p8 + g holds channels 8 g .. 8 g + 7 of the
+        // pixels 32 q + 8 it + p8 (it = 0..3), hi + lo
+        const int q = warp - 2, g = lane & 3, p8 = lane >> 2;
+        float acc[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] = 0.0f;
+        const int64_t rows = end - begin;
+        for (int64_t md = 0; md < rows; ++md) {
+            const uint32_t ds = (uint32_t)(md % kWgDzSlots);
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&dfull[ds], (uint32_t)(md / kWgDzSlots) & 1u, kWaitCycles))) {
+                ok = false;
+                break;
+            }
+            const uint8_t *dz = wg_smem + kWgDz0 + ds * kWgDzBytes;
+#pragma unroll
+            for (int it = 0; it < 4; ++it) {
+                const int px = 32 * q + 8 * it + p8;
+                const uint4 h = *reinterpret_cast<const uint4 *>(dz + g * kWgPlane + px * 16);
+                const uint4 l = *reinterpret_cast<const uint4 *>(dz + (kGroups + g) * kWgPlane + px * 16);
+                const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[2 * j] += bf16_lo(hw[j]) + bf16_lo(lw[j]);
+                    acc[2 * j + 1] += bf16_hi(hw[j]) + bf16_hi(lw[j]);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&dempty[ds]);
+        }
+        // lanes of one channel group (lane ^ 4, ^ 8, ^ 16), then the four warps in order
+#pragma unroll
+        for (int sh = 4; sh < 32; sh <<= 1)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], sh);
+        if (lane < 4)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) bias_part[q * kCh + 8 * g + j] = acc[j];
+    }
+    if (__syncthreads_or(!ok)) ok = false;
+    tc::fence_after_sync();
+    if (warp >= 2 && ok) {
+        // TMEM lane m = 32 quad + lane: input channel i = lane of tap column
+        // dx = quad (quad < 3); lanes 96..127 are not used
+        const int quad = warp & 3;
+        float *out = p.partial + (int64_t)blockIdx.x * (kN2 + kCh);
+#pragma unroll 1
+        for (int dy = 0; dy < 3; ++dy) {
+#pragma unroll 1
+            for (int oh = 0; oh < 2; ++oh) {
+                float vh[16], vl[16];
+                const uint32_t ta = tmem + (uint32_t)(dy * kWgN + 16 * oh) + ((uint32_t)(quad * 32) << 16);
+                tc::tmem_ld16(ta, vh);
+                tc::tmem_ld16(ta + (uint32_t)kCh, vl);
+                if (quad < 3)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) out[((16 * oh + j) * kCh + lane) * 9 + 3 * dy + quad] = vh[j] + vl[j];
+            }
+        }
+        if (warp == 2)
+            out[kN2 + lane] = ((bias_part[lane] + bias_part[kCh + lane]) + bias_part[2 * kCh + lane]) +
+                              bias_part[3 * kCh + lane];
+    }
+    if (!ok && tid == 0) atomicExch(&g_tc_error, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, kWgTmemCols);
     }
 }
 
@@ -1694,6 +1988,7 @@ int check_chains(int64_t L, int64_t C)
 struct NetWork {
     float *z1, *z2, *z3, *da, *db, *partial, *P, *tz;
     __nv_bfloat16 *a1, *a2, *a3, *ta, *gb1, *gb2;  // gb: bfloat16 gradients with halo columns (training)
+    __nv_bfloat16 *gr1, *gr2;                      // the bfloat16 roundings of their remainders
     int64_t n_cta;
     size_t bytes;
 };
@@ -1718,6 +2013,9 @@ NetWork net_layout(int64_t L, int64_t C, int train, char *base)
         w.a3 = (__nv_bfloat16 *)take(apx * 2);
         w.da = (float *)take(pix * 4); w.db = (float *)take(pix * 4);
         w.gb1 = (__nv_bfloat16 *)take(apx * 2); w.gb2 = (__nv_bfloat16 *)take(apx * 2);
+        if (L % kTileM == 0) {
+            w.gr1 = (__nv_bfloat16 *)take(apx * 2); w.gr2 = (__nv_bfloat16 *)take(apx * 2);
+        }
         DeviceInfo info{152};
         device_info(&info);
         w.n_cta = (int64_t)info.sm_count * kWgradCtasPerSm;
@@ -1787,9 +2085,10 @@ bool encode_rows(CUtensorMap (&m)[kGroups], const __nv_bfloat16 *a, int L, int64
 
 // The data gradient of a 32 -> 32 layer (weights at w_off) on the tensor
 // cores: dz_prev = gelu'(zg) * conv^T(in), in the bfloat16 gradient with halo
-// columns; writes d_out (FP32) and, if given, a_out (bfloat16, halo columns).
+// columns; writes d_out (FP32) and, if given, a_out (bfloat16, halo columns)
+// and a_lo (the bfloat16 rounding of d_out - a_out).
 int launch_ring_bwd(int L, int64_t C, const float *params, int w_off, const __nv_bfloat16 *in, const float *zg,
-                    float *d_out, __nv_bfloat16 *a_out, cudaStream_t s)
+                    float *d_out, __nv_bfloat16 *a_out, __nv_bfloat16 *a_lo, cudaStream_t s)
 {
     DeviceInfo info{152};
     device_info(&info);
@@ -1797,6 +2096,7 @@ int launch_ring_bwd(int L, int64_t C, const float *params, int w_off, const __nv
     if (!encode_rows(p.tmap, in, L, C)) return nfail(ISING_ECUDA, "cuTensorMapEncodeTiled failed");
     p.a_in = in;
     p.a_out = a_out;
+    p.a_lo = a_lo;
     p.zg = zg;
     p.d_out = d_out;
     p.params = params;
@@ -1814,6 +2114,43 @@ int launch_ring_bwd(int L, int64_t C, const float *params, int w_off, const __nv
     cudaFuncSetAttribute(conv32_ring_kernel<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)RingLayout<false>::bytes);
     conv32_ring_kernel<false, true, false><<<grid, kRingThreads, RingLayout<false>::bytes, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ISING_OK : nfail(ISING_ECUDA, cudaGetErrorString(e));
+}
+
+// The weight gradients of a 32 -> 32 layer on the tensor cores (L a multiple
+// of 128): the layer's input a (bfloat16, halo columns) and its gradient as
+// hi = bf16(dz), lo = bf16(dz - hi) (same layout); one CTA per SM writes its
+// partial sums into partial[cta][kN2 + kCh].  Returns the number of CTAs.
+int launch_wgrad_tc(int L, int64_t C, const __nv_bfloat16 *a, const __nv_bfloat16 *hi, const __nv_bfloat16 *lo,
+                    float *partial, int64_t max_ctas, cudaStream_t s, int64_t *n_cta)
+{
+    EncodeTiledFn fn = encode_tiled_fn();
+    if (fn == nullptr) return nfail(ISING_ECUDA, "cuTensorMapEncodeTiled is not available");
+    DeviceInfo info{152};
+    device_info(&info);
+    WgradTc p{};
+    const cuuint64_t dims[4] = {(cuuint64_t)kCh, (cuuint64_t)L + 2, (cuuint64_t)L, (cuuint64_t)C};
+    const cuuint64_t strides[3] = {(cuuint64_t)kCh * 2, (cuuint64_t)(L + 2) * kCh * 2,
+                                   (cuuint64_t)L * (L + 2) * kCh * 2};
+    const cuuint32_t box[4] = {8, kTileM, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const __nv_bfloat16 *src[3] = {a, hi, lo};
+    CUtensorMap *maps[3] = {&p.act, &p.hi, &p.lo};
+    for (int t = 0; t < 3; ++t)
+        if (fn(maps[t], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)src[t], dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return nfail(ISING_ECUDA, "cuTensorMapEncodeTiled failed");
+    p.partial = partial;
+    p.L = L;
+    p.segs = L / kTileM;
+    p.lines = C * p.segs * L;
+    // every CTA gets at least one row, so every partial row is written
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>({(int64_t)info.sm_count, max_ctas, p.lines}));
+    cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
+    wgrad_tc_kernel<<<(unsigned)grid, kWgThreads, kWgSmem, s>>>(p);
+    *n_cta = grid;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ISING_OK : nfail(ISING_ECUDA, cudaGetErrorString(e));
 }
@@ -2035,38 +2372,48 @@ ISING_API int ising_net_backward(int64_t L, int64_t C, const void *black_dev, co
     cudaFuncSetAttribute(wgrad_kernel<kCh, kCh>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm32);
     cudaFuncSetAttribute(wgrad_kernel<kCh, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
     cudaFuncSetAttribute(wgrad_kernel<1, kCh>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
-    auto reduce = [&](int ne, int nw, int w_off, int b_off) {
-        reduce_partials_kernel<<<(unsigned)((ne + 31) / 32), 32 * kReduceWarps, 0, s>>>(w.partial, w.n_cta, ne, nw,
+    auto reduce = [&](int ne, int nw, int w_off, int b_off, int64_t n_cta) {
+        reduce_partials_kernel<<<(unsigned)((ne + 31) / 32), 32 * kReduceWarps, 0, s>>>(w.partial, n_cta, ne, nw,
                                                                                        grad_dev, w_off, b_off);
     };
     // layer 4
     wgrad_kernel<kCh, 1><<<gw, 256, sm4, s>>>(ch, C, w.a3, nullptr, dlogits_dev, w.partial);
-    reduce(kN1 + 1, kN1, kOffW4, kOffB4);
-    // the data gradients of the 32 -> 32 layers run on the tensor cores for L a multiple of 128
+    reduce(kN1 + 1, kN1, kOffW4, kOffB4, w.n_cta);
+    // for L a multiple of 128 the data and weight gradients of the 32 -> 32
+    // layers run on the tensor cores; their gradients are then also kept as
+    // bfloat16 parts (gb: the rounding, gr: the rounding of the remainder)
     const bool ring = L % kTileM == 0;
     l4_bwd_data_kernel<<<grid1d(4 * npix, kThreads), kThreads, 0, s>>>((int)L, C, params_dev, dlogits_dev, w.z3,
-                                                                     w.da, ring ? w.gb1 : nullptr);  // dz3
+                                                                     w.da, ring ? w.gb1 : nullptr,
+                                                                     ring ? w.gr1 : nullptr);  // dz3
     // layer 3
-    wgrad_kernel<kCh, kCh><<<gw, 256, sm32, s>>>(ch, C, w.a2, w.da, nullptr, w.partial);
-    reduce(kN2 + kCh, kN2, kOffW3, kOffB3);
+    int64_t n_tc = 0;
     if (ring) {
-        rc = launch_ring_bwd((int)L, C, params_dev, kOffW3, w.gb1, w.z2, w.db, w.gb2, s);  // dz2
+        rc = launch_wgrad_tc((int)L, C, w.a2, w.gb1, w.gr1, w.partial, w.n_cta, s, &n_tc);
+        if (rc) return rc;
+        reduce(kN2 + kCh, kN2, kOffW3, kOffB3, n_tc);
+        rc = launch_ring_bwd((int)L, C, params_dev, kOffW3, w.gb1, w.z2, w.db, w.gb2, w.gr2, s);  // dz2
         if (rc) return rc;
     } else {
+        wgrad_kernel<kCh, kCh><<<gw, 256, sm32, s>>>(ch, C, w.a2, w.da, nullptr, w.partial);
+        reduce(kN2 + kCh, kN2, kOffW3, kOffB3, w.n_cta);
         conv32_bwd_data_kernel<<<g, kThreads, smem, s>>>((int)L, C, params_dev, kOffW3, w.da, w.z2, w.db);  // dz2
     }
     // layer 2
-    wgrad_kernel<kCh, kCh><<<gw, 256, sm32, s>>>(ch, C, w.a1, w.db, nullptr, w.partial);
-    reduce(kN2 + kCh, kN2, kOffW2, kOffB2);
     if (ring) {
-        rc = launch_ring_bwd((int)L, C, params_dev, kOffW2, w.gb2, w.z1, w.da, nullptr, s);  // dz1
+        rc = launch_wgrad_tc((int)L, C, w.a1, w.gb2, w.gr2, w.partial, w.n_cta, s, &n_tc);
+        if (rc) return rc;
+        reduce(kN2 + kCh, kN2, kOffW2, kOffB2, n_tc);
+        rc = launch_ring_bwd((int)L, C, params_dev, kOffW2, w.gb2, w.z1, w.da, nullptr, nullptr, s);  // dz1
         if (rc) return rc;
     } else {
+        wgrad_kernel<kCh, kCh><<<gw, 256, sm32, s>>>(ch, C, w.a1, w.db, nullptr, w.partial);
+        reduce(kN2 + kCh, kN2, kOffW2, kOffB2, w.n_cta);
         conv32_bwd_data_kernel<<<g, kThreads, smem, s>>>((int)L, C, params_dev, kOffW2, w.db, w.z1, w.da);  // dz1
     }
     // layer 1
     wgrad_kernel<1, kCh><<<gw, 256, sm1, s>>>(ch, C, nullptr, w.da, nullptr, w.partial);
-    reduce(kN1 + kCh, kN1, kOffW1, kOffB1);
+    reduce(kN1 + kCh, kN1, kOffW1, kOffB1, w.n_cta);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ISING_OK : nfail(ISING_ECUDA, cudaGetErrorString(e));
 }

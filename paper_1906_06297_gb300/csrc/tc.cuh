@@ -4,11 +4,15 @@
 // through an mbarrier, the warp-wide TMEM loads of the epilogue, and the
 // tensor copies (TMA) that stage operands in shared memory.
 //
-// Operand layout used here: K-major, no swizzle.  A "core matrix" is 8 rows x
-// 16 bytes (8 bf16 along K) stored as 128 contiguous bytes, row r at +16 r.
-// The descriptor's leading byte offset (LBO) is the distance between core
-// matrices that are neighbours along K, its stride byte offset (SBO) the
-// distance between neighbouring 8-row groups along M (or N).
+// Operand layouts used here, both without swizzle.  A "core matrix" is 8 rows
+// of 16 bytes stored as 128 contiguous bytes, row r at +16 r.
+//   K-major: a row is one M (or N) index, its 16 bytes 8 bf16 along K.
+//   MN-major: a row is one K index, its 16 bytes 8 consecutive M (or N)
+//            indices (so an NHWC tile of 8 channels x pixels, pixels along K,
+//            is already in this form).
+// In both, the descriptor's leading byte offset (LBO) is the distance between
+// core matrices that are neighbours along K and its stride byte offset (SBO)
+// the distance between neighbouring 8-index groups along M (or N).
 #pragma once
 
 #include <cstdint>
@@ -35,6 +39,12 @@ __host__ __device__ constexpr uint64_t smem_desc(uint32_t saddr, uint32_t lbo, u
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// The same with both operands MN-major (transpose bits 15 and 16).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N)
+{
+    return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
 }
 
 // TMEM allocation of `ncols` columns (a power of two >= 32) by one whole warp;

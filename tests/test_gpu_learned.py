@@ -177,7 +177,10 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable():
     assert torch.equal(again, want)
 
 
-@pytest.mark.parametrize("L,C", [(32, 2), (128, 2)])
+# (32, 2): CUDA-core weight gradients; (128, 2) and (256, 3): tensor-core
+# weight gradients of the 32 -> 32 layers, one and two row segments, CTA
+# ranges of one or two rows that run across chain boundaries, and of ~10 rows
+@pytest.mark.parametrize("L,C", [(32, 2), (128, 2), (256, 3)])
 def test_backward_and_loss_match_oracle(L, C):
     mv = chains(L, C, 5)
     th = theta32(2, 0.15)
@@ -200,6 +203,11 @@ def test_backward_and_loss_match_oracle(L, C):
     g = grad.cpu().numpy().astype(np.float64)
     scale = np.abs(want_grad).max()
     np.testing.assert_allclose(g, want_grad, rtol=2e-3, atol=2e-5 * scale)
+    # the reductions have a fixed order: a second backward pass is bit-identical
+    again = torch.zeros_like(grad)
+    ising.ising_net_backward(L, C, mv.black, mv.white, params, dlogits, again, work)
+    ising.ising_net_check()
+    assert torch.equal(again, grad)
 
 
 def test_proposals_acceptances_and_flips_match_oracle():
