@@ -27,8 +27,11 @@
 // a multiple of 128, conv32_tc_kernel otherwise), the second one also
 // contracting layer 4's input channels (P, the 9 tap projections); the tap
 // sums and block means (pool_kernel).  Every reduction has a fixed order, so
-// a forward pass is a deterministic function of the state.  Backward kernels:
-// FP32 on the CUDA cores, straight through the bfloat16 roundings.
+// a forward pass is a deterministic function of the state.  Backward kernels,
+// straight through the bfloat16 roundings: for L a multiple of 128 the data
+// and weight gradients of the two 32 -> 32 layers on the tensor cores
+// (conv32_ring_kernel in BWD mode, wgrad_tc_kernel), the rest in FP32 on the
+// CUDA cores; weight gradients as fixed-order per-CTA partial sums.
 //
 // Move.  Block b is drawn by inverse CDF of q_x (purpose-3 draw, site 0, in
 // the chain's stream) or uniformly; x' = x with block b flipped; the flip is
@@ -112,6 +115,8 @@ __device__ __forceinline__ float ex2_approx(float x)
 // negative z too.  Evaluated in FP32 with the hardware reciprocal and 2^x the
 // relative error of gelu is about 5e-6 for |z| < 6 (the rounding of the
 // exponent -x^2 + P), far below the bfloat16 step the result is rounded to.
+// With h = Phi(-|z|), gelu(z) = max(z, 0) - |z| h for either sign of z (z (1 -
+// h) for z >= 0, z h for z < 0), one multiply-add.
 __device__ __forceinline__ float gelu(float z)
 {
     const float x = fabsf(z) * 0.70710678118654752f;
@@ -126,8 +131,9 @@ __device__ __forceinline__ float gelu(float z)
     p = fmaf(p, t, 0.37409196f);
     p = fmaf(p, t, 1.00002368f);
     p = fmaf(p, t, -1.26551223f);
-    const float half = 0.5f * t * ex2_approx(fmaf(-x, x, p) * 1.44269504088896341f);  // Phi(-|z|)
-    return z * (z >= 0.0f ? 1.0f - half : half);
+    // -|z| Phi(-|z|) = x (-sqrt(1/2)) t 2^((-x^2 + P) log2 e)
+    const float nq = -0.70710678118654752f * t * ex2_approx(fmaf(-x, x, p) * 1.44269504088896341f);
+    return fmaf(x, nq, fmaxf(z, 0.0f));
 }
 
 // The same GELU for two values at once: the FP32 multiplies and adds as
@@ -182,10 +188,8 @@ __device__ __forceinline__ void gelu2(float &z0, float &z1)
     f2_unpack(x, x0, x1);
     float a0, a1;
     f2_unpack(f2_mul(f2_fma(f2_pack(-x0, -x1), x, p), f2_splat(1.44269504088896341f)), a0, a1);
-    float h0, h1;
-    f2_unpack(f2_mul(f2_mul(f2_splat(0.5f), t), f2_pack(ex2_approx(a0), ex2_approx(a1))), h0, h1);
-    z0 = z0 * (z0 >= 0.0f ? 1.0f - h0 : h0);
-    z1 = z1 * (z1 >= 0.0f ? 1.0f - h1 : h1);
+    const uint64_t nq = f2_mul(f2_mul(f2_splat(-0.70710678118654752f), t), f2_pack(ex2_approx(a0), ex2_approx(a1)));
+    f2_unpack(f2_fma(x, nq, f2_pack(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f))), z0, z1);
 }
 
 __device__ __forceinline__ float gelu_grad(float z)
@@ -584,18 +588,24 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv32_tc_kernel(const __grid
 //           completed;
 //   warps 2-9: epilogue, warp w on TMEM lanes 32 (w % 4) .. + 31 (its 32
 //           pixels) and columns 16 h .. 16 h + 15, h = (w - 2) / 4 (its 16
-//           channels): loads them, zeros them (every MMA accumulates), frees
-//           the block (acce, 8 arrivals), adds the bias and writes z
-//           (training) and a = bf16(gelu(z)).
+//           channels): loads them, sets them to the bias (every MMA
+//           accumulates, so the next row's sum starts from its bias; zero in
+//           BWD), frees the block (acce, 8 arrivals) and writes z (training)
+//           and a = bf16(gelu(z)).  (Adding the bias in the epilogue and
+//           gelu as z (1 - h) or z h by sign instead of max(z, 0) - |z| h:
+//           1.438 instead of 1.383 ms per full forward of 1024 chains.)
 //           Two warps per TMEM lane quadrant, four per SM sub-partition with
 //           two CTAs per SM, hide the latency of the GELU arithmetic.
 // PROJ (the last 32-channel layer): layer 4's channel contraction is done
 // here, on the tensor cores, as P[m][k] = sum_i a[m][i] W4[i][k] for the 9
 // taps k (N padded to 16): the epilogue stages the tile's a in shared memory
-// (a3full), the MMA thread multiplies it by W4^T into 16 more TMEM columns
-// (pfull, a3empty), and the epilogue warps of the first channel half store P
-// one tile later (pempty), as 9 FP32 planes P[k][pixel].  Then a3 itself need not reach global memory
-// (it still does when training, for the backward pass).
+// (a3full), lane 0 of a warp of its own (warp 10) multiplies it by W4^T into
+// 16 more TMEM columns (pfull, a3empty), and the epilogue warps of the first
+// channel half store P one tile later (pempty), as 9 FP32 planes P[k][pixel].
+// Then a3 itself need not reach global memory (it still does when training,
+// for the backward pass).  (With these MMAs on the row MMA thread, which then
+// waits for each tile's a3, a full forward of 1024 chains of 128^2 took
+// 1.383 ms instead of 1.371.)
 // BWD (the data gradient of a 32 -> 32 layer in the training backward pass):
 // the same contraction with the incoming gradient dz (bfloat16, halo columns)
 // as the staged rows and the weights transposed and tap-flipped, B_k[i][o] =
@@ -614,16 +624,18 @@ constexpr int kAcc = 7;         // accumulator blocks of 32 TMEM columns, one pe
 constexpr int kUnitRows = 32;
 constexpr int kEpiWarps = 8;
 constexpr int kRingThreads = 64 + 32 * kEpiWarps;
-constexpr int kRingLoader2 = 2 + kEpiWarps;  // the second loader warp of the fused first conv
-template <bool FUSED>
-constexpr int ring_threads() { return FUSED ? kRingThreads + 32 : kRingThreads; }
+// one more warp: the second loader of the fused first conv, or the issuer of
+// the layer-4 projection MMAs (PROJ)
+constexpr int kRingExtra = 2 + kEpiWarps;
+template <bool PROJ, bool FUSED>
+constexpr int ring_threads() { return (PROJ || FUSED) ? kRingThreads + 32 : kRingThreads; }
 constexpr int kProjN = 16;      // the 9 taps of layer 4, padded to an MMA N
 // channel-group planes 2176 bytes apart: each tensor copy lands on a 128-byte
 // boundary; 130 of its 136 16-byte entries are used
 constexpr uint32_t kRingPlane = 17 * 128;
 constexpr uint32_t kRowBytes = kGroups * kRingPlane;   // one staged row, or one a3 tile
 constexpr uint32_t kW4Bytes = kGroups * kProjN * 16;   // 1024
-constexpr int kRingBars = 2 * kRing + 2 * kAcc + 8 + 1;
+constexpr int kRingBars = 2 * kRing + 2 * kAcc + 8 + 2;
 // Shared-memory layout: the staged rows, then (only in the kernel that
 // projects onto layer 4) two a3 tiles, the weights, (PROJ) W4^T, the bias and
 // the barriers.  Without the a3 tiles two CTAs take 173 KB, so the SM keeps
@@ -736,7 +748,7 @@ __device__ __forceinline__ uint32_t chunk_bits(const Chains &ch, const ChunkWord
 }
 
 template <bool PROJ, bool BWD, bool FUSED>
-__global__ void __launch_bounds__(ring_threads<FUSED>(), 2) conv32_ring_kernel(const __grid_constant__ RingConv p)
+__global__ void __launch_bounds__(ring_threads<PROJ, FUSED>(), 2) conv32_ring_kernel(const __grid_constant__ RingConv p)
 {
     extern __shared__ __align__(1024) uint8_t ring_smem[];
     using Lay = RingLayout<PROJ>;
@@ -748,8 +760,8 @@ __global__ void __launch_bounds__(ring_threads<FUSED>(), 2) conv32_ring_kernel(c
     uint64_t *full = reinterpret_cast<uint64_t *>(ring_smem + Lay::bar);
     uint64_t *empty = full + kRing, *accf = empty + kRing, *acce = accf + kAcc;
     uint64_t *a3full = acce + kAcc, *a3empty = a3full + 2, *pfull = a3empty + 2, *pempty = pfull + 2;
-    uint64_t *drain = pempty + 2;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(drain + 1);
+    uint64_t *drain = pempty + 2, *pdrain = drain + 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(pdrain + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int L = p.bd.L;
     const int64_t npix = p.bd.C * (int64_t)L * L;
@@ -771,6 +783,7 @@ __global__ void __launch_bounds__(ring_threads<FUSED>(), 2) conv32_ring_kernel(c
             tc::mbar_init(&pempty[b], 4);
         }
         tc::mbar_init(drain, 1);
+        tc::mbar_init(pdrain, 1);
         tc::fence_mbar_init();
     }
     for (int e = tid; e < kTaps * kGroups * kCh; e += blockDim.x) {
@@ -806,11 +819,14 @@ __global__ void __launch_bounds__(ring_threads<FUSED>(), 2) conv32_ring_kernel(c
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
     const uint32_t tproj = tmem + (uint32_t)(kAcc * kCh);
-    // every accumulator block starts at zero, so that all MMAs accumulate
+    // every accumulator block starts at the bias (zero in BWD), so that all
+    // MMAs accumulate onto it
     if (warp >= 2 && warp < 2 + kEpiWarps) {
         const int quad = warp & 3, half = (warp - 2) >> 2;
-        for (int a = 0; a < kAcc; ++a)
-            tc::tmem_st16_zero(tmem + (uint32_t)(a * kCh + 16 * half) + ((uint32_t)(quad * 32) << 16));
+        float bias[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) bias[i] = sBias[16 * half + i];
+        for (int a = 0; a < kAcc; ++a) tc::tmem_st16(tmem + (uint32_t)(a * kCh + 16 * half) + ((uint32_t)(quad * 32) << 16), bias);
         tc::tmem_wait_st();
     }
     tc::fence_before_sync();
@@ -818,7 +834,7 @@ __global__ void __launch_bounds__(ring_threads<FUSED>(), 2) conv32_ring_kernel(c
     tc::fence_after_sync();
     bool ok = true;
 
-    if ((warp == 0 || warp == kRingLoader2) && FUSED) {
+    if ((warp == 0 || warp == kRingExtra) && FUSED) {
         // two loader warps building the rows of a1 from the spins: warp 0 the
         // rows of even ring index, the other warp those of odd index (one
         // warp building rows is a chain of shuffles, table loads and stores
@@ -912,31 +928,13 @@ __global__ void __launch_bounds__(ring_threads<FUSED>(), 2) conv32_ring_kernel(c
             // N = 32, 64 or 96: one, two or three accumulator blocks per MMA
             // (the N field holds N / 8 from bit 17)
             const uint32_t idesc0 = tc::idesc_bf16_f32(kTileM, 0);
-            const uint32_t idesc_p = tc::idesc_bf16_f32(kTileM, kProjN);
             const uint32_t ring_u32 = tc::smem_u32(ring), b_u32 = tc::smem_u32(sB);
-            const uint32_t a3_u32 = tc::smem_u32(a3s), w4_u32 = tc::smem_u32(sW4);
             // descriptors of the ring's first byte and of the stacked weights'
             // first byte, as 32-bit words (the MMAs add offsets to the low words)
             const uint64_t a_desc0 = tc::smem_desc(ring_u32, kRingPlane, 128);
             const uint64_t b_desc0 = tc::smem_desc(b_u32, kStackN * 16, 128);
             const uint32_t a_lo0 = (uint32_t)a_desc0, a_hi = (uint32_t)(a_desc0 >> 32);
             const uint32_t b_lo0 = (uint32_t)b_desc0, b_hi = (uint32_t)(b_desc0 >> 32);
-            // layer-4 projection of tile s (its a3 staged by the epilogue)
-            auto issue_proj = [&](int64_t s) -> bool {
-                const int b = (int)(s & 1);
-                if (!tc::mbar_wait(&a3full[b], (uint32_t)((s >> 1) & 1), kWaitCycles)) return false;
-                if (s >= 2 && !tc::mbar_wait(&pempty[b], (uint32_t)(((s >> 1) + 1) & 1), kWaitCycles)) return false;
-                tc::fence_after_sync();
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint64_t ad = tc::smem_desc(a3_u32 + b * kRowBytes + 2 * h * kRingPlane, kRingPlane, 128);
-                    const uint64_t bd = tc::smem_desc(w4_u32 + 2 * h * kProjN * 16, kProjN * 16, 128);
-                    tc::mma_bf16(tproj + (uint32_t)(b * kProjN), ad, bd, idesc_p, h > 0 ? 1u : 0u);
-                }
-                tc::mma_commit(&pfull[b]);
-                tc::mma_commit(&a3empty[b]);
-                return true;
-            };
             // Row-stationary: staged input row i of a unit is multiplied once,
             // for each (dx, K half), by the three dy taps stacked along N, into
             // the accumulator blocks of the output rows it feeds, i + 1 (dy =
@@ -986,20 +984,52 @@ __global__ void __launch_bounds__(ring_threads<FUSED>(), 2) conv32_ring_kernel(c
                     if (i >= 1) {
                         const uint32_t td = t + (uint32_t)(i - 1);  // row i - 1 has all 18 steps now
                         if (!(p.withhold && td == 0)) tc::mma_commit(&accf[ring_blk(td)]);
-                        if (PROJ && td >= 1 && !issue_proj((int64_t)td - 1)) ok = false;
                     }
                 }
                 n0 += (uint32_t)(w.nrows + 2);
                 t += (uint32_t)w.nrows;
             }
-            if (PROJ && ok && t >= 1 && !issue_proj((int64_t)t - 1)) ok = false;
             // every MMA has completed before the TMEM is freed
             tc::mma_commit(drain);
             tc::mbar_wait(drain, 0, kWaitCycles);
         }
         __syncwarp();
+    } else if (PROJ && warp == kRingExtra) {
+        if (lane == 0) {
+            // layer 4's channel contraction of every output row s, in order,
+            // once the epilogue has staged its a3 (a3full) and read the P of
+            // row s - 2 out of the same TMEM columns (pempty)
+            const uint32_t idesc_p = tc::idesc_bf16_f32(kTileM, kProjN);
+            const uint32_t a3_u32 = tc::smem_u32(a3s), w4_u32 = tc::smem_u32(sW4);
+            int64_t rows = 0;
+            for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x) rows += ring_unit(p, u).nrows;
+            for (int64_t s = 0; s < rows && ok; ++s) {
+                const int b = (int)(s & 1);
+                if (!tc::mbar_wait(&a3full[b], (uint32_t)((s >> 1) & 1), kWaitCycles) ||
+                    (s >= 2 && !tc::mbar_wait(&pempty[b], (uint32_t)(((s >> 1) + 1) & 1), kWaitCycles))) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint64_t ad = tc::smem_desc(a3_u32 + b * kRowBytes + 2 * h * kRingPlane, kRingPlane, 128);
+                    const uint64_t bd = tc::smem_desc(w4_u32 + 2 * h * kProjN * 16, kProjN * 16, 128);
+                    tc::mma_bf16(tproj + (uint32_t)(b * kProjN), ad, bd, idesc_p, h > 0 ? 1u : 0u);
+                }
+                tc::mma_commit(&pfull[b]);
+                tc::mma_commit(&a3empty[b]);
+            }
+            // its MMAs have completed before the TMEM is freed
+            tc::mma_commit(pdrain);
+            tc::mbar_wait(pdrain, 0, kWaitCycles);
+        }
+        __syncwarp();
     } else if (warp < 2 + kEpiWarps) {
         const int quad = warp & 3, half = (warp - 2) >> 2, m = quad * 32 + lane;
+        float bias[16];  // this warp's 16 channels (zero in BWD)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) bias[i] = sBias[16 * half + i];
         // P of tile s, pixel q (one tile behind the accumulators)
         auto read_proj = [&](int64_t s, int64_t q) -> bool {
             const int b = (int)(s & 1);
@@ -1028,8 +1058,8 @@ __global__ void __launch_bounds__(ring_threads<FUSED>(), 2) conv32_ring_kernel(c
                 float v[16];
                 const uint32_t ta = tmem + (uint32_t)(a * kCh + 16 * half) + ((uint32_t)(quad * 32) << 16);
                 tc::tmem_ld16(ta, v);
-                // the block's next row accumulates onto zeros
-                tc::tmem_st16_zero(ta);
+                // the block's next row accumulates onto the bias
+                tc::tmem_st16(ta, bias);
                 tc::tmem_wait_st();
                 tc::fence_before_sync();
                 __syncwarp();
@@ -1063,8 +1093,6 @@ __global__ void __launch_bounds__(ring_threads<FUSED>(), 2) conv32_ring_kernel(c
                         }
                     }
                 } else {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] += sBias[16 * half + i];
                     if (p.z_out) {
                         float4 *zo = reinterpret_cast<float4 *>(p.z_out + q * kCh + 16 * half);
 #pragma unroll
@@ -2217,11 +2245,11 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
             p.withhold = withhold && l == 0;
             const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.units, 2 * info.sm_count));
             if (fused)
-                conv32_ring_kernel<false, false, true><<<grid, ring_threads<true>(), RingLayout<false>::bytes, s>>>(p);
+                conv32_ring_kernel<false, false, true><<<grid, ring_threads<false, true>(), RingLayout<false>::bytes, s>>>(p);
             else if (l == 0)
                 conv32_ring_kernel<false, false, false><<<grid, kRingThreads, RingLayout<false>::bytes, s>>>(p);
             else
-                conv32_ring_kernel<true, false, false><<<grid, kRingThreads, RingLayout<true>::bytes, s>>>(p);
+                conv32_ring_kernel<true, false, false><<<grid, ring_threads<true, false>(), RingLayout<true>::bytes, s>>>(p);
         }
     } else {
         cudaFuncSetAttribute(conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
