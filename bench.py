@@ -300,6 +300,23 @@ def time_sweeps(ising, torch, lat, beta, seed, steps, warmup, trace, stream, per
     return total, black, white
 
 
+def sweep_config(args, world):
+    """The `config` of the single-lattice line (one lattice per rank)."""
+    L, plane_bytes = args.L, args.L * args.L // 4
+    return {"workload": f"msc4 L={L} {args.init} start seed {args.seed}+rank beta={args.beta}, 1 sweep per step",
+            "L": L, "layout": "msc4", "beta": args.beta, "spins": L * L, "plane_bytes": plane_bytes,
+            "l2": f"inputs larger than L2 (two planes of {plane_bytes / 1e9:.2f} GB each), no flush",
+            "parallelism": f"replicas{world}"}
+
+
+def slab_config(args, world, seed):
+    """The `config` of the slab line (one lattice cut into horizontal slabs)."""
+    return {"workload": f"msc4 L={args.L} random start seed {seed} beta={args.beta} as "
+                        f"{args.slabs if world == 1 else world} horizontal slabs with halo rows",
+            "L": args.L, "layout": "msc4", "beta": args.beta, "parallelism": f"slabs{world}",
+            "l2": "inputs larger than L2, no flush"}
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -340,10 +357,7 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "impl": "ours",
-        "config": {"workload": f"msc4 L={L} {args.init} start seed {args.seed}+rank beta={beta}, 1 sweep per step",
-                   "L": L, "layout": "msc4", "beta": beta, "spins": n_sites,
-                   "plane_bytes": plane_bytes, "l2": "inputs larger than L2 (two planes of "
-                   f"{plane_bytes / 1e9:.2f} GB each), no flush", "parallelism": f"replicas{world}"},
+        "config": sweep_config(args, world),
         "gpu_launches": 2 * args.steps,
         "kernel_ms": {"black_mean": round(statistics.mean(black), 4), "white_mean": round(statistics.mean(white), 4),
                       "min": round(min(black + white), 4)},
@@ -539,10 +553,7 @@ def run_slabs(args, world, rank, local):
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "ours",
-        "config": {"workload": f"msc4 L={L} random start seed {seed} beta={beta} as "
-                               f"{args.slabs if world == 1 else world} horizontal slabs with halo rows",
-                   "L": L, "layout": "msc4", "beta": beta, "parallelism": f"slabs{world}",
-                   "l2": "inputs larger than L2, no flush"},
+        "config": slab_config(args, world, seed),
         "gpu_launches": launches * args.steps,
         "clocks": clk.summary(),
     }
@@ -1036,8 +1047,8 @@ def run_reference(args, world, rank):
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic", "impl": "reference",
-        "config": {"workload": f"msc4 L={args.L} random start seed {args.seed}+rank beta={args.beta}, "
-                               "1 sweep per step", "L": args.L, "beta": args.beta, "sample_L": L},
+        # the workload our arm runs at this world size; each step here is a bounded sample of it
+        "config": sweep_config(args, world) if world == 1 else slab_config(args, world, args.seed),
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
