@@ -434,7 +434,13 @@ ISING_API int ising_net_wait_selftest(int64_t L, int64_t C, const void *black_de
                                      ising_stream_t stream);
 
 /* grad_dev = d(sum dlogits * logits)/d(params) for the last training forward
- * on the same chains and parameters (straight-through the bfloat16 rounding). */
+ * on the same chains and parameters (straight-through the bfloat16 rounding).
+ * For L a multiple of 128 the data and weight gradients of the 32 -> 32
+ * layers run on the tensor cores (the weight gradients see the output
+ * gradient as two bfloat16 parts, its rounding and the rounding of the
+ * remainder, which carry it to about 2^-17); a bounded wait that gives up there
+ * is reported by the next ising_net_check.  Every weight gradient is a sum of
+ * per-CTA partials in a fixed order: the result is deterministic. */
 ISING_API int ising_net_backward(int64_t L, int64_t C, const void *black_dev, const void *white_dev,
                                  const float *params_dev, const float *dlogits_dev, float *grad_dev, void *work_dev,
                                  size_t work_bytes, ising_stream_t stream);
