@@ -254,6 +254,11 @@ __device__ void march_rows(const BatchParams &p, const BatchGroup &G, int64_t c0
     DrawCtx dc{(uint32_t)t, counter_word3(colour, kPurposeMetropolis, t), 0u, 0u, 0u};
     const uint64_t *src = src_all;
     uint64_t *tgt = tgt_all;
+    // row addresses carried from row to row (no multiply per row): the target
+    // row r and the source row (r + 2) mod L; q = r L/8 + 8 j
+    const uint64_t *src2 = src_all;
+    uint64_t *tgt_r = tgt_all;
+    uint32_t q = 0;
     int64_t lat = 0;
     uint32_t stream = 0, ones = 0, dsum = 0, nrows = 0;
     // lattice li from row r on, for step s: its stream and thresholds, and
@@ -262,6 +267,9 @@ __device__ void march_rows(const BatchParams &p, const BatchGroup &G, int64_t c0
         lat = G.first + li;
         src = src_all + li * lat_words;
         tgt = tgt_all + li * lat_words;
+        tgt_r = tgt + (int64_t)r * wpr;
+        src2 = src + (int64_t)(r + 2 >= L ? r + 2 - L : r + 2) * wpr;
+        q = (uint32_t)r * qrow + qlane;
         const int slot = p.slot_of[lat];
         dc.T3 = p.thr[2 * slot];
         dc.T4 = p.thr[2 * slot + 1];
@@ -279,9 +287,8 @@ __device__ void march_rows(const BatchParams &p, const BatchGroup &G, int64_t c0
         // rows two ahead (source) and one ahead (target) of the same lattice;
         // none after its last row, where the next step enters a new lattice
         const bool ahead = more && !last_row;
-        const int r2 = r + 2 >= L ? r + 2 - L : r + 2;
-        cp16_if(&ring.src[(s + 2) & 3][lane], src + (int64_t)r2 * wpr, ahead);
-        cp16_if(&ring.tgt[(s + 1) & 1][lane], tgt + (int64_t)(r + 1) * wpr, ahead);
+        cp16_if(&ring.src[(s + 2) & 3][lane], src2, ahead);
+        cp16_if(&ring.tgt[(s + 1) & 1][lane], tgt_r + wpr, ahead);
         cp_commit();
         cp_wait_all_but_last();
         const uint4 up = ring.src[(s + 3) & 3][lane];
@@ -302,14 +309,13 @@ __device__ void march_rows(const BatchParams &p, const BatchGroup &G, int64_t c0
             sd.z = __funnelshift_r(cur.z, cur.w, 4);
             sd.w = __funnelshift_r(cur.w, next, 4);
         }
-        const uint32_t q = (uint32_t)r * qrow + qlane;
         uint32_t dacc = 0;
         uint4 ns;
         ns.x = update_half<OBS, false>(tg.x, up.x + dn.x + cur.x, sd.x, q, stream, dc, p.rk, dacc);
         ns.y = update_half<OBS, false>(tg.y, up.y + dn.y + cur.y, sd.y, q | 2, stream, dc, p.rk, dacc);
         ns.z = update_half<OBS, false>(tg.z, up.z + dn.z + cur.z, sd.z, q | 4, stream, dc, p.rk, dacc);
         ns.w = update_half<OBS, false>(tg.w, up.w + dn.w + cur.w, sd.w, q | 6, stream, dc, p.rk, dacc);
-        *reinterpret_cast<uint4 *>(tgt + (int64_t)r * wpr) = ns;
+        *reinterpret_cast<uint4 *>(tgt_r) = ns;
         if (OBS) {
             const uint32_t n8 = ns.x + ns.y + ns.z + ns.w + cur.x + cur.y + cur.z + cur.w;
             const uint32_t sb = (n8 & 0x0F0F0F0Fu) + ((n8 >> 4) & 0x0F0F0F0Fu);
@@ -318,6 +324,9 @@ __device__ void march_rows(const BatchParams &p, const BatchGroup &G, int64_t c0
             nrows += 1;
         }
         ++r;
+        tgt_r += wpr;
+        q += qrow;
+        src2 = r + 2 == L ? src : src2 + wpr;
         if (last_row) {
             march_flush<OBS>(p, lat, gmask, lpr, j, ones, dsum, nrows);
             ++li;
