@@ -1321,158 +1321,223 @@ __global__ void __launch_bounds__(kThreads) conv32_bwd_data_kernel(int L, int64_
     }
 }
 
-// Weight gradients as per-CTA partial sums (fixed order).  The pixels are cut
-// into tiles of 8 rows x 32 columns of one chain; CTA j handles tiles j,
-// j + gridDim.x, ... in order.  A tile's output gradients dz (and the layer's
-// input a, with a one-pixel halo) are staged in shared memory; thread (oq, iq)
-// of 16 x 16 accumulates the 2 x 2 (output, input) channel pairs 2 oq + {0, 1}
-// x 2 iq + {0, 1} for all 9 taps, and threads with iq = 0 the bias sums.
-// partial[cta][e]: e = (o * CIN + i) * 9 + k for weights, then the biases.
+// Weight gradients of a 32 -> 32 layer on the CUDA cores (L not a multiple of
+// 128; wgrad_tc_kernel below serves the others), as per-CTA partial sums
+// (fixed order).  The pixels are cut into tiles of 8 rows x 32 columns of one
+// chain; CTA j handles tiles j, j + gridDim.x, ... in order.  A tile's output
+// gradients dz (and the layer's input a, with a one-pixel halo) are staged in
+// shared memory; thread (oq, iq) of 16 x 16 accumulates the 2 x 2 (output,
+// input) channel pairs 2 oq + {0, 1} x 2 iq + {0, 1} for all 9 taps, and
+// threads with iq = 0 the bias sums.  partial[cta][e]: e = (o * 32 + i) * 9 + k
+// for weights, then the biases.
 constexpr int kTy = 8, kTx = 32;
 
-template <int CIN, int COUT>
-__device__ __forceinline__ void wgrad_stage(const Chains &ch, const __nv_bfloat16 *a_prev, const float *dz,
-                                            const float *dlogits, int64_t c, int y0, int x0, float *sa, float *sd)
+__device__ __forceinline__ void wgrad_stage(const Chains &ch, const __nv_bfloat16 *a_prev, const float *dz, int64_t c,
+                                            int y0, int x0, float *sa, float *sd)
 {
-    const int L = ch.L, nb1 = L / kBlk;
-    // input tile with halo: (kTy + 2) x (kTx + 2) pixels x CIN channels; 32
-    // channels come as four 16-byte loads of 8 bfloat16 per pixel
-    if constexpr (CIN == kCh) {
-        constexpr int kOct = CIN / 8;
-        for (int e = threadIdx.x; e < (kTy + 2) * (kTx + 2) * kOct; e += blockDim.x) {
-            const int pix = e / kOct, q = e - pix * kOct;
-            const int ty = pix / (kTx + 2), tx = pix - ty * (kTx + 2);
-            int y = y0 + ty - 1, x = x0 + tx - 1;
-            y = y < 0 ? y + L : (y >= L ? y - L : y);
-            x = x < 0 ? x + L : (x >= L ? x - L : x);
-            const uint4 v = *reinterpret_cast<const uint4 *>(a_prev + apix(L, c, y, x) * CIN + 8 * q);
-            float4 *dst = reinterpret_cast<float4 *>(sa + pix * CIN + 8 * q);
-            dst[0] = make_float4(bf16_lo(v.x), bf16_hi(v.x), bf16_lo(v.y), bf16_hi(v.y));
-            dst[1] = make_float4(bf16_lo(v.z), bf16_hi(v.z), bf16_lo(v.w), bf16_hi(v.w));
-        }
-    } else {
-        for (int e = threadIdx.x; e < (kTy + 2) * (kTx + 2); e += blockDim.x) {
-            const int ty = e / (kTx + 2), tx = e - ty * (kTx + 2);
-            int y = y0 + ty - 1, x = x0 + tx - 1;
-            y = y < 0 ? y + L : (y >= L ? y - L : y);
-            x = x < 0 ? x + L : (x >= L ? x - L : x);
-            sa[e] = spin_at(ch, c, y, x, -1);
-        }
+    const int L = ch.L;
+    // input tile with halo: (kTy + 2) x (kTx + 2) pixels x 32 channels, as four
+    // 16-byte loads of 8 bfloat16 per pixel
+    constexpr int kOct = kCh / 8;
+    for (int e = threadIdx.x; e < (kTy + 2) * (kTx + 2) * kOct; e += blockDim.x) {
+        const int pix = e / kOct, q = e - pix * kOct;
+        const int ty = pix / (kTx + 2), tx = pix - ty * (kTx + 2);
+        int y = y0 + ty - 1, x = x0 + tx - 1;
+        y = y < 0 ? y + L : (y >= L ? y - L : y);
+        x = x < 0 ? x + L : (x >= L ? x - L : x);
+        const uint4 v = *reinterpret_cast<const uint4 *>(a_prev + apix(L, c, y, x) * kCh + 8 * q);
+        float4 *dst = reinterpret_cast<float4 *>(sa + pix * kCh + 8 * q);
+        dst[0] = make_float4(bf16_lo(v.x), bf16_hi(v.x), bf16_lo(v.y), bf16_hi(v.y));
+        dst[1] = make_float4(bf16_lo(v.z), bf16_hi(v.z), bf16_lo(v.w), bf16_hi(v.w));
     }
     // output gradients of the tile: a tile row of 32 pixels x 32 channels is
     // contiguous, loaded as float4
-    if constexpr (COUT == kCh) {
-        for (int e = threadIdx.x; e < kTy * kTx * COUT / 4; e += blockDim.x) {
-            const int row = e / (kTx * COUT / 4), v = e - row * (kTx * COUT / 4);
-            const float4 *src = reinterpret_cast<const float4 *>(dz + ((c * L + y0 + row) * (int64_t)L + x0) * COUT);
-            reinterpret_cast<float4 *>(sd)[e] = src[v];
-        }
-    } else {
-        for (int e = threadIdx.x; e < kTy * kTx; e += blockDim.x) {
-            const int y = y0 + e / kTx, x = x0 + e % kTx;
-            sd[e] = dlogits[c * nb1 * nb1 + (y / kBlk) * nb1 + x / kBlk] * (1.0f / (kBlk * kBlk));
-        }
+    for (int e = threadIdx.x; e < kTy * kTx * kCh / 4; e += blockDim.x) {
+        const int row = e / (kTx * kCh / 4), v = e - row * (kTx * kCh / 4);
+        const float4 *src = reinterpret_cast<const float4 *>(dz + ((c * L + y0 + row) * (int64_t)L + x0) * kCh);
+        reinterpret_cast<float4 *>(sd)[e] = src[v];
     }
 }
 
-// N (1 or 2) consecutive floats of shared memory; a pair is one 8-byte load
-// (the address is even).
-template <int N>
-__device__ __forceinline__ void load_pair(const float *p, float (&v)[N])
-{
-    if constexpr (N == 2) {
-        const float2 t = *reinterpret_cast<const float2 *>(p);
-        v[0] = t.x;
-        v[1] = t.y;
-    } else {
-        v[0] = p[0];
-    }
-}
-
-template <int CIN, int COUT>
 __global__ void __launch_bounds__(256) wgrad_kernel(Chains ch, int64_t C, const __nv_bfloat16 *a_prev, const float *dz,
-                                                    const float *dlogits, float *partial)
+                                                    float *partial)
 {
     extern __shared__ float smem[];
-    float *sa = smem;                                 // (kTy+2) (kTx+2) CIN
-    float *sd = smem + (kTy + 2) * (kTx + 2) * CIN;   // kTy kTx COUT
-    constexpr int NE = COUT * CIN * 9 + COUT;
+    float *sa = smem;                                 // (kTy+2) (kTx+2) 32
+    float *sd = smem + (kTy + 2) * (kTx + 2) * kCh;   // kTy kTx 32
+    constexpr int NE = kN2 + kCh;
     const int L = ch.L;
     const int tiles_x = L / kTx, tiles_y = L / kTy;
     const int64_t n_tiles = C * tiles_x * tiles_y;
-    // thread roles: oq, iq in 0..15 cover output / input channel pairs; for
-    // CIN == 1 or COUT == 1 the unused index collapses
-    constexpr int OQ = COUT == 1 ? 1 : COUT / 2, IQ = CIN == 1 ? 1 : CIN / 2;
-    constexpr int OPT = COUT == 1 ? 1 : 2, IPT = CIN == 1 ? 1 : 2;
-    const int role = threadIdx.x;
-    const bool active = role < OQ * IQ;
-    const int oq = active ? role / IQ : 0, iq = active ? role - (role / IQ) * IQ : 0;
-    float acc[OPT][IPT][9];
-    float bacc[OPT];
+    const int oq = threadIdx.x >> 4, iq = threadIdx.x & 15;  // channel pairs 2 oq, 2 oq + 1 and 2 iq, 2 iq + 1
+    float acc[2][2][9];
+    float bacc[2] = {0.0f, 0.0f};
 #pragma unroll
-    for (int a = 0; a < OPT; ++a) {
-        bacc[a] = 0.0f;
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int b = 0; b < IPT; ++b)
+        for (int b = 0; b < 2; ++b)
 #pragma unroll
             for (int k = 0; k < 9; ++k) acc[a][b][k] = 0.0f;
-    }
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t c = tile / (tiles_x * tiles_y);
         const int rem = (int)(tile - c * tiles_x * tiles_y);
         const int y0 = (rem / tiles_x) * kTy, x0 = (rem % tiles_x) * kTx;
         __syncthreads();
-        wgrad_stage<CIN, COUT>(ch, a_prev, dz, dlogits, c, y0, x0, sa, sd);
+        wgrad_stage(ch, a_prev, dz, c, y0, x0, sa, sd);
         __syncthreads();
-        if (active) {
-            // pixels in row order; along a tile row the 3 x 3 input window
-            // slides in registers, so each pixel loads one new column per dy
-            // (channel pairs as float2 where there are two)
-            for (int ty = 0; ty < kTy; ++ty) {
-                float win[3][3][IPT];  // [dy][dx][input channel]
+        // pixels in row order; along a tile row the 3 x 3 input window slides
+        // in registers, so each pixel loads one new column per dy (channel
+        // pairs as float2)
+        for (int ty = 0; ty < kTy; ++ty) {
+            float2 win[3][3];  // [dy][dx], input channels 2 iq, 2 iq + 1
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx)
+                    win[dy][dx] = *reinterpret_cast<const float2 *>(sa + ((ty + dy) * (kTx + 2) + dx) * kCh + 2 * iq);
+#pragma unroll
+            for (int tx = 0; tx < kTx; ++tx) {
 #pragma unroll
                 for (int dy = 0; dy < 3; ++dy)
+                    win[dy][2] = *reinterpret_cast<const float2 *>(sa + ((ty + dy) * (kTx + 2) + tx + 2) * kCh + 2 * iq);
+                const float2 g2 = *reinterpret_cast<const float2 *>(sd + (ty * kTx + tx) * kCh + 2 * oq);
+                const float g[2] = {g2.x, g2.y};
 #pragma unroll
-                    for (int dx = 0; dx < 2; ++dx) load_pair<IPT>(sa + ((ty + dy) * (kTx + 2) + dx) * CIN + IPT * iq,
-                                                              win[dy][dx]);
+                for (int a = 0; a < 2; ++a) bacc[a] += g[a];
 #pragma unroll
-                for (int tx = 0; tx < kTx; ++tx) {
+                for (int k = 0; k < 9; ++k) {
+                    const float2 wv = win[k / 3][k % 3];
 #pragma unroll
-                    for (int dy = 0; dy < 3; ++dy)
-                        load_pair<IPT>(sa + ((ty + dy) * (kTx + 2) + tx + 2) * CIN + IPT * iq, win[dy][2]);
-                    float g[OPT];
-                    load_pair<OPT>(sd + (ty * kTx + tx) * COUT + OPT * oq, g);
+                    for (int a = 0; a < 2; ++a) {
+                        acc[a][0][k] = fmaf(g[a], wv.x, acc[a][0][k]);
+                        acc[a][1][k] = fmaf(g[a], wv.y, acc[a][1][k]);
+                    }
+                }
 #pragma unroll
-                    for (int a = 0; a < OPT; ++a) bacc[a] += g[a];
-#pragma unroll
-                    for (int k = 0; k < 9; ++k)
-#pragma unroll
-                        for (int b = 0; b < IPT; ++b)
-#pragma unroll
-                            for (int a = 0; a < OPT; ++a)
-                                acc[a][b][k] = fmaf(g[a], win[k / 3][k % 3][b], acc[a][b][k]);
-#pragma unroll
-                    for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                        for (int b = 0; b < IPT; ++b) {
-                            win[dy][0][b] = win[dy][1][b];
-                            win[dy][1][b] = win[dy][2][b];
-                        }
+                for (int dy = 0; dy < 3; ++dy) {
+                    win[dy][0] = win[dy][1];
+                    win[dy][1] = win[dy][2];
                 }
             }
         }
     }
-    if (active) {
-        float *out = partial + (int64_t)blockIdx.x * NE;
+    float *out = partial + (int64_t)blockIdx.x * NE;
 #pragma unroll
-        for (int a = 0; a < OPT; ++a)
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
-            for (int b = 0; b < IPT; ++b)
+        for (int b = 0; b < 2; ++b)
 #pragma unroll
-                for (int k = 0; k < 9; ++k) out[((OPT * oq + a) * CIN + IPT * iq + b) * 9 + k] = acc[a][b][k];
-        if (iq == 0)
+            for (int k = 0; k < 9; ++k) out[((2 * oq + a) * kCh + 2 * iq + b) * 9 + k] = acc[a][b][k];
+    if (iq == 0)
 #pragma unroll
-            for (int a = 0; a < OPT; ++a) out[COUT * CIN * 9 + OPT * oq + a] = bacc[a];
+        for (int a = 0; a < 2; ++a) out[kN2 + 2 * oq + a] = bacc[a];
+}
+
+// Weight gradients of the layers with one input or one output channel, warp
+// per run of rows, lane per channel:
+//   layer 1 (spins -> 32): dW1[o][k] = sum_p dz1(p)[o] s(p + off_k),
+//                          db1[o] = sum_p dz1(p)[o]                (lane o);
+//   layer 4 (32 -> 1):     dW4[i][k] = sum_q a3(q)[i] d4(q - off_k),
+//                          db4 = sum_p d4(p), d4(p) = dlogit(block of p) / 64
+//                                                                 (lane i).
+// Per pixel q the lane's value v (dz1(q)[o] or a3(q)[i]) multiplies a 3 x 3
+// window of a field that is the same for all lanes (the spins, or d4).  A
+// warp walks its rows in order, each in chunks of 32 pixels: lane j holds the
+// field at column x0 + j of rows y - 1, y, y + 1, the halo columns are loaded
+// by every lane, and the window slides along the chunk by one shuffle per row
+// and pixel.  Per pixel and lane: one load, three shuffles, nine FMAs.  The
+// CTA's warps are added in warp order and written as the CTA's partial sums
+// (layout of wgrad_kernel), summed by reduce_partials_kernel.  (wgrad_kernel
+// gives these layers 16 busy threads per CTA.)
+constexpr int kThinWarps = 8;
+
+template <bool L4>
+__device__ __forceinline__ float thin_field(const Chains &ch, const float *dlogits, int64_t c, int y, int x)
+{
+    const int L = ch.L;
+    y = wrap(y, L);
+    x = wrap(x, L);
+    if constexpr (L4) {
+        const int nb1 = L / kBlk;
+        return dlogits[c * nb1 * nb1 + (y / kBlk) * nb1 + x / kBlk] * (1.0f / (kBlk * kBlk));
+    } else {
+        return spin_at(ch, c, y, x, -1);
+    }
+}
+
+template <bool L4>
+__global__ void __launch_bounds__(32 * kThinWarps, 2) wgrad_thin_kernel(Chains ch, int64_t C, const float *dz1,
+                                                                      const __nv_bfloat16 *a3, const float *dlogits,
+                                                                      float *partial)
+{
+    constexpr int NE = L4 ? kN1 + 1 : kN1 + kCh;
+    __shared__ float red[kThinWarps][32][10];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int L = ch.L;
+    const int64_t rows = C * L;
+    const int64_t nw = (int64_t)gridDim.x * kThinWarps, gw = (int64_t)blockIdx.x * kThinWarps + warp;
+    const int64_t r0 = gw * rows / nw, r1 = (gw + 1) * rows / nw;
+    float acc[9], bacc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
+    for (int64_t gr = r0; gr < r1; ++gr) {
+        const int64_t c = gr / L;
+        const int y = (int)(gr - c * L);
+        for (int x0 = 0; x0 < L; x0 += 32) {
+            float f[3], hl[3], hr[3], w[3][3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                f[d] = thin_field<L4>(ch, dlogits, c, y - 1 + d, x0 + lane);
+                hl[d] = thin_field<L4>(ch, dlogits, c, y - 1 + d, x0 - 1);
+                hr[d] = thin_field<L4>(ch, dlogits, c, y - 1 + d, x0 + 32);
+                w[d][0] = hl[d];
+                w[d][1] = __shfl_sync(0xffffffffu, f[d], 0);
+                w[d][2] = __shfl_sync(0xffffffffu, f[d], 1);
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                float v;
+                if constexpr (L4) {
+                    v = __bfloat162float(a3[apix(L, c, y, x0 + j) * kCh + lane]);
+                    bacc += w[1][1];  // d4 of the pixel itself
+                } else {
+                    v = dz1[((c * L + y) * (int64_t)L + x0 + j) * kCh + lane];
+                    bacc += v;
+                }
+                // window entry (d, e) is the field at (y - 1 + d, x + e - 1): tap
+                // 3 d + e of layer 1 (p + off_k), tap 8 - 3 d - e of layer 4 (q - off_k)
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        const int k = L4 ? 8 - 3 * d - e : 3 * d + e;
+                        acc[k] = fmaf(v, w[d][e], acc[k]);
+                    }
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    w[d][0] = w[d][1];
+                    w[d][1] = w[d][2];
+                    w[d][2] = j + 2 < 32 ? __shfl_sync(0xffffffffu, f[d], (j + 2) & 31) : hr[d];
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) red[warp][lane][k] = acc[k];
+    red[warp][lane][9] = bacc;
+    __syncthreads();
+    float *out = partial + (int64_t)blockIdx.x * NE;
+    for (int t = threadIdx.x; t < 32 * 10; t += blockDim.x) {
+        const int l = t / 10, k = t - 10 * l;
+        float sum = 0.0f;
+#pragma unroll
+        for (int q = 0; q < kThinWarps; ++q) sum += red[q][l][k];
+        if (k < 9)
+            out[l * 9 + k] = sum;  // layer 1: (o, k); layer 4: (i, k)
+        else if (!L4)
+            out[kN1 + l] = sum;    // db1[o]
+        else if (l == 0)
+            out[kN1] = sum;        // db4 (every lane summed the same d4)
     }
 }
 
@@ -2395,18 +2460,18 @@ ISING_API int ising_net_backward(int64_t L, int64_t C, const void *black_dev, co
     const unsigned gw = (unsigned)w.n_cta;
     cudaFuncSetAttribute(conv32_bwd_data_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const size_t sm32 = (size_t)((kTy + 2) * (kTx + 2) * kCh + kTy * kTx * kCh) * sizeof(float);
-    const size_t sm4 = (size_t)((kTy + 2) * (kTx + 2) * kCh + kTy * kTx) * sizeof(float);
-    const size_t sm1 = (size_t)((kTy + 2) * (kTx + 2) + kTy * kTx * kCh) * sizeof(float);
-    cudaFuncSetAttribute(wgrad_kernel<kCh, kCh>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm32);
-    cudaFuncSetAttribute(wgrad_kernel<kCh, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
-    cudaFuncSetAttribute(wgrad_kernel<1, kCh>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm32);
     auto reduce = [&](int ne, int nw, int w_off, int b_off, int64_t n_cta) {
         reduce_partials_kernel<<<(unsigned)((ne + 31) / 32), 32 * kReduceWarps, 0, s>>>(w.partial, n_cta, ne, nw,
                                                                                        grad_dev, w_off, b_off);
     };
     // layer 4
-    wgrad_kernel<kCh, 1><<<gw, 256, sm4, s>>>(ch, C, w.a3, nullptr, dlogits_dev, w.partial);
-    reduce(kN1 + 1, kN1, kOffW4, kOffB4, w.n_cta);
+    // the thin weight gradients: one wave of two CTAs per SM
+    DeviceInfo info{152};
+    device_info(&info);
+    const int64_t n_thin = std::min<int64_t>(w.n_cta, 2 * (int64_t)info.sm_count);
+    wgrad_thin_kernel<true><<<(unsigned)n_thin, 32 * kThinWarps, 0, s>>>(ch, C, nullptr, w.a3, dlogits_dev, w.partial);
+    reduce(kN1 + 1, kN1, kOffW4, kOffB4, n_thin);
     // for L a multiple of 128 the data and weight gradients of the 32 -> 32
     // layers run on the tensor cores; their gradients are then also kept as
     // bfloat16 parts (gb: the rounding, gr: the rounding of the remainder)
@@ -2423,7 +2488,7 @@ ISING_API int ising_net_backward(int64_t L, int64_t C, const void *black_dev, co
         rc = launch_ring_bwd((int)L, C, params_dev, kOffW3, w.gb1, w.z2, w.db, w.gb2, w.gr2, s);  // dz2
         if (rc) return rc;
     } else {
-        wgrad_kernel<kCh, kCh><<<gw, 256, sm32, s>>>(ch, C, w.a2, w.da, nullptr, w.partial);
+        wgrad_kernel<<<gw, 256, sm32, s>>>(ch, C, w.a2, w.da, w.partial);
         reduce(kN2 + kCh, kN2, kOffW3, kOffB3, w.n_cta);
         conv32_bwd_data_kernel<<<g, kThreads, smem, s>>>((int)L, C, params_dev, kOffW3, w.da, w.z2, w.db);  // dz2
     }
@@ -2435,13 +2500,13 @@ ISING_API int ising_net_backward(int64_t L, int64_t C, const void *black_dev, co
         rc = launch_ring_bwd((int)L, C, params_dev, kOffW2, w.gb2, w.z1, w.da, nullptr, nullptr, s);  // dz1
         if (rc) return rc;
     } else {
-        wgrad_kernel<kCh, kCh><<<gw, 256, sm32, s>>>(ch, C, w.a1, w.db, nullptr, w.partial);
+        wgrad_kernel<<<gw, 256, sm32, s>>>(ch, C, w.a1, w.db, w.partial);
         reduce(kN2 + kCh, kN2, kOffW2, kOffB2, w.n_cta);
         conv32_bwd_data_kernel<<<g, kThreads, smem, s>>>((int)L, C, params_dev, kOffW2, w.db, w.z1, w.da);  // dz1
     }
     // layer 1
-    wgrad_kernel<1, kCh><<<gw, 256, sm1, s>>>(ch, C, nullptr, w.da, nullptr, w.partial);
-    reduce(kN1 + kCh, kN1, kOffW1, kOffB1, w.n_cta);
+    wgrad_thin_kernel<false><<<(unsigned)n_thin, 32 * kThinWarps, 0, s>>>(ch, C, w.da, nullptr, nullptr, w.partial);
+    reduce(kN1 + kCh, kN1, kOffW1, kOffB1, n_thin);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ISING_OK : nfail(ISING_ECUDA, cudaGetErrorString(e));
 }
