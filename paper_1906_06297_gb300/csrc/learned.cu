@@ -1586,13 +1586,15 @@ __global__ void __launch_bounds__(32 * kReduceWarps) reduce_partials_kernel(cons
 // about 2^-17 and the FP32 accumulation sees the unrounded gradient to that
 // accuracy (dW = D[.][o] + D[.][32 + o]).
 // Both operands are MN-major and come straight from the NHWC buffers: a
-// plane of 128 pixels x 16 bytes (8 channels) is the core-matrix form with
-// K rows of 16 bytes, LBO = 128 bytes along K, SBO = 2048 bytes between the
-// planes of 8-channel groups.  A staged input row is 12 tensor copies
-// (dx, channel group) of the row starting at pixel x0 - 1 + dx; the unused M
-// rows 96..127 read the 8 KB after it (the next slot, or the first gradient
-// slot after the last one), whose products land in TMEM lanes no one reads.
-// A staged gradient row holds 8 planes (h, channel group).
+// tensor copy of 128 whole pixels (32 channels, 64 bytes each) with the
+// 64-byte swizzle is the MN-major 64-byte-swizzled operand form: 8 K rows
+// (pixels) of 64 bytes per 512-byte atom, SBO = 512 bytes between the 8-row
+// groups along K, LBO = 8 KB between the 32-channel groups along M (or N).
+// So every sector a copy fetches is used whole.  A staged input row is three
+// such copies, of the row starting at pixels x0 - 1 + dx; the unused M rows
+// 96..127 read the 8 KB after it (the next slot, or the first gradient slot
+// after the last one), whose products land in TMEM lanes no one reads.  A
+// staged gradient row is two copies (hi, lo).
 // Work: the (chain, segment, row) lines of all chains are cut into one
 // contiguous range per CTA (ranges differ by at most one row); a range is
 // walked as runs of consecutive rows of one (chain, segment), each staging
@@ -1609,9 +1611,9 @@ __global__ void __launch_bounds__(32 * kReduceWarps) reduce_partials_kernel(cons
 constexpr int kWgActSlots = 6;                      // staged input rows (3 in use, 3 ahead)
 constexpr int kWgDzSlots = 4;                       // staged gradient rows (1 in use, 3 ahead)
 constexpr int kWgBiasWarps = 4;
-constexpr uint32_t kWgPlane = kTileM * 16;          // 128 pixels x 8 channels, bfloat16
-constexpr uint32_t kWgActBytes = 12 * kWgPlane;     // (dx, channel group)
-constexpr uint32_t kWgDzBytes = 8 * kWgPlane;       // hi and lo, 4 channel groups each
+constexpr uint32_t kWgBox = kTileM * kCh * 2;      // 128 pixels x 32 channels, bfloat16, 64-byte swizzled
+constexpr uint32_t kWgActBytes = 3 * kWgBox;        // dx = 0, 1, 2
+constexpr uint32_t kWgDzBytes = 2 * kWgBox;         // hi, lo
 constexpr uint32_t kWgDz0 = kWgActSlots * kWgActBytes;
 constexpr uint32_t kWgBias = kWgDz0 + kWgDzSlots * kWgDzBytes;   // per bias warp 32 sums
 constexpr uint32_t kWgBar = kWgBias + kWgBiasWarps * kCh * 4;
@@ -1619,7 +1621,8 @@ constexpr uint32_t kWgSmem = kWgBar + (2 * kWgActSlots + 2 * kWgDzSlots + 1) * 8
 constexpr int kWgThreads = 64 + 32 * kWgBiasWarps;
 constexpr int kWgN = 2 * kCh;                       // columns per accumulator (hi, lo)
 constexpr uint32_t kWgTmemCols = 256;               // 3 x 64 used
-static_assert(kWgDz0 >= kWgActBytes + 4 * kWgPlane && kWgSmem <= 227 * 1024,
+static_assert(kWgDz0 >= kWgActBytes + kWgBox && kWgSmem <= 227 * 1024 && kWgActBytes % 1024 == 0 &&
+                  kWgDz0 % 1024 == 0,
               "the unused M rows of the last input slot read the gradient slots; one CTA per SM");
 
 struct WgradTc {
@@ -1686,11 +1689,7 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_co
                 tc::mbar_arrive_expect_tx(&afull[s], kWgActBytes);
                 uint8_t *dst = wg_smem + s * kWgActBytes;
 #pragma unroll
-                for (int dx = 0; dx < 3; ++dx)
-#pragma unroll
-                    for (int g = 0; g < kGroups; ++g)
-                        tc::tma_load_4d(dst + (dx * kGroups + g) * kWgPlane, &p.act, 8 * g, w.x0 + dx, y, (int)w.c,
-                                        &afull[s]);
+                for (int dx = 0; dx < 3; ++dx) tc::tma_load_4d(dst + dx * kWgBox, &p.act, 0, w.x0 + dx, y, (int)w.c, &afull[s]);
                 ++na;
                 return true;
             };
@@ -1700,11 +1699,8 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_co
                     return false;
                 tc::mbar_arrive_expect_tx(&dfull[s], kWgDzBytes);
                 uint8_t *dst = wg_smem + kWgDz0 + s * kWgDzBytes;
-#pragma unroll
-                for (int g = 0; g < kGroups; ++g) {
-                    tc::tma_load_4d(dst + g * kWgPlane, &p.hi, 8 * g, w.x0 + 1, r, (int)w.c, &dfull[s]);
-                    tc::tma_load_4d(dst + (kGroups + g) * kWgPlane, &p.lo, 8 * g, w.x0 + 1, r, (int)w.c, &dfull[s]);
-                }
+                tc::tma_load_4d(dst, &p.hi, 0, w.x0 + 1, r, (int)w.c, &dfull[s]);
+                tc::tma_load_4d(dst + kWgBox, &p.lo, 0, w.x0 + 1, r, (int)w.c, &dfull[s]);
                 ++nd;
                 return true;
             };
@@ -1726,8 +1722,8 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_co
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_bf16_f32_mn(kTileM, kWgN);
-            const uint64_t a_desc0 = tc::smem_desc(tc::smem_u32(wg_smem), 128, kWgPlane);
-            const uint64_t b_desc0 = tc::smem_desc(tc::smem_u32(wg_smem + kWgDz0), 128, kWgPlane);
+            const uint64_t a_desc0 = tc::smem_desc_sw64(tc::smem_u32(wg_smem), kWgBox, 512);
+            const uint64_t b_desc0 = tc::smem_desc_sw64(tc::smem_u32(wg_smem + kWgDz0), kWgBox, 512);
             const uint32_t a_lo0 = (uint32_t)a_desc0, a_hi = (uint32_t)(a_desc0 >> 32);
             const uint32_t b_lo0 = (uint32_t)b_desc0, b_hi = (uint32_t)(b_desc0 >> 32);
             uint32_t ma = 0, md = 0, ready = 0;  // first input row of the run; gradient rows consumed; input rows landed
@@ -1751,9 +1747,9 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_co
                     for (int dy = 0; dy < 3; ++dy) {
                         const uint32_t a_row = a_lo0 + (((ma + (uint32_t)(j + dy)) % kWgActSlots) * kWgActBytes >> 4);
 #pragma unroll
-                        for (int ks = 0; ks < kTileM / 16; ++ks)
-                            tc::mma_bf16_w(tmem + (uint32_t)(dy * kWgN), a_row + (uint32_t)(ks * 16), a_hi,
-                                           b_row + (uint32_t)(ks * 16), b_hi, idesc, (first && ks == 0) ? 0u : 1u);
+                        for (int ks = 0; ks < kTileM / 16; ++ks)  // 16 pixels = two 512-byte atoms
+                            tc::mma_bf16_w(tmem + (uint32_t)(dy * kWgN), a_row + (uint32_t)(ks * 64), a_hi,
+                                           b_row + (uint32_t)(ks * 64), b_hi, idesc, (first && ks == 0) ? 0u : 1u);
                     }
                     first = false;
                     tc::mma_commit(&dempty[ds]);
@@ -1773,7 +1769,9 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_co
     } else {
         // bias sums: bias warp q adds pixels 32 q .. 32 q + 31 of every staged
         // gradient row; lane = 4 p8 + g holds channels 8 g .. 8 g + 7 of the
-        // pixels 32 q + 8 it + p8 (it = 0..3), hi + lo
+        // pixels 32 q + 8 it + p8 (it = 0..3), hi + lo.  In the 64-byte
+        // swizzle, channel group g of pixel px is the 16-byte chunk
+        // g ^ ((px >> 1) & 3) of the pixel's 64 bytes.
         const int q = warp - 2, g = lane & 3, p8 = lane >> 2;
         float acc[8];
 #pragma unroll
@@ -1789,8 +1787,9 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_co
 #pragma unroll
             for (int it = 0; it < 4; ++it) {
                 const int px = 32 * q + 8 * it + p8;
-                const uint4 h = *reinterpret_cast<const uint4 *>(dz + g * kWgPlane + px * 16);
-                const uint4 l = *reinterpret_cast<const uint4 *>(dz + (kGroups + g) * kWgPlane + px * 16);
+                const uint32_t at = px * 64 + ((g ^ ((px >> 1) & 3)) << 4);
+                const uint4 h = *reinterpret_cast<const uint4 *>(dz + at);
+                const uint4 l = *reinterpret_cast<const uint4 *>(dz + kWgBox + at);
                 const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -2226,13 +2225,13 @@ int launch_wgrad_tc(int L, int64_t C, const __nv_bfloat16 *a, const __nv_bfloat1
     const cuuint64_t dims[4] = {(cuuint64_t)kCh, (cuuint64_t)L + 2, (cuuint64_t)L, (cuuint64_t)C};
     const cuuint64_t strides[3] = {(cuuint64_t)kCh * 2, (cuuint64_t)(L + 2) * kCh * 2,
                                    (cuuint64_t)L * (L + 2) * kCh * 2};
-    const cuuint32_t box[4] = {8, kTileM, 1, 1};
+    const cuuint32_t box[4] = {kCh, kTileM, 1, 1};  // whole pixels, 64 bytes: the 64-byte swizzle
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     const __nv_bfloat16 *src[3] = {a, hi, lo};
     CUtensorMap *maps[3] = {&p.act, &p.hi, &p.lo};
     for (int t = 0; t < 3; ++t)
         if (fn(maps[t], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)src[t], dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return nfail(ISING_ECUDA, "cuTensorMapEncodeTiled failed");
     p.partial = partial;

@@ -32,6 +32,16 @@ __host__ __device__ constexpr uint64_t smem_desc(uint32_t saddr, uint32_t lbo, u
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// The same for an operand in the 64-byte-swizzled layout (layout type 4 in
+// bits 61-63): atoms of 8 rows of 64 bytes (512 bytes, 512-byte aligned), the
+// 16-byte chunks of a row permuted by the row pair.  For an MN-major operand
+// LBO is the distance between 32-element groups along M (or N) and SBO the
+// distance between 8-row groups along K.
+__host__ __device__ constexpr uint64_t smem_desc_sw64(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return smem_desc(saddr, lbo, sbo) | (4ull << 61);
+}
+
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator,
 // both operands K-major, dense: D format bits 4-5 = 1 (F32), A format bits
 // 7-9 = 1 (BF16), B format bits 10-12 = 1 (BF16), N >> 3 in bits 17-22,
