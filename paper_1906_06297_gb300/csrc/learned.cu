@@ -192,9 +192,44 @@ __device__ __forceinline__ void gelu2(float &z0, float &z1)
     f2_unpack(f2_fma(x, nq, f2_pack(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f))), z0, z1);
 }
 
+// gelu'(z) = Phi(z) + z phi(z), phi the normal density, with Phi from the
+// same Numerical Recipes erfc fit as gelu and phi(z) = 2^(-x^2 log2 e) /
+// sqrt(2 pi), x = |z| / sqrt 2; for two values at once (packed FP32 as in
+// gelu2).  Relative error about 1e-6, far below the gradient tolerance.
+__device__ __forceinline__ void gelu_grad2(float &z0, float &z1)
+{
+    const uint64_t x = f2_mul(f2_pack(fabsf(z0), fabsf(z1)), f2_splat(0.70710678118654752f));
+    float d0, d1;
+    f2_unpack(f2_fma(f2_splat(0.5f), x, f2_splat(1.0f)), d0, d1);
+    const uint64_t t = f2_pack(rcp_approx(d0), rcp_approx(d1));
+    uint64_t p = f2_splat(0.17087277f);
+    p = f2_fma(p, t, f2_splat(-0.82215223f));
+    p = f2_fma(p, t, f2_splat(1.48851587f));
+    p = f2_fma(p, t, f2_splat(-1.13520398f));
+    p = f2_fma(p, t, f2_splat(0.27886807f));
+    p = f2_fma(p, t, f2_splat(-0.18628806f));
+    p = f2_fma(p, t, f2_splat(0.09678418f));
+    p = f2_fma(p, t, f2_splat(0.37409196f));
+    p = f2_fma(p, t, f2_splat(1.00002368f));
+    p = f2_fma(p, t, f2_splat(-1.26551223f));
+    float x0, x1;
+    f2_unpack(x, x0, x1);
+    const uint64_t nx2 = f2_mul(f2_pack(-x0, -x1), x);  // -x^2
+    float a0, a1, b0, b1;
+    f2_unpack(f2_mul(f2_fma(f2_splat(1.0f), nx2, p), f2_splat(1.44269504088896341f)), a0, a1);
+    f2_unpack(f2_mul(nx2, f2_splat(1.44269504088896341f)), b0, b1);
+    float h0, h1, g0, g1;
+    f2_unpack(f2_mul(f2_mul(f2_splat(0.5f), t), f2_pack(ex2_approx(a0), ex2_approx(a1))), h0, h1);  // Phi(-|z|)
+    f2_unpack(f2_mul(f2_pack(ex2_approx(b0), ex2_approx(b1)), f2_splat(0.39894228040143268f)), g0, g1);  // phi(z)
+    const float P0 = z0 >= 0.0f ? 1.0f - h0 : h0, P1 = z1 >= 0.0f ? 1.0f - h1 : h1;
+    f2_unpack(f2_fma(f2_pack(z0, z1), f2_pack(g0, g1), f2_pack(P0, P1)), z0, z1);
+}
+
 __device__ __forceinline__ float gelu_grad(float z)
 {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+    float other = 0.0f;
+    gelu_grad2(z, other);
+    return z;
 }
 
 struct Chains {
@@ -1072,10 +1107,13 @@ __global__ void __launch_bounds__(ring_threads<PROJ, FUSED>(), 2) conv32_ring_ke
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const float4 zz = __ldg(zq + i);
-                        v[4 * i] *= gelu_grad(zz.x);
-                        v[4 * i + 1] *= gelu_grad(zz.y);
-                        v[4 * i + 2] *= gelu_grad(zz.z);
-                        v[4 * i + 3] *= gelu_grad(zz.w);
+                        float g0 = zz.x, g1 = zz.y, g2 = zz.z, g3 = zz.w;
+                        gelu_grad2(g0, g1);
+                        gelu_grad2(g2, g3);
+                        v[4 * i] *= g0;
+                        v[4 * i + 1] *= g1;
+                        v[4 * i + 2] *= g2;
+                        v[4 * i + 3] *= g3;
                         dq[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
                     }
                     if (p.a_out) {
@@ -1257,13 +1295,17 @@ __global__ void __launch_bounds__(kThreads) l4_bwd_data_kernel(int L, int64_t C,
         const float4 *zp = reinterpret_cast<const float4 *>(z3 + p * kCh + i8);
         const float4 za = zp[0], zb = zp[1];
         const float z[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
-        float v[8];
+        float v[8], gz[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) gz[i] = z[i];
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) gelu_grad2(gz[i], gz[i + 1]);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             float g = 0.0f;
 #pragma unroll
             for (int k = 0; k < 9; ++k) g = fmaf(W[(i8 + i) * 9 + k], d[k], g);
-            v[i] = g * gelu_grad(z[i]);
+            v[i] = g * gz[i];
         }
         float4 *out = reinterpret_cast<float4 *>(dz3 + p * kCh + i8);
         out[0] = make_float4(v[0], v[1], v[2], v[3]);
