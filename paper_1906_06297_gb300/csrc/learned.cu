@@ -1906,15 +1906,18 @@ __device__ int block_delta_E(const Chains &ch, int64_t c, int b)
 
 // t_b = min(0, -beta dE_b); r = logit - t; dlogits = 2 r / (C nb); per-chain
 // squared-residual sums for the loss.
-__global__ void targets_loss_kernel(Chains ch, int64_t C, double beta, const float *logits, float *dlogits,
-                                    float *chain_sq)
+// CTA per chain (kThreads threads): thread t takes blocks t, t + kThreads,
+// ...; the squared residuals are summed in a fixed order (per thread, then a
+// warp tree, then the warps in order).
+__global__ void __launch_bounds__(kThreads) targets_loss_kernel(Chains ch, int64_t C, double beta,
+                                                                const float *logits, float *dlogits, float *chain_sq)
 {
+    __shared__ float part[kThreads / 32];
     const int nb1 = ch.L / kBlk, nb = nb1 * nb1;
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < C; c += nw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t c = blockIdx.x; c < C; c += gridDim.x) {
         float sq = 0.0f;
-        for (int b = lane; b < nb; b += 32) {
+        for (int b = threadIdx.x; b < nb; b += kThreads) {
             const int dE = block_delta_E(ch, c, b);
             const float t = (float)fmin(0.0, -beta * (double)dE);
             const float r = logits[c * nb + b] - t;
@@ -1923,7 +1926,15 @@ __global__ void targets_loss_kernel(Chains ch, int64_t C, double beta, const flo
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
-        if (lane == 0) chain_sq[c] = sq;
+        __syncthreads();  // the previous chain's sums have been read
+        if (lane == 0) part[warp] = sq;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float tot = 0.0f;
+#pragma unroll
+            for (int q = 0; q < kThreads / 32; ++q) tot += part[q];
+            chain_sq[c] = tot;
+        }
     }
 }
 
@@ -2563,8 +2574,8 @@ ISING_API int ising_net_targets_loss(int64_t L, int64_t C, const void *black_dev
         return nfail(ISING_EINVAL, "chain_sq and loss must be device memory");
     cudaStream_t s = (cudaStream_t)stream;
     Chains ch{(const uint64_t *)black_dev, (const uint64_t *)white_dev, (int)L, (int)(L / 32)};
-    targets_loss_kernel<<<grid1d(C * 32, kThreads), kThreads, 0, s>>>(ch, C, beta, logits_dev, dlogits_dev,
-                                                                      chain_sq_dev);
+    targets_loss_kernel<<<(unsigned)std::min<int64_t>(C, 1 << 30), kThreads, 0, s>>>(ch, C, beta, logits_dev,
+                                                                                     dlogits_dev, chain_sq_dev);
     loss_reduce_kernel<<<1, 32, 0, s>>>(chain_sq_dev, C, (int)((L / 8) * (L / 8)), loss_dev);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ISING_OK : nfail(ISING_ECUDA, cudaGetErrorString(e));
