@@ -662,8 +662,11 @@ constexpr int kRingThreads = 64 + 32 * kEpiWarps;
 // one more warp: the second loader of the fused first conv, or the issuer of
 // the layer-4 projection MMAs (PROJ)
 constexpr int kRingExtra = 2 + kEpiWarps;
+// PROJ: four more warps (kRingExtra + 1 .. + 4, one per TMEM lane quadrant)
+// read the tap projections P out of tensor memory and store them
+constexpr int kProjWarps = 4;
 template <bool PROJ, bool FUSED>
-constexpr int ring_threads() { return (PROJ || FUSED) ? kRingThreads + 32 : kRingThreads; }
+constexpr int ring_threads() { return PROJ ? kRingThreads + 32 * (1 + kProjWarps) : (FUSED ? kRingThreads + 32 : kRingThreads); }
 constexpr int kProjN = 16;      // the 9 taps of layer 4, padded to an MMA N
 // channel-group planes 2176 bytes apart: each tensor copy lands on a 128-byte
 // boundary; 130 of its 136 16-byte entries are used
@@ -1065,22 +1068,7 @@ __global__ void __launch_bounds__(ring_threads<PROJ, FUSED>(), 2) conv32_ring_ke
         float bias[16];  // this warp's 16 channels (zero in BWD)
 #pragma unroll
         for (int i = 0; i < 16; ++i) bias[i] = sBias[16 * half + i];
-        // P of tile s, pixel q (one tile behind the accumulators)
-        auto read_proj = [&](int64_t s, int64_t q) -> bool {
-            const int b = (int)(s & 1);
-            if (!__all_sync(0xffffffffu, tc::mbar_wait(&pfull[b], (uint32_t)((s >> 1) & 1), kWaitCycles)))
-                return false;
-            tc::fence_after_sync();
-            float pv[16];
-            tc::tmem_ld16(tproj + (uint32_t)(b * kProjN) + ((uint32_t)(quad * 32) << 16), pv);
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&pempty[b]);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) p.P[k * npix + q] = pv[k];
-            return true;
-        };
-        int64_t t = 0, q_prev = 0;
+        int64_t t = 0;
         for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
             const RingUnit w = ring_unit(p, u);
             for (int j = 0; j < w.nrows; ++j, ++t) {
@@ -1160,16 +1148,36 @@ __global__ void __launch_bounds__(ring_threads<PROJ, FUSED>(), 2) conv32_ring_ke
                         tc::fence_async_smem();
                         __syncwarp();
                         if (lane == 0) tc::mbar_arrive(&a3full[b]);
-                        if (half == 0 && t >= 1 && !read_proj(t - 1, q_prev)) {
-                            ok = false;
-                            break;
-                        }
-                        q_prev = q;
                     }
                 }
             }
         }
-        if (PROJ && ok && half == 0 && t >= 1 && !read_proj(t - 1, q_prev)) ok = false;
+    } else if (PROJ && warp > kRingExtra && warp <= kRingExtra + kProjWarps) {
+        // P of every output row, pixel lane 32 quad + lane: waits for the
+        // projection (pfull), reads its 16 TMEM columns, frees them (pempty,
+        // four arrivals) and stores the 9 taps as FP32 planes P[k][pixel]
+        const int quad = warp & 3, m = quad * 32 + lane;
+        int64_t s = 0;
+        for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+            const RingUnit w = ring_unit(p, u);
+            for (int j = 0; j < w.nrows; ++j, ++s) {
+                const int b = (int)(s & 1);
+                if (!__all_sync(0xffffffffu, tc::mbar_wait(&pfull[b], (uint32_t)((s >> 1) & 1), kWaitCycles))) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                float pv[16];
+                tc::tmem_ld16(tproj + (uint32_t)(b * kProjN) + ((uint32_t)(quad * 32) << 16), pv);
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&pempty[b]);
+                const int y = ring_row(p, w.c, w.r0 + j);
+                const int64_t q = (w.c * L + y) * (int64_t)L + w.x0 + m;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) p.P[k * npix + q] = pv[k];
+            }
+        }
     }
     if (!ok) atomicExch(&g_tc_error, 1);
     tc::fence_before_sync();
