@@ -635,12 +635,14 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv32_tc_kernel(const __grid
 // here, on the tensor cores, as P[m][k] = sum_i a[m][i] W4[i][k] for the 9
 // taps k (N padded to 16): the epilogue stages the tile's a in shared memory
 // (a3full), lane 0 of a warp of its own (warp 10) multiplies it by W4^T into
-// 16 more TMEM columns (pfull, a3empty), and the epilogue warps of the first
-// channel half store P one tile later (pempty), as 9 FP32 planes P[k][pixel].
-// Then a3 itself need not reach global memory (it still does when training,
-// for the backward pass).  (With these MMAs on the row MMA thread, which then
-// waits for each tile's a3, a full forward of 1024 chains of 128^2 took
-// 1.383 ms instead of 1.371.)
+// 16 more TMEM columns (pfull, a3empty), and four more warps (11-14, one per
+// TMEM lane quadrant) store P (pempty), as 9 FP32 planes P[k][pixel].  Then
+// a3 itself need not reach global memory (it still does when training, for
+// the backward pass).  Measured per full forward of 1024 chains of 128^2:
+// these MMAs on the row MMA thread, which then waits for each tile's a3,
+// 1.383 ms; on their own warp with P stored by the epilogue warps of the
+// first channel half 1.371; as here 1.366; with three a3 tiles (planes 2048
+// bytes apart) 1.400.
 // BWD (the data gradient of a 32 -> 32 layer in the training backward pass):
 // the same contraction with the incoming gradient dz (bfloat16, halo columns)
 // as the staged rows and the weights transposed and tap-flipped, B_k[i][o] =
