@@ -847,10 +847,11 @@ def time_network(ising, torch, L, C, params, beta, seed, device, stream, reps=10
     conv_flops = 2 * 2 * (9 * 32) * 32 * px  # two 32 -> 32 layers, 2 flops per multiply-add
     # algorithmic HBM traffic of a full inference forward (layer 1 is formed inside the first
     # conv, so a1 never reaches HBM): a2 (bfloat16, rows of L + 2 pixels) written once and read
-    # once, the 9 FP32 tap projections written and read, the spins and the logits; the conv
-    # layers' operands are below the GB300 ridge (~280 FLOP/B), so HBM is the roofline
+    # once, the row partials of z4 (9 FP32 values per row and 8-pixel block column) written and
+    # read, the spins and the logits; the conv layers' operands are below the GB300 ridge
+    # (~280 FLOP/B), so HBM is the roofline
     act = C * L * (L + 2) * 64
-    alg_bytes = 2 * act + 2 * 9 * 4 * px + px // 2 + C * (L // 8) ** 2 * 4
+    alg_bytes = 2 * act + 2 * 9 * 4 * (px // 8) + px // 2 + C * (L // 8) ** 2 * 4
     peaks, source = measured_peaks()
     t = out["full_forward_ms"] * 1e-3
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))

@@ -804,7 +804,6 @@ __global__ void __launch_bounds__(ring_threads<PROJ, FUSED>(), 2) conv32_ring_ke
     uint32_t *tslot = reinterpret_cast<uint32_t *>(pdrain + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int L = p.bd.L;
-    const int64_t npix = p.bd.C * (int64_t)L * L;
 
     if (warp == 1) tc::tmem_alloc(tslot, kRingTmemCols);
     if (tid == 0) {
@@ -1174,10 +1173,29 @@ __global__ void __launch_bounds__(ring_threads<PROJ, FUSED>(), 2) conv32_ring_ke
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&pempty[b]);
+                // row partials of z4 (see pool_rows_kernel): P_k of this pixel
+                // (y, x), tap k = 3 (dy + 1) + (dx + 1), goes to z4 at (y - dy,
+                // x - dx); per dy, the part that stays in the pixel's 8 x 8
+                // block column is summed over the block's 8 pixels (xor tree),
+                // the block's first pixel sends its dx = +1 part to the block on
+                // the left and its last pixel its dx = -1 part to the right
                 const int y = ring_row(p, w.c, w.r0 + j);
-                const int64_t q = (w.c * L + y) * (int64_t)L + w.x0 + m;
+                const int x = w.x0 + m, u = lane & 7, bx = x / kBlk, nb1 = L / kBlk;
+                float *Rrow = p.P + (w.c * L + y) * (int64_t)(9 * nb1) + bx;
 #pragma unroll
-                for (int k = 0; k < 9; ++k) p.P[k * npix + q] = pv[k];
+                for (int d = 0; d < 3; ++d) {
+                    float own = pv[3 * d + 1];
+                    if (u != 0) own += pv[3 * d + 2];
+                    if (u != 7) own += pv[3 * d];
+                    own += __shfl_xor_sync(0xffffffffu, own, 1);
+                    own += __shfl_xor_sync(0xffffffffu, own, 2);
+                    own += __shfl_xor_sync(0xffffffffu, own, 4);
+                    if (u == 0) {
+                        Rrow[(3 * d + 0) * nb1] = own;
+                        Rrow[(3 * d + 1) * nb1] = pv[3 * d + 2];
+                    }
+                    if (u == 7) Rrow[(3 * d + 2) * nb1] = pv[3 * d];
+                }
             }
         }
     }
@@ -1268,6 +1286,44 @@ __global__ void __launch_bounds__(kThreads) pool_kernel(int L, int64_t C, int br
 #pragma unroll
         for (int off = 4; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
         if ((lane & 7) == 0) logits[c * nb + by * nb1 + 4 * bg + (lane >> 3)] = part * (1.0f / (kBlk * kBlk));
+    }
+}
+
+// The block logits from the row partials the projecting ring kernel writes
+// (L a multiple of 128): R[c][y][3 dy' + j][bx], dy' = dy + 1, holds for the
+// P values of row y with tap row dy (they feed z4 in row y - dy)
+//   j = 0: the sum over block column bx of the parts that stay in it,
+//   j = 1: the dx = +1 part of the block's first pixel (feeds block bx - 1),
+//   j = 2: the dx = -1 part of the block's last pixel (feeds block bx + 1),
+// so that sum over the block of z4 = 64 b4 + sum over its 8 rows y' and the
+// three dy of R[y' + dy][dy'][0][bx] + R[..][dy'][2][bx - 1] + R[..][dy'][1][bx + 1]
+// (periodic), added in that fixed order.  Thread per logit.
+__global__ void __launch_bounds__(kThreads) pool_rows_kernel(int L, int64_t C, int brows, const int32_t *flip,
+                                                             const float *params, const float *R, float *logits)
+{
+    const float b4 = bf16r(params[kOffB4]);
+    const int nb1 = L / kBlk, nb = nb1 * nb1;
+    const int64_t n = C * brows * nb1;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / (brows * nb1);
+        const int r = (int)(e - c * brows * nb1), rb = r / nb1, bx = r - rb * nb1;
+        int by = rb;
+        if (flip) {
+            const int f = flip[c];
+            by = wrap((f < 0 ? 0 : f / nb1) - 1 + rb, nb1);
+        }
+        const int bl = bx == 0 ? nb1 - 1 : bx - 1, br = bx + 1 == nb1 ? 0 : bx + 1;
+        float sum = 0.0f;
+#pragma unroll
+        for (int yy = 0; yy < kBlk; ++yy) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int y = wrap(by * kBlk + yy + d - 1, L);  // the source row of tap row dy = d - 1
+                const float *Rr = R + (c * L + y) * (int64_t)(9 * nb1) + 3 * d * nb1;
+                sum += __ldg(Rr + bx) + __ldg(Rr + 2 * nb1 + bl) + __ldg(Rr + nb1 + br);
+            }
+        }
+        logits[c * nb + by * nb1 + bx] = b4 + sum * (1.0f / (kBlk * kBlk));
     }
 }
 
@@ -2398,9 +2454,15 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
                                                                                              w.P);
     }
     const int brows = band ? kBandRows[3] : L / kBlk;
-    const int64_t warps = C * brows * (L / kBlk / 4);
-    pool_kernel<<<grid1d(warps * 32, kThreads), kThreads, 0, s>>>(L, C, brows, band ? flip : nullptr, params, w.P,
-                                                                  logits);
+    if (L % kTileM == 0) {
+        // the projecting ring kernel left row partials of z4 in w.P
+        pool_rows_kernel<<<grid1d(C * brows * (L / kBlk), kThreads), kThreads, 0, s>>>(
+            L, C, brows, band ? flip : nullptr, params, w.P, logits);
+    } else {
+        const int64_t warps = C * brows * (L / kBlk / 4);
+        pool_kernel<<<grid1d(warps * 32, kThreads), kThreads, 0, s>>>(L, C, brows, band ? flip : nullptr, params, w.P,
+                                                                      logits);
+    }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ISING_OK : nfail(ISING_ECUDA, cudaGetErrorString(e));
 }
