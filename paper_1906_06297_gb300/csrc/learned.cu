@@ -25,8 +25,10 @@
 // Forward kernels: layer 1 by table lookup (l1_table_kernel, l1_kernel); the
 // two 32 -> 32 layers on the tensor cores (tcgen05; conv32_ring_kernel for L
 // a multiple of 128, conv32_tc_kernel otherwise), the second one also
-// contracting layer 4's input channels (P, the 9 tap projections); the tap
-// sums and block means (pool_kernel).  Every reduction has a fixed order, so
+// contracting layer 4's input channels (P, the 9 tap projections; reduced to
+// row partials of z4 per 8-pixel block column where L is a multiple of 128);
+// the tap sums and block means (pool_rows_kernel, pool_kernel).  Every
+// reduction has a fixed order, so
 // a forward pass is a deterministic function of the state.  Backward kernels,
 // straight through the bfloat16 roundings: for L a multiple of 128 the data
 // and weight gradients of the two 32 -> 32 layers on the tensor cores
@@ -636,13 +638,14 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv32_tc_kernel(const __grid
 // taps k (N padded to 16): the epilogue stages the tile's a in shared memory
 // (a3full), lane 0 of a warp of its own (warp 10) multiplies it by W4^T into
 // 16 more TMEM columns (pfull, a3empty), and four more warps (11-14, one per
-// TMEM lane quadrant) store P (pempty), as 9 FP32 planes P[k][pixel].  Then
-// a3 itself need not reach global memory (it still does when training, for
-// the backward pass).  Measured per full forward of 1024 chains of 128^2:
-// these MMAs on the row MMA thread, which then waits for each tile's a3,
-// 1.383 ms; on their own warp with P stored by the epilogue warps of the
-// first channel half 1.371; as here 1.366; with three a3 tiles (planes 2048
-// bytes apart) 1.400.
+// TMEM lane quadrant) read P out (pempty) and reduce it to row partials of z4
+// (see pool_rows_kernel).  Then a3 itself need not reach global memory (it
+// still does when training, for the backward pass).  Measured per full
+// forward of 1024 chains of 128^2: these MMAs on the row MMA thread, which
+// then waits for each tile's a3, 1.383 ms; on their own warp with P stored as
+// 9 planes by the epilogue warps of the first channel half 1.371; stored by
+// the four P warps 1.366 (1.400 with three a3 tiles, planes 2048 bytes
+// apart); reduced to row partials as here 1.272.
 // BWD (the data gradient of a 32 -> 32 layer in the training backward pass):
 // the same contraction with the incoming gradient dz (bfloat16, halo columns)
 // as the staged rows and the weights transposed and tap-flipped, B_k[i][o] =
@@ -665,7 +668,8 @@ constexpr int kRingThreads = 64 + 32 * kEpiWarps;
 // the layer-4 projection MMAs (PROJ)
 constexpr int kRingExtra = 2 + kEpiWarps;
 // PROJ: four more warps (kRingExtra + 1 .. + 4, one per TMEM lane quadrant)
-// read the tap projections P out of tensor memory and store them
+// read the tap projections P out of tensor memory and reduce them to row
+// partials of z4
 constexpr int kProjWarps = 4;
 template <bool PROJ, bool FUSED>
 constexpr int ring_threads() { return PROJ ? kRingThreads + 32 * (1 + kProjWarps) : (FUSED ? kRingThreads + 32 : kRingThreads); }
@@ -2195,7 +2199,9 @@ int check_chains(int64_t L, int64_t C)
 // Work layout: training keeps z1 z2 z3 (FP32), a1 a2 a3 (bfloat16) and two
 // FP32 gradient buffers, then the weight-gradient partials; inference keeps
 // a1 and a2 (bfloat16; where a3 is written at all it reuses a1's buffer).
-// Both end with the 9 FP32 planes P of layer 4's tap projections.
+// Both end with room for the 9 FP32 planes P of layer 4's tap projections
+// (for L a multiple of 128 it holds the row partials of z4 instead, 9 values
+// per row and 8-pixel block column).
 struct NetWork {
     float *z1, *z2, *z3, *da, *db, *partial, *P, *tz;
     __nv_bfloat16 *a1, *a2, *a3, *ta, *gb1, *gb2;  // gb: bfloat16 gradients with halo columns (training)
