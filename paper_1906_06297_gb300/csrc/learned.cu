@@ -1688,15 +1688,18 @@ __global__ void __launch_bounds__(32 * kReduceWarps) reduce_partials_kernel(cons
 // 128).  With a the layer's input (bfloat16, halo columns) and dz the gradient
 // of its pre-activations,
 //   dW[o][i][k] = sum_p dz(p)[o] a(p + off_k)[i],   db[o] = sum_p dz(p)[o],
-// off_k = (dy - 1, dx - 1) for tap k = 3 dy + dx.  Per 128-pixel row segment
-// of output row y this is, for each dy, one GEMM over the 128 pixels (K):
-//   D_dy[m][n] += sum_x A_y+dy-1[m][x] B_y[n][x]
+// off_k = (dy - 1, dx - 1) for tap k = 3 dy + dx.  Input row y' meets the
+// gradient rows y' + 1, y', y' - 1 (dy = 0, 1, 2), so per 128-pixel row
+// segment of input row y' there is one GEMM over the segment's 128 pixels (K):
+//   D[m][n] += sum_x A_y'[m][x] B_y'[n][x]
 // with M = 128 rows, of which rows m = 32 dx + i (dx = 0..2) are the input row
-// y + dy - 1 shifted by dx - 1 and rows 96..127 are not used, and N = 64
-// columns n = 32 h + o: dz in two bfloat16 parts, h = 0 its rounding and
-// h = 1 the rounding of the remainder, so that a x (hi + lo) carries dz to
-// about 2^-17 and the FP32 accumulation sees the unrounded gradient to that
-// accuracy (dW = D[.][o] + D[.][32 + o]).
+// shifted by dx - 1 and rows 96..127 are not used, and N = 192 columns
+// n = 64 b + 32 h + o for the gradient rows y' - 1, y', y' + 1 (b = 0, 1, 2:
+// dy = 2 - b), each as two bfloat16 parts, h = 0 its rounding and h = 1 the
+// rounding of the remainder, so that a x (hi + lo) carries dz to about 2^-17
+// and the FP32 accumulation sees the unrounded gradient to that accuracy
+// (dW = D[.][64 b + o] + D[.][64 b + 32 + o]).  Eight MMAs of M128 x N192 x
+// K16 per input row segment.
 // Both operands are MN-major and come straight from the NHWC buffers: a
 // tensor copy of 128 whole pixels (32 channels, 64 bytes each) with the
 // 64-byte swizzle is the MN-major 64-byte-swizzled operand form: 8 K rows
@@ -1706,39 +1709,44 @@ __global__ void __launch_bounds__(32 * kReduceWarps) reduce_partials_kernel(cons
 // such copies, of the row starting at pixels x0 - 1 + dx; the unused M rows
 // 96..127 read the 8 KB after it (the next slot, or the first gradient slot
 // after the last one), whose products land in TMEM lanes no one reads.  A
-// staged gradient row is two copies (hi, lo).
+// staged gradient row is two copies (hi, lo) in a slot of a ring whose first
+// two slots are also copied behind its last one, so that any three
+// consecutive gradient rows lie at one stride (the N operand).
 // Work: the (chain, segment, row) lines of all chains are cut into one
 // contiguous range per CTA (ranges differ by at most one row); a range is
-// walked as runs of consecutive rows of one (chain, segment), each staging
-// its input rows r0 - 1 .. r0 + n once.  The three accumulators (3 x 64 TMEM
-// columns) collect the CTA's whole range; at the end they are written as the
-// CTA's partial sums in the weight-gradient layout (e = (o CIN + i) 9 + k,
-// then the biases).
+// walked as runs of consecutive gradient rows r0 .. r0 + n - 1 of one
+// (chain, segment).  A run stages the input rows r0 - 1 .. r0 + n and the
+// gradient rows r0 - 2 .. r0 + n + 1, those outside the run as zeros (tensor
+// copies of a row past the lattice's last, which the copy fills with zeros),
+// so that every (input row, gradient row) pair is counted by exactly one CTA.
+// The accumulators (192 TMEM columns) collect the CTA's whole range; at the
+// end they are written as the CTA's partial sums in the weight-gradient
+// layout (e = (o CIN + i) 9 + k, then the biases).
 // Warp roles (bounded mbarrier waits): warp 0 lane 0 issues the tensor
-// copies, up to 3 rows ahead; warp 1 lane 0 the MMAs (three per 16-pixel K
-// step: 24 per row); warps 2..5 add up every staged gradient row for the bias
-// sums (fixed order) and, after the last MMA, read the accumulators.  A
-// gradient slot is free once its MMAs have completed and the four bias
-// warps have read it.
-constexpr int kWgActSlots = 6;                      // staged input rows (3 in use, 3 ahead)
-constexpr int kWgDzSlots = 4;                       // staged gradient rows (1 in use, 3 ahead)
+// copies; warp 1 lane 0 the MMAs; warps 2..5 add up every staged gradient row
+// for the bias sums (fixed order; the zero rows add nothing) and, after the
+// last MMA, read the accumulators.  A gradient slot is free once the MMAs of
+// its last input row have completed and the four bias warps have read it.
+constexpr int kWgActSlots = 3;                      // staged input rows
+constexpr int kWgDzSlots = 4;                       // staged gradient rows (3 in use, 1 ahead)
+constexpr int kWgDzMirror = 2;                      // slots 0, 1 repeated after the last
 constexpr int kWgBiasWarps = 4;
 constexpr uint32_t kWgBox = kTileM * kCh * 2;      // 128 pixels x 32 channels, bfloat16, 64-byte swizzled
 constexpr uint32_t kWgActBytes = 3 * kWgBox;        // dx = 0, 1, 2
 constexpr uint32_t kWgDzBytes = 2 * kWgBox;         // hi, lo
 constexpr uint32_t kWgDz0 = kWgActSlots * kWgActBytes;
-constexpr uint32_t kWgBias = kWgDz0 + kWgDzSlots * kWgDzBytes;   // per bias warp 32 sums
+constexpr uint32_t kWgBias = kWgDz0 + (kWgDzSlots + kWgDzMirror) * kWgDzBytes;  // per bias warp 32 sums
 constexpr uint32_t kWgBar = kWgBias + kWgBiasWarps * kCh * 4;
 constexpr uint32_t kWgSmem = kWgBar + (2 * kWgActSlots + 2 * kWgDzSlots + 1) * 8 + 16;
 constexpr int kWgThreads = 64 + 32 * kWgBiasWarps;
-constexpr int kWgN = 2 * kCh;                       // columns per accumulator (hi, lo)
-constexpr uint32_t kWgTmemCols = 256;               // 3 x 64 used
+constexpr int kWgN = 6 * kCh;                       // three gradient rows, hi and lo
+constexpr uint32_t kWgTmemCols = 256;               // 192 used
 static_assert(kWgDz0 >= kWgActBytes + kWgBox && kWgSmem <= 227 * 1024 && kWgActBytes % 1024 == 0 &&
                   kWgDz0 % 1024 == 0,
               "the unused M rows of the last input slot read the gradient slots; one CTA per SM");
 
 struct WgradTc {
-    CUtensorMap act;  // a: (32 channels, L + 2 pixels, L rows, C chains), boxes 8 x 128 x 1 x 1
+    CUtensorMap act;  // a: (32 channels, L + 2 pixels, L rows, C chains), boxes 32 x 128 x 1 x 1, 64-byte swizzle
     CUtensorMap hi;   // bf16(dz), same layout
     CUtensorMap lo;   // bf16(dz - bf16(dz)), same layout
     float *partial;   // [gridDim.x][kN2 + kCh]
@@ -1805,22 +1813,28 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_co
                 ++na;
                 return true;
             };
+            // gradient row r of the run, or zeros (row L, past the lattice) when r is outside it
             auto stage_dz = [&](const RingUnit &w, int r) -> bool {
                 const uint32_t s = nd % kWgDzSlots;
                 if (nd >= kWgDzSlots && !tc::mbar_wait(&dempty[s], ((nd / kWgDzSlots) + 1) & 1, kWaitCycles))
                     return false;
-                tc::mbar_arrive_expect_tx(&dfull[s], kWgDzBytes);
-                uint8_t *dst = wg_smem + kWgDz0 + s * kWgDzBytes;
-                tc::tma_load_4d(dst, &p.hi, 0, w.x0 + 1, r, (int)w.c, &dfull[s]);
-                tc::tma_load_4d(dst + kWgBox, &p.lo, 0, w.x0 + 1, r, (int)w.c, &dfull[s]);
+                const int y = (r >= w.r0 && r < w.r0 + w.nrows) ? r : L;
+                const int copies = s < (uint32_t)kWgDzMirror ? 2 : 1;
+                tc::mbar_arrive_expect_tx(&dfull[s], copies * kWgDzBytes);
+                for (int k = 0; k < copies; ++k) {
+                    uint8_t *dst = wg_smem + kWgDz0 + (s + k * kWgDzSlots) * kWgDzBytes;
+                    tc::tma_load_4d(dst, &p.hi, 0, w.x0 + 1, y, (int)w.c, &dfull[s]);
+                    tc::tma_load_4d(dst + kWgBox, &p.lo, 0, w.x0 + 1, y, (int)w.c, &dfull[s]);
+                }
                 ++nd;
                 return true;
             };
             for (int64_t lin = begin; lin < end && ok;) {
                 const RingUnit w = wg_run(p, lin, end);
                 lin += w.nrows;
-                ok = stage_act(w, w.r0 - 1) && stage_act(w, w.r0);
-                for (int j = 0; j < w.nrows && ok; ++j) ok = stage_act(w, w.r0 + j + 1) && stage_dz(w, w.r0 + j);
+                // gradient rows r0 - 2, r0 - 1, then per input row r0 - 1 + a that row and gradient row r0 + a
+                ok = stage_dz(w, w.r0 - 2) && stage_dz(w, w.r0 - 1);
+                for (int a = 0; a < w.nrows + 2 && ok; ++a) ok = stage_act(w, w.r0 - 1 + a) && stage_dz(w, w.r0 + a);
             }
             // on a failure no copy may still be writing into shared memory when the CTA exits
             if (!ok) {
@@ -1838,40 +1852,37 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_co
             const uint64_t b_desc0 = tc::smem_desc_sw64(tc::smem_u32(wg_smem + kWgDz0), kWgBox, 512);
             const uint32_t a_lo0 = (uint32_t)a_desc0, a_hi = (uint32_t)(a_desc0 >> 32);
             const uint32_t b_lo0 = (uint32_t)b_desc0, b_hi = (uint32_t)(b_desc0 >> 32);
-            uint32_t ma = 0, md = 0, ready = 0;  // first input row of the run; gradient rows consumed; input rows landed
+            uint32_t ma = 0, md = 0, dready = 0;  // input rows consumed; first gradient row of the run; gradient rows landed
             bool first = true;
             for (int64_t lin = begin; lin < end && ok;) {
                 const RingUnit w = wg_run(p, lin, end);
                 lin += w.nrows;
-                for (int j = 0; j < w.nrows && ok; ++j) {
-                    // gradient row r0 + j needs input rows r0 + j - 1 .. r0 + j + 1 (indices ma + j .. ma + j + 2)
-                    while (ready < ma + (uint32_t)j + 3 && ok) {
-                        if (!tc::mbar_wait(&afull[ready % kWgActSlots], (ready / kWgActSlots) & 1u, kWaitCycles))
+                for (int a = 0; a < w.nrows + 2 && ok; ++a) {
+                    // input row r0 - 1 + a meets gradient rows r0 - 2 + a .. r0 + a (indices md + a .. md + a + 2)
+                    while (dready < md + (uint32_t)a + 3 && ok) {
+                        if (!tc::mbar_wait(&dfull[dready % kWgDzSlots], (dready / kWgDzSlots) & 1u, kWaitCycles))
                             ok = false;
-                        ++ready;
+                        ++dready;
                     }
-                    const uint32_t ds = md % kWgDzSlots;
-                    if (ok && !tc::mbar_wait(&dfull[ds], (md / kWgDzSlots) & 1u, kWaitCycles)) ok = false;
+                    const uint32_t as = ma % kWgActSlots;
+                    if (ok && !tc::mbar_wait(&afull[as], (ma / kWgActSlots) & 1u, kWaitCycles)) ok = false;
                     if (!ok) break;
                     tc::fence_after_sync();
-                    const uint32_t b_row = b_lo0 + ((ds * kWgDzBytes) >> 4);
+                    const uint32_t a_row = a_lo0 + ((as * kWgActBytes) >> 4);
+                    const uint32_t b_row = b_lo0 + ((((md + (uint32_t)a) % kWgDzSlots) * kWgDzBytes) >> 4);
 #pragma unroll
-                    for (int dy = 0; dy < 3; ++dy) {
-                        const uint32_t a_row = a_lo0 + (((ma + (uint32_t)(j + dy)) % kWgActSlots) * kWgActBytes >> 4);
-#pragma unroll
-                        for (int ks = 0; ks < kTileM / 16; ++ks)  // 16 pixels = two 512-byte atoms
-                            tc::mma_bf16_w(tmem + (uint32_t)(dy * kWgN), a_row + (uint32_t)(ks * 64), a_hi,
-                                           b_row + (uint32_t)(ks * 64), b_hi, idesc, (first && ks == 0) ? 0u : 1u);
-                    }
+                    for (int ks = 0; ks < kTileM / 16; ++ks)  // 16 pixels = two 512-byte atoms
+                        tc::mma_bf16_w(tmem, a_row + (uint32_t)(ks * 64), a_hi, b_row + (uint32_t)(ks * 64), b_hi, idesc,
+                                       (first && ks == 0) ? 0u : 1u);
                     first = false;
-                    tc::mma_commit(&dempty[ds]);
-                    ++md;
-                    tc::mma_commit(&aempty[(ma + (uint32_t)j) % kWgActSlots]);  // input row r0 + j - 1: last use
+                    tc::mma_commit(&aempty[as]);
+                    ++ma;
+                    tc::mma_commit(&dempty[(md + (uint32_t)a) % kWgDzSlots]);  // gradient row r0 - 2 + a: last use
                 }
                 if (!ok) break;
-                tc::mma_commit(&aempty[(ma + (uint32_t)w.nrows) % kWgActSlots]);
-                tc::mma_commit(&aempty[(ma + (uint32_t)w.nrows + 1) % kWgActSlots]);
-                ma += (uint32_t)w.nrows + 2;
+                tc::mma_commit(&dempty[(md + (uint32_t)w.nrows + 2) % kWgDzSlots]);
+                tc::mma_commit(&dempty[(md + (uint32_t)w.nrows + 3) % kWgDzSlots]);
+                md += (uint32_t)w.nrows + 4;
             }
             // every MMA has completed before the accumulators are read and the TMEM is freed
             tc::mma_commit(drain);
@@ -1880,16 +1891,21 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_co
         __syncwarp();
     } else {
         // bias sums: bias warp q adds pixels 32 q .. 32 q + 31 of every staged
-        // gradient row; lane = 4 p8 + g holds channels 8 g .. 8 g + 7 of the
-        // pixels 32 q + 8 it + p8 (it = 0..3), hi + lo.  In the 64-byte
-        // swizzle, channel group g of pixel px is the 16-byte chunk
-        // g ^ ((px >> 1) & 3) of the pixel's 64 bytes.
+        // gradient row (the zero rows add nothing); lane = 4 p8 + g holds
+        // channels 8 g .. 8 g + 7 of the pixels 32 q + 8 it + p8 (it = 0..3),
+        // hi + lo.  In the 64-byte swizzle, channel group g of pixel px is the
+        // 16-byte chunk g ^ ((px >> 1) & 3) of the pixel's 64 bytes.
         const int q = warp - 2, g = lane & 3, p8 = lane >> 2;
         float acc[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[j] = 0.0f;
-        const int64_t rows = end - begin;
-        for (int64_t md = 0; md < rows; ++md) {
+        int64_t staged = 0;  // gradient rows staged for this CTA: n + 4 per run
+        for (int64_t lin = begin; lin < end;) {
+            const RingUnit w = wg_run(p, lin, end);
+            lin += w.nrows;
+            staged += w.nrows + 4;
+        }
+        for (int64_t md = 0; md < staged; ++md) {
             const uint32_t ds = (uint32_t)(md % kWgDzSlots);
             if (!__all_sync(0xffffffffu, tc::mbar_wait(&dfull[ds], (uint32_t)(md / kWgDzSlots) & 1u, kWaitCycles))) {
                 ok = false;
@@ -1925,20 +1941,22 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_co
     tc::fence_after_sync();
     if (warp >= 2 && ok) {
         // TMEM lane m = 32 quad + lane: input channel i = lane of tap column
-        // dx = quad (quad < 3); lanes 96..127 are not used
+        // dx = quad (quad < 3); lanes 96..127 are not used.  Column block b
+        // holds tap row dy = 2 - b.
         const int quad = warp & 3;
         float *out = p.partial + (int64_t)blockIdx.x * (kN2 + kCh);
 #pragma unroll 1
-        for (int dy = 0; dy < 3; ++dy) {
+        for (int b = 0; b < 3; ++b) {
 #pragma unroll 1
             for (int oh = 0; oh < 2; ++oh) {
                 float vh[16], vl[16];
-                const uint32_t ta = tmem + (uint32_t)(dy * kWgN + 16 * oh) + ((uint32_t)(quad * 32) << 16);
+                const uint32_t ta = tmem + (uint32_t)(64 * b + 16 * oh) + ((uint32_t)(quad * 32) << 16);
                 tc::tmem_ld16(ta, vh);
                 tc::tmem_ld16(ta + (uint32_t)kCh, vl);
                 if (quad < 3)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) out[((16 * oh + j) * kCh + lane) * 9 + 3 * dy + quad] = vh[j] + vl[j];
+                    for (int j = 0; j < 16; ++j)
+                        out[((16 * oh + j) * kCh + lane) * 9 + 3 * (2 - b) + quad] = vh[j] + vl[j];
             }
         }
         if (warp == 2)
