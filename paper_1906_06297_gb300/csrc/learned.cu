@@ -1078,6 +1078,24 @@ __global__ void __launch_bounds__(ring_threads<PROJ, FUSED>(), 2) conv32_ring_ke
             const RingUnit w = ring_unit(p, u);
             for (int j = 0; j < w.nrows; ++j, ++t) {
                 const int a = ring_blk((uint32_t)t);
+                const int y = ring_row(p, w.c, w.r0 + j);
+                const int64_t q = (w.c * L + y) * (int64_t)L + w.x0 + m;
+                // BWD: gelu'(z_prev) of this row does not depend on the
+                // accumulator; load and evaluate it while the MMAs run
+                float gz[16];
+                if constexpr (BWD) {
+                    const float4 *zq = reinterpret_cast<const float4 *>(p.zg + q * kCh + 16 * half);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 zz = __ldg(zq + i);
+                        gz[4 * i] = zz.x;
+                        gz[4 * i + 1] = zz.y;
+                        gz[4 * i + 2] = zz.z;
+                        gz[4 * i + 3] = zz.w;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 16; i += 2) gelu_grad2(gz[i], gz[i + 1]);
+                }
                 if (!__all_sync(0xffffffffu, tc::mbar_wait(&accf[a], ring_use((uint32_t)t) & 1u, kWaitCycles))) {
                     ok = false;
                     break;
@@ -1092,23 +1110,12 @@ __global__ void __launch_bounds__(ring_threads<PROJ, FUSED>(), 2) conv32_ring_ke
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&acce[a]);
-                const int y = ring_row(p, w.c, w.r0 + j);
-                const int64_t q = (w.c * L + y) * (int64_t)L + w.x0 + m;
                 if constexpr (BWD) {
-                    const float4 *zq = reinterpret_cast<const float4 *>(p.zg + q * kCh + 16 * half);
                     float4 *dq = reinterpret_cast<float4 *>(p.d_out + q * kCh + 16 * half);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float4 zz = __ldg(zq + i);
-                        float g0 = zz.x, g1 = zz.y, g2 = zz.z, g3 = zz.w;
-                        gelu_grad2(g0, g1);
-                        gelu_grad2(g2, g3);
-                        v[4 * i] *= g0;
-                        v[4 * i + 1] *= g1;
-                        v[4 * i + 2] *= g2;
-                        v[4 * i + 3] *= g3;
-                        dq[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                    }
+                    for (int i = 0; i < 16; ++i) v[i] *= gz[i];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) dq[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
                     if (p.a_out) {
 #pragma unroll
                         for (int h8 = 0; h8 < 2; ++h8) {
