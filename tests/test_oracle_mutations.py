@@ -29,10 +29,13 @@ MUTANTS = {
     "swap_exponent_sign": ("double p = exp(-x);", "double p = exp(x);"),
     "swap_keeps_slot": ("                    slot_of[a] = (int32_t)(k + 1);\n", ""),
     "stream_ignored": ("ctr[1] = (uint32_t)(q >> 32) + stream;", "ctr[1] = (uint32_t)(q >> 32);"),
+    "black_is_odd": ("return (int)((i + c) & 1); }", "return (int)((i + c + 1) & 1); }"),
+    "plane_split_shifted": ("int8_t *dst = colour_of(i, c) == 0 ? black_row : white_row;",
+                            "int8_t *dst = colour_of(i, c + 1) == 0 ? black_row : white_row;"),
 }
 
 PIN_FILES = ["tests/test_oracle_philox.py", "tests/test_oracle_rules.py", "tests/test_oracle_batch.py",
-             "tests/test_oracle_statistics.py"]
+             "tests/test_oracle_statistics.py", "tests/test_golden.py"]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
