@@ -268,7 +268,8 @@ def sweep_roofline(torch, device, L, plane_bytes, launch_ms, mul_peak=None):
         "peak_derived": {"t_mul_per_s": round(derived_tmul, 3),
                          "derivation": f"{sms} SMs x {SMSP_PER_SM} sub-partitions x {WIDE_MUL_PER_CLK_PER_SMSP} "
                                        f"IMAD.WIDE/clk x {clk_hz / 1e6:.0f} MHz"},
-        "work_per_spin": f"{WIDE_MUL_PER_SPIN} wide multiplies per spin update (Philox4x32-10 per 4 draws)",
+        "work_per_spin": f"{WIDE_MUL_PER_SPIN} wide multiplies per spin update (Philox4x32-10 per 4 draws; "
+                         "every block computed, no skip of blocks whose 4 sites all have a <= 2)",
         "peak_flips_per_ns": round(peak_tmul * 1e12 / WIDE_MUL_PER_SPIN / 1e9, 1),
         "alg_bytes_per_launch": alg_bytes,
         "hbm": {"achieved": round(hbm_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
