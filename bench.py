@@ -70,7 +70,8 @@ def parse_args(argv=None):
                         "replicas: one independent lattice per GPU; pt / learned / ...: only that leg")
     p.add_argument("--no-learned", action="store_true", help="skip the learned block-proposal leg")
     p.add_argument("--learned-steps", type=int, default=1000, help="training steps of the proposal network")
-    p.add_argument("--learned-cycles", type=int, default=4500, help="measured sweep + move cycles")
+    p.add_argument("--learned-cycles", type=int, default=32000,
+                   help="measured sweep + move cycles (at least 50 tau_int of |m| at 128^2, beta_c)")
     p.add_argument("--learned-configs", type=int, default=100000, help="training configurations")
     p.add_argument("--learned-chains", type=int, default=1024, help="chains of the measured learned cycles")
     p.add_argument("--net-reps", type=int, default=10, help="timed network evaluations (--workload network)")
