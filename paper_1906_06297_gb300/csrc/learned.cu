@@ -686,14 +686,21 @@ constexpr int kRingBars = 2 * kRing + 2 * kAcc + 8 + 2;
 // ~60 KB of L1 (a 196 KB carveout), enough for layer 1's 32 KB table that the
 // fused first layer reads for every pixel (with the a3 tiles: 28 KB, and about
 // 40% of its table reads missed L1).
-template <bool PROJ>
+//
+// The data-gradient kernel (BWD) also holds a 2 KB staging tile per epilogue
+// warp: its FP32 loads and stores and its bfloat16 stores of a row go through
+// it, so that every global access of a warp covers whole sectors of a few
+// lines (a lane's own pixel is 64 or 128 bytes apart from its neighbour's).
+constexpr uint32_t kStageBytes = 32 * 16 * 4;  // 32 pixels x 16 FP32 channels
+template <bool PROJ, bool STAGE = false>
 struct RingLayout {
     static constexpr uint32_t ring = 0;
     static constexpr uint32_t a3 = ring + kRing * kRowBytes;
     static constexpr uint32_t b = PROJ ? a3 + 2 * kRowBytes : a3;
     static constexpr uint32_t w4 = b + kBBytes;
     static constexpr uint32_t bias = PROJ ? w4 + kW4Bytes : w4;
-    static constexpr uint32_t bar = bias + kCh * 4;
+    static constexpr uint32_t stage = bias + kCh * 4;
+    static constexpr uint32_t bar = STAGE ? stage + kEpiWarps * kStageBytes : stage;
     static constexpr uint32_t bytes = bar + kRingBars * 8 + 16;
 };
 constexpr uint32_t kRingTmemCols = 256;  // 7 x 32 accumulator + 2 x 16 projection columns
@@ -706,6 +713,70 @@ __device__ __forceinline__ uint32_t ring_use(uint32_t t) { return t / (uint32_t)
 static_assert((kRing & (kRing - 1)) == 0 && kRing >= 6, "ring of a power-of-two rows, 3 in use and 3 ahead");
 static_assert(2 * RingLayout<true>::bytes <= 228 * 1024, "two CTAs per SM");
 static_assert(2 * RingLayout<false>::bytes + 2048 <= 196 * 1024, "two CTAs per SM in a 196 KB carveout");
+static_assert(2 * RingLayout<false, true>::bytes <= 228 * 1024 && RingLayout<false, true>::stage % 16 == 0,
+              "two data-gradient CTAs per SM");
+
+// A warp's staging tile: 32 pixels (lane = pixel in the per-pixel accesses) x
+// 64 bytes.  FP32 tiles: chunk cc (4 channels, 16 bytes) of pixel pp at 16-byte
+// slot 4 pp + (cc ^ ((pp >> 1) & 3)); the coalesced accesses take lane =
+// 4 (pixel % 8) + chunk.  bfloat16 tiles (32 bytes per pixel): chunk cc (8
+// channels) at slot 2 pp + (cc ^ ((pp >> 2) & 1)), coalesced lane = 2 (pixel %
+// 16) + chunk.  Either way the eight lanes of each 128-bit shared-memory phase
+// hit eight different 16-byte slots of a 128-byte window: no bank conflicts.
+__device__ __forceinline__ int stage_slot32(int pp, int cc) { return 4 * pp + (cc ^ ((pp >> 1) & 3)); }
+__device__ __forceinline__ int stage_slot16(int pp, int cc) { return 2 * pp + (cc ^ ((pp >> 2) & 1)); }
+
+// v[16] = this lane's 16 FP32 channels of the tile at g (pixel pp at g + pp kCh).
+__device__ __forceinline__ void tile_load_f32(const float *g, float4 *stg, int lane, float (&v)[16])
+{
+    __syncwarp();
+    float4 t[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        t[k] = __ldg(reinterpret_cast<const float4 *>(g + (8 * k + (lane >> 2)) * kCh + 4 * (lane & 3)));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) stg[stage_slot32(8 * k + (lane >> 2), lane & 3)] = t[k];
+    __syncwarp();
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+        const float4 x = stg[stage_slot32(lane, cc)];
+        v[4 * cc] = x.x;
+        v[4 * cc + 1] = x.y;
+        v[4 * cc + 2] = x.z;
+        v[4 * cc + 3] = x.w;
+    }
+}
+
+// The tile at g = this lane's 16 FP32 channels v[16] (pixel pp at g + pp kCh).
+__device__ __forceinline__ void tile_store_f32(float *g, float4 *stg, int lane, const float (&v)[16])
+{
+    __syncwarp();
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc)
+        stg[stage_slot32(lane, cc)] = make_float4(v[4 * cc], v[4 * cc + 1], v[4 * cc + 2], v[4 * cc + 3]);
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        *reinterpret_cast<float4 *>(g + (8 * k + (lane >> 2)) * kCh + 4 * (lane & 3)) =
+            stg[stage_slot32(8 * k + (lane >> 2), lane & 3)];
+}
+
+// 16 bfloat16 channels per pixel (first8 = channels off .. off + 7, last8 =
+// off + 8 .. off + 15, packed) into activations `a`, pixels x0 .. x0 + 31 of
+// row y of chain c, with the halo column copies of pixels 0 and L - 1.
+__device__ __forceinline__ void tile_store_bf16(__nv_bfloat16 *a, int L, int64_t c, int y, int x0, int off,
+                                                uint4 *stg, int lane, uint4 first8, uint4 last8)
+{
+    __syncwarp();
+    stg[stage_slot16(lane, 0)] = first8;
+    stg[stage_slot16(lane, 1)] = last8;
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int pp = 16 * k + (lane >> 1), cc = lane & 1;
+        store_act(a, L, c, y, x0 + pp, off + 8 * cc, stg[stage_slot16(pp, cc)]);
+    }
+}
 static_assert(kAcc * kCh + 2 * kProjN <= (int)kRingTmemCols && 2 * kRingTmemCols <= 512, "TMEM columns");
 
 struct RingConv {
@@ -795,7 +866,7 @@ template <bool PROJ, bool BWD, bool FUSED>
 __global__ void __launch_bounds__(ring_threads<PROJ, FUSED>(), 2) conv32_ring_kernel(const __grid_constant__ RingConv p)
 {
     extern __shared__ __align__(1024) uint8_t ring_smem[];
-    using Lay = RingLayout<PROJ>;
+    using Lay = RingLayout<PROJ, BWD>;
     uint8_t *ring = ring_smem + Lay::ring;
     uint8_t *a3s = ring_smem + Lay::a3;
     uint8_t *sB = ring_smem + Lay::b;
@@ -1070,6 +1141,8 @@ __global__ void __launch_bounds__(ring_threads<PROJ, FUSED>(), 2) conv32_ring_ke
         __syncwarp();
     } else if (warp < 2 + kEpiWarps) {
         const int quad = warp & 3, half = (warp - 2) >> 2, m = quad * 32 + lane;
+        // BWD: this warp's staging tile
+        float4 *stg = reinterpret_cast<float4 *>(ring_smem + Lay::stage + (uint32_t)(warp - 2) * kStageBytes);
         float bias[16];  // this warp's 16 channels (zero in BWD)
 #pragma unroll
         for (int i = 0; i < 16; ++i) bias[i] = sBias[16 * half + i];
@@ -1081,18 +1154,12 @@ __global__ void __launch_bounds__(ring_threads<PROJ, FUSED>(), 2) conv32_ring_ke
                 const int y = ring_row(p, w.c, w.r0 + j);
                 const int64_t q = (w.c * L + y) * (int64_t)L + w.x0 + m;
                 // BWD: gelu'(z_prev) of this row does not depend on the
-                // accumulator; load and evaluate it while the MMAs run
+                // accumulator; load (through the warp's tile: q0 is the
+                // warp's first pixel) and evaluate it while the MMAs run
+                const int64_t q0 = q - lane;
                 float gz[16];
                 if constexpr (BWD) {
-                    const float4 *zq = reinterpret_cast<const float4 *>(p.zg + q * kCh + 16 * half);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float4 zz = __ldg(zq + i);
-                        gz[4 * i] = zz.x;
-                        gz[4 * i + 1] = zz.y;
-                        gz[4 * i + 2] = zz.z;
-                        gz[4 * i + 3] = zz.w;
-                    }
+                    tile_load_f32(p.zg + q0 * kCh + 16 * half, stg, lane, gz);
 #pragma unroll
                     for (int i = 0; i < 16; i += 2) gelu_grad2(gz[i], gz[i + 1]);
                 }
@@ -1111,24 +1178,27 @@ __global__ void __launch_bounds__(ring_threads<PROJ, FUSED>(), 2) conv32_ring_ke
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&acce[a]);
                 if constexpr (BWD) {
-                    float4 *dq = reinterpret_cast<float4 *>(p.d_out + q * kCh + 16 * half);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] *= gz[i];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) dq[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    tile_store_f32(p.d_out + q0 * kCh + 16 * half, stg, lane, v);
                     if (p.a_out) {
+                        uint32_t hb[2][4], rb[2][4];
 #pragma unroll
                         for (int h8 = 0; h8 < 2; ++h8) {
                             float v8[8];
 #pragma unroll
                             for (int i = 0; i < 8; ++i) v8[i] = v[8 * h8 + i];
-                            uint32_t hb[4], rb[4];
-                            split_bf16(v8, hb, rb);
-                            store_act(p.a_out, L, w.c, y, w.x0 + m, 16 * half + 8 * h8, make_uint4(hb[0], hb[1], hb[2], hb[3]));
-                            if (p.a_lo)
-                                store_act(p.a_lo, L, w.c, y, w.x0 + m, 16 * half + 8 * h8,
-                                          make_uint4(rb[0], rb[1], rb[2], rb[3]));
+                            split_bf16(v8, hb[h8], rb[h8]);
                         }
+                        uint4 *st16 = reinterpret_cast<uint4 *>(stg);
+                        const int xw = w.x0 + 32 * quad;  // the warp's first pixel
+                        tile_store_bf16(p.a_out, L, w.c, y, xw, 16 * half, st16, lane,
+                                        make_uint4(hb[0][0], hb[0][1], hb[0][2], hb[0][3]),
+                                        make_uint4(hb[1][0], hb[1][1], hb[1][2], hb[1][3]));
+                        if (p.a_lo)
+                            tile_store_bf16(p.a_lo, L, w.c, y, xw, 16 * half, st16, lane,
+                                            make_uint4(rb[0][0], rb[0][1], rb[0][2], rb[0][3]),
+                                            make_uint4(rb[1][0], rb[1][1], rb[1][2], rb[1][3]));
                     }
                 } else {
                     if (p.z_out) {
@@ -2354,8 +2424,8 @@ int launch_ring_bwd(int L, int64_t C, const float *params, int w_off, const __nv
     p.units = C * p.segs * p.units_per_col;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.units, 2 * info.sm_count));
     cudaFuncSetAttribute(conv32_ring_kernel<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)RingLayout<false>::bytes);
-    conv32_ring_kernel<false, true, false><<<grid, kRingThreads, RingLayout<false>::bytes, s>>>(p);
+                         (int)RingLayout<false, true>::bytes);
+    conv32_ring_kernel<false, true, false><<<grid, kRingThreads, RingLayout<false, true>::bytes, s>>>(p);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ISING_OK : nfail(ISING_ECUDA, cudaGetErrorString(e));
 }
