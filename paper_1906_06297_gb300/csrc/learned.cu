@@ -687,10 +687,11 @@ constexpr int kRingBars = 2 * kRing + 2 * kAcc + 8 + 2;
 // fused first layer reads for every pixel (with the a3 tiles: 28 KB, and about
 // 40% of its table reads missed L1).
 //
-// The data-gradient kernel (BWD) also holds a 2 KB staging tile per epilogue
-// warp: its FP32 loads and stores and its bfloat16 stores of a row go through
-// it, so that every global access of a warp covers whole sectors of a few
-// lines (a lane's own pixel is 64 or 128 bytes apart from its neighbour's).
+// The data-gradient kernel (BWD) and the training forward of the first
+// 32 -> 32 layer also hold a 2 KB staging tile per epilogue warp: their FP32
+// loads and stores and their bfloat16 stores of a row go through it, so that
+// every global access of a warp covers whole sectors of a few lines (a lane's
+// own pixel is 64 or 128 bytes apart from its neighbour's).
 constexpr uint32_t kStageBytes = 32 * 16 * 4;  // 32 pixels x 16 FP32 channels
 template <bool PROJ, bool STAGE = false>
 struct RingLayout {
@@ -866,7 +867,10 @@ template <bool PROJ, bool BWD, bool FUSED>
 __global__ void __launch_bounds__(ring_threads<PROJ, FUSED>(), 2) conv32_ring_kernel(const __grid_constant__ RingConv p)
 {
     extern __shared__ __align__(1024) uint8_t ring_smem[];
-    using Lay = RingLayout<PROJ, BWD>;
+    // the data-gradient kernel and the training forward of the first 32 -> 32
+    // layer (neither fused with layer 1 nor projecting) stage their epilogue I/O
+    constexpr bool STAGE = BWD || (!PROJ && !FUSED);
+    using Lay = RingLayout<PROJ, STAGE>;
     uint8_t *ring = ring_smem + Lay::ring;
     uint8_t *a3s = ring_smem + Lay::a3;
     uint8_t *sB = ring_smem + Lay::b;
@@ -1141,8 +1145,10 @@ __global__ void __launch_bounds__(ring_threads<PROJ, FUSED>(), 2) conv32_ring_ke
         __syncwarp();
     } else if (warp < 2 + kEpiWarps) {
         const int quad = warp & 3, half = (warp - 2) >> 2, m = quad * 32 + lane;
-        // BWD: this warp's staging tile
+        // STAGE: this warp's staging tile
         float4 *stg = reinterpret_cast<float4 *>(ring_smem + Lay::stage + (uint32_t)(warp - 2) * kStageBytes);
+        uint4 *st16 = reinterpret_cast<uint4 *>(stg);
+        const int xw = 32 * quad;  // the warp's first pixel in the tile (add w.x0)
         float bias[16];  // this warp's 16 channels (zero in BWD)
 #pragma unroll
         for (int i = 0; i < 16; ++i) bias[i] = sBias[16 * half + i];
@@ -1190,21 +1196,24 @@ __global__ void __launch_bounds__(ring_threads<PROJ, FUSED>(), 2) conv32_ring_ke
                             for (int i = 0; i < 8; ++i) v8[i] = v[8 * h8 + i];
                             split_bf16(v8, hb[h8], rb[h8]);
                         }
-                        uint4 *st16 = reinterpret_cast<uint4 *>(stg);
-                        const int xw = w.x0 + 32 * quad;  // the warp's first pixel
-                        tile_store_bf16(p.a_out, L, w.c, y, xw, 16 * half, st16, lane,
+                        tile_store_bf16(p.a_out, L, w.c, y, w.x0 + xw, 16 * half, st16, lane,
                                         make_uint4(hb[0][0], hb[0][1], hb[0][2], hb[0][3]),
                                         make_uint4(hb[1][0], hb[1][1], hb[1][2], hb[1][3]));
                         if (p.a_lo)
-                            tile_store_bf16(p.a_lo, L, w.c, y, xw, 16 * half, st16, lane,
+                            tile_store_bf16(p.a_lo, L, w.c, y, w.x0 + xw, 16 * half, st16, lane,
                                             make_uint4(rb[0][0], rb[0][1], rb[0][2], rb[0][3]),
                                             make_uint4(rb[1][0], rb[1][1], rb[1][2], rb[1][3]));
                     }
                 } else {
                     if (p.z_out) {
-                        float4 *zo = reinterpret_cast<float4 *>(p.z_out + q * kCh + 16 * half);
+                        if constexpr (STAGE) {
+                            tile_store_f32(p.z_out + q0 * kCh + 16 * half, stg, lane, v);
+                        } else {
+                            float4 *zo = reinterpret_cast<float4 *>(p.z_out + q * kCh + 16 * half);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) zo[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                            for (int i = 0; i < 4; ++i)
+                                zo[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                        }
                     }
                     uint32_t pk[8];
 #pragma unroll
@@ -1214,8 +1223,14 @@ __global__ void __launch_bounds__(ring_threads<PROJ, FUSED>(), 2) conv32_ring_ke
                         pk[i] = pack_bf16x2(g0, g1);
                     }
                     if (p.a_out) {
-                        store_act(p.a_out, L, w.c, y, w.x0 + m, 16 * half, make_uint4(pk[0], pk[1], pk[2], pk[3]));
-                        store_act(p.a_out, L, w.c, y, w.x0 + m, 16 * half + 8, make_uint4(pk[4], pk[5], pk[6], pk[7]));
+                        if constexpr (STAGE) {
+                            tile_store_bf16(p.a_out, L, w.c, y, w.x0 + xw, 16 * half, st16, lane,
+                                            make_uint4(pk[0], pk[1], pk[2], pk[3]), make_uint4(pk[4], pk[5], pk[6], pk[7]));
+                        } else {
+                            store_act(p.a_out, L, w.c, y, w.x0 + m, 16 * half, make_uint4(pk[0], pk[1], pk[2], pk[3]));
+                            store_act(p.a_out, L, w.c, y, w.x0 + m, 16 * half + 8,
+                                      make_uint4(pk[4], pk[5], pk[6], pk[7]));
+                        }
                     }
                     if (PROJ) {
                         const int b = (int)(t & 1);
@@ -2501,7 +2516,7 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
         cudaFuncSetAttribute(conv32_ring_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)RingLayout<false>::bytes);
         cudaFuncSetAttribute(conv32_ring_kernel<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)RingLayout<false>::bytes);
+                             (int)RingLayout<false, true>::bytes);
         cudaFuncSetAttribute(conv32_ring_kernel<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)RingLayout<true>::bytes);
         // shared memory for two CTAs of the first conv, the rest as L1 for the layer-1 table
@@ -2531,7 +2546,7 @@ int launch_forward(const Chains &ch, int64_t C, const int32_t *flip, bool band, 
             if (fused)
                 conv32_ring_kernel<false, false, true><<<grid, ring_threads<false, true>(), RingLayout<false>::bytes, s>>>(p);
             else if (l == 0)
-                conv32_ring_kernel<false, false, false><<<grid, kRingThreads, RingLayout<false>::bytes, s>>>(p);
+                conv32_ring_kernel<false, false, false><<<grid, kRingThreads, RingLayout<false, true>::bytes, s>>>(p);
             else
                 conv32_ring_kernel<true, false, false><<<grid, ring_threads<true, false>(), RingLayout<true>::bytes, s>>>(p);
         }
