@@ -681,8 +681,8 @@ constexpr uint32_t kRowBytes = kGroups * kRingPlane;   // one staged row, or one
 constexpr uint32_t kW4Bytes = kGroups * kProjN * 16;   // 1024
 constexpr int kRingBars = 2 * kRing + 2 * kAcc + 8 + 2;
 // Shared-memory layout: the staged rows, then (only in the kernel that
-// projects onto layer 4) two a3 tiles, the weights, (PROJ) W4^T, the bias and
-// the barriers.  Without the a3 tiles two CTAs take 173 KB, so the SM keeps
+// projects onto layer 4) two a3 tiles, the weights, (PROJ) W4^T, the bias,
+// (STAGE) the epilogue warps' staging tiles and the barriers.  Without the a3 tiles two CTAs take 173 KB, so the SM keeps
 // ~60 KB of L1 (a 196 KB carveout), enough for layer 1's 32 KB table that the
 // fused first layer reads for every pixel (with the a3 tiles: 28 KB, and about
 // 40% of its table reads missed L1).
